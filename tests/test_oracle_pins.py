@@ -1,0 +1,388 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed forms, exact
+invariants, brute-force sums on tiny inputs, special cases that reduce to textbook results,
+or finite differences. Together they are chosen so that a dropped term, a wrong sign, index
+or offset, or a transposed operand in any oracle step fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2103_02046_gb300 import bunches as B
+
+KE = O.coulomb_k()
+
+
+def small_params(**kw):
+    base = dict(n=(8, 9, 10), lo=(-1.0e-3, -1.1e-3, 0.2e-3), h=(0.25e-3, 0.27e-3, 0.22e-3))
+    base.update(kw)
+    return O.Params(**base)
+
+
+def random_inside(P, N, seed, margin=1.6):
+    rng = np.random.default_rng(seed)
+    lo = np.array(P.lo) + margin * np.array(P.h)
+    hi = np.array(P.lo) + (np.array(P.n) - 1 - margin) * np.array(P.h)
+    return lo + rng.random((N, 3)) * (hi - lo)
+
+
+# ------------------------------------------------------------------------------------------
+# deposit (eq. (rho_L))
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [1, 2])
+def test_deposit_total_charge_and_first_moment(order):
+    P = small_params(assign_order=order)
+    x = random_inside(P, 500, 1)
+    Q, bad = O.deposit(x, P)
+    assert bad == 0
+    assert abs(Q.sum() - len(x) * P.q) <= 1e-13 * len(x) * P.q
+    # B-splines of order >= 1 reproduce linear functions: sum_g Q_g x_g = q sum_i xi_i
+    gz, gy, gx = np.meshgrid(*[np.arange(P.n[d]) for d in (2, 1, 0)], indexing="ij")
+    for d, g in zip(range(3), (gx, gy, gz)):
+        xg = P.lo[d] + g * P.h[d]
+        assert abs((Q * xg).sum() - P.q * x[:, d].sum()) <= 1e-12 * P.q * np.abs(x[:, d]).sum()
+
+
+def test_tsc_single_particle_on_node_and_second_moment():
+    P = small_params()
+    node = np.array([3, 4, 5])
+    x = (np.array(P.lo) + node * np.array(P.h))[None, :]
+    Q, _ = O.deposit(x, P)
+    assert Q[5, 4, 3] == pytest.approx(P.q * 27 / 64, rel=1e-14)
+    assert Q[5, 4, 4] == pytest.approx(P.q * (3 / 4) ** 2 / 8, rel=1e-14)
+    assert Q[6, 5, 4] == pytest.approx(P.q / 512, rel=1e-14)
+    assert np.count_nonzero(Q) == 27
+    # the TSC kernel has variance 1/4 (in mesh units) wherever the particle sits
+    rng = np.random.default_rng(3)
+    gz, gy, gx = np.meshgrid(*[np.arange(P.n[d]) for d in (2, 1, 0)], indexing="ij")
+    for _ in range(5):
+        x = random_inside(P, 1, int(rng.integers(1 << 30)))
+        Q, _ = O.deposit(x, P)
+        for d, g in zip(range(3), (gx, gy, gz)):
+            s = (x[0, d] - P.lo[d]) / P.h[d]
+            assert (Q * (g - s) ** 2).sum() / P.q == pytest.approx(0.25, abs=1e-12)
+
+
+def test_deposit_counts_invalid_particles():
+    P = small_params()
+    x = random_inside(P, 10, 2)
+    x[3, 0] = P.lo[0] + 0.3 * P.h[0]  # nearest node 0: outside the TSC-valid range
+    x[7, 2] = P.lo[2] + (P.n[2] - 1.2) * P.h[2]  # nearest node n-1
+    Q, bad = O.deposit(x, P)
+    assert bad == 2
+    assert Q.sum() == pytest.approx(8 * P.q, rel=1e-13)
+
+
+# ------------------------------------------------------------------------------------------
+# interpolation / long-range force (eq. (eom_p3m_coord))
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [1, 2])
+def test_interp_linear_potential_gives_uniform_force(order):
+    P = small_params(assign_order=order)
+    a = np.array([3.0e4, -1.5e4, 2.2e4])
+    gz, gy, gx = np.meshgrid(*[np.arange(P.n[d]) for d in (2, 1, 0)], indexing="ij")
+    phi = (a[0] * (P.lo[0] + gx * P.h[0]) + a[1] * (P.lo[1] + gy * P.h[1])
+           + a[2] * (P.lo[2] + gz * P.h[2]) + 7.0)
+    x = random_inside(P, 200, 4)
+    F, pa, bad = O.interp(x, phi, P)
+    assert bad == 0
+    np.testing.assert_allclose(F, np.broadcast_to(-P.q * a, F.shape), rtol=1e-10)
+    np.testing.assert_allclose(pa, x @ a + 7.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("pm_bc", [0, 1])
+def test_long_range_force_is_minus_gradient_of_mesh_energy(pm_bc):
+    P = small_params(pm_bc=pm_bc, z_cathode=0.0)
+    x = random_inside(P, 6, 5, margin=2.0)
+    kern = O.green_kernels(P)
+
+    def energy(y):
+        Q, _ = O.deposit(y, P)
+        return 0.5 * float(np.sum(Q * O.solve(Q, P, kern)))
+
+    r = O.forces(x, P, kernels=kern, parts=2)
+    eps = 1e-7 * min(P.h)
+    for i in range(len(x)):
+        for d in range(3):
+            xp = x.copy(); xp[i, d] += eps
+            xm = x.copy(); xm[i, d] -= eps
+            fd = -(energy(xp) - energy(xm)) / (2 * eps)
+            assert fd == pytest.approx(r.F_pm[i, d], rel=1e-5, abs=1e-7 * np.abs(r.F_pm).max())
+
+
+# ------------------------------------------------------------------------------------------
+# mesh solve (eq. (phi_L), eq. (GreenFunc_planar_cathode))
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("pm_bc", [0, 1])
+def test_fft_solve_equals_direct_sum(pm_bc):
+    P = small_params(pm_bc=pm_bc, z_cathode=0.1e-3, rc_over_h=2.0)
+    x = random_inside(P, 300, 6)
+    Q, _ = O.deposit(x, P)
+    np.testing.assert_allclose(O.solve(Q, P), O.mesh_direct(Q, P), rtol=1e-11,
+                               atol=1e-12 * np.abs(O.mesh_direct(Q, P)).max())
+
+
+@pytest.mark.parametrize("pm_bc", [0, 1])
+def test_solve_point_charge_closed_form(pm_bc):
+    # With alpha so large that erf(alpha r) = 1 at every node distance >= h, G^L is the Coulomb
+    # kernel and the potential of one node charge is k_e Q (1/r - 1/r_image).
+    P = small_params(pm_bc=pm_bc, z_cathode=-0.05e-3, alpha=1e6)
+    Q = np.zeros((P.n[2], P.n[1], P.n[0]))
+    src = (4, 3, 2)  # (gz, gy, gx)
+    Q[src] = 2.5e-15
+    phi = O.solve(Q, P)
+    gz, gy, gx = np.meshgrid(*[np.arange(P.n[d]) for d in (2, 1, 0)], indexing="ij")
+    X = [P.lo[0] + gx * P.h[0], P.lo[1] + gy * P.h[1], P.lo[2] + gz * P.h[2]]
+    S = [P.lo[0] + src[2] * P.h[0], P.lo[1] + src[1] * P.h[1], P.lo[2] + src[0] * P.h[2]]
+    r = np.sqrt((X[0] - S[0]) ** 2 + (X[1] - S[1]) ** 2 + (X[2] - S[2]) ** 2)
+    ri = np.sqrt((X[0] - S[0]) ** 2 + (X[1] - S[1]) ** 2 + (X[2] + S[2] - 2 * P.z_cathode) ** 2)
+    mask = r > 0
+    expect = KE * 2.5e-15 * (1.0 / r[mask] - (pm_bc / ri[mask]))
+    np.testing.assert_allclose(phi[mask], expect, rtol=1e-11)
+
+
+def test_influence_factor_is_bspline_transform():
+    # U(k) must be the continuous Fourier transform of the assignment function: for TSC the
+    # triple convolution of the unit box, i.e. sinc(k h/2)^3. Integrate the TSC shape numerically.
+    P = O.Params(n=(8, 8, 8), h=(1.0, 1.0, 1.0), assign_order=2)
+    U2 = O._assignment_spectrum_sq(P)
+    t = np.linspace(-1.5, 1.5, 300001)
+    w = np.where(np.abs(t) <= 0.5, 0.75 - t * t,
+                 np.where(np.abs(t) <= 1.5, 0.5 * (1.5 - np.abs(t)) ** 2, 0.0))
+    for kx in (0, 1, 3, 8):
+        k = 2 * math.pi * kx / 16.0
+        ft = np.trapezoid(w * np.cos(k * t), t)
+        assert U2[0, 0, kx] == pytest.approx(ft ** 2, rel=1e-8)
+
+
+# ------------------------------------------------------------------------------------------
+# short range (eq. (summation_short) with G^S = erfc(a r)/r)
+# ------------------------------------------------------------------------------------------
+def cathode_bunch(N, seed, zc=0.0):
+    x = B.gaussian(N, (1e-3, 1e-3, 1e-3), seed)
+    return B.lift_to_plane(x, zc, 0.05e-3)
+
+
+@pytest.mark.parametrize("pp_bc", [0, 1])
+def test_pp_cell_list_equals_brute_force(pp_bc):
+    x = cathode_bunch(1500, 7)
+    P = O.auto_mesh(x, 16, pp_bc=pp_bc, pm_bc=1, rc_over_h=3.0)
+    Fc, pc, cc = O.pp(x, P)
+    Fb, pb, cb = O.pp_brute(x, P)
+    assert cc == cb
+    assert cc[0] > 1000 and (pp_bc == 0 or cc[1] > 10)
+    np.testing.assert_allclose(Fc, Fb, rtol=1e-12, atol=1e-13 * np.abs(Fb).max())
+    np.testing.assert_allclose(pc, pb, rtol=1e-12, atol=1e-13 * np.abs(pb).max())
+    # a sample gives the same rows
+    idx = np.array([0, 17, 999, 1499])
+    Fs, _, _ = O.pp(x, P, sample=idx)
+    np.testing.assert_allclose(Fs, Fc[idx], rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_pp_reduces_to_coulomb_without_screening(bc):
+    # alpha -> 0 and r_c -> infinity turn the screened sum into the plain Coulomb sum.
+    x = cathode_bunch(300, 8)
+    P = O.Params(alpha=1e-9, rc_over_h=1e6, h=(1e-3, 1e-3, 1e-3), pp_bc=bc, z_cathode=0.0)
+    F, phi, _ = O.pp_brute(x, P)
+    Fc, phic = O.coulomb_brute(x, P, bc=bc)
+    np.testing.assert_allclose(F, Fc, rtol=1e-7, atol=1e-9 * np.abs(Fc).max())
+    np.testing.assert_allclose(phi, phic, rtol=1e-6)
+
+
+def test_coulomb_two_charges_and_own_image():
+    q = 1e-15
+    P = O.Params(q=q, z_cathode=0.0)
+    x = np.array([[0.0, 0.0, 1e-3], [0.0, 2e-3, 1e-3]])
+    F, phi = O.coulomb_brute(x, P, bc=0)
+    assert F[0, 1] == pytest.approx(-KE * q * q / 4e-6, rel=1e-14)
+    assert F[1, 1] == pytest.approx(KE * q * q / 4e-6, rel=1e-14)
+    x1 = np.array([[0.3e-3, -0.2e-3, 0.7e-3]])
+    F, phi = O.coulomb_brute(x1, P, bc=1)
+    # a charge at height z above a grounded plane is pulled down with k_e q^2 / (2z)^2
+    assert F[0, 2] == pytest.approx(-KE * q * q / (1.4e-3) ** 2, rel=1e-14)
+    assert F[0, 0] == 0.0 and F[0, 1] == 0.0
+    assert phi[0] == pytest.approx(-KE * q / 1.4e-3, rel=1e-14)
+
+
+def test_isolated_particle_short_range_image_force():
+    # Sec. 3.1.1: the short-range error of neglecting the cathode is the screened field of the
+    # particle's own image; it vanishes once the image is beyond the cutoff (2z >= r_c).
+    q = 1e-15
+    rc = 0.3e-3
+    P = O.Params(q=q, h=(rc / 3,) * 3, rc_over_h=3.0, kappa=3.0, pp_bc=1, z_cathode=0.0)
+    a = P.a
+    for z in (0.02e-3, 0.07e-3, 0.149e-3, 0.151e-3, 0.4e-3):
+        x = np.array([[0.1e-3, 0.2e-3, z]])
+        F, _, cnt = O.pp(x, P)
+        d = 2 * z
+        if d < rc:
+            expect = -KE * q * q * (math.erfc(a * d) / d ** 2
+                                    + 2 * a / math.sqrt(math.pi) * math.exp(-a * a * d * d) / d)
+            assert F[0, 2] == pytest.approx(expect, rel=1e-13)
+            assert cnt[1] == 1
+        else:
+            assert F[0, 2] == 0.0 and cnt[1] == 0
+        assert F[0, 0] == 0.0 and F[0, 1] == 0.0
+
+
+def test_pp_momentum_conservation():
+    x = B.gaussian(3000, (1e-3, 1e-3, 2e-3), 9)
+    P = O.auto_mesh(x, 16, rc_over_h=2.0)
+    F, _, cnt = O.pp(x, P)
+    assert cnt[0] > 10000
+    assert np.abs(F.sum(axis=0)).max() <= 1e-13 * np.abs(F).sum()
+
+
+def test_pp_boundary_error_is_local():
+    # Sec. 3.1.1 (fig. ShortError): treating the cathode in the short range changes only the
+    # forces of particles whose images come within r_c, i.e. z_i + z_j - 2 z_c < r_c. Particles
+    # at least r_c above the plane are exactly unaffected.
+    zc = 0.1e-3
+    x = cathode_bunch(4000, 10, zc)
+    P0 = O.auto_mesh(x, 16, rc_over_h=3.0, pm_bc=1, pp_bc=0, z_cathode=zc)
+    P1 = O.replace(P0, pp_bc=1)
+    F0, _, _ = O.pp(x, P0)
+    F1, _, c1 = O.pp(x, P1)
+    dz = x[:, 2] - zc
+    far = dz >= P0.rc
+    assert np.all(F1[far] == F0[far])
+    near = dz < 0.5 * P0.rc
+    assert near.sum() > 3 and np.all(np.abs(F1[near] - F0[near]).sum(axis=1) > 0)
+    assert c1[1] > 0
+
+
+# ------------------------------------------------------------------------------------------
+# whole method
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", [0, 1])
+def test_p3m_converges_to_coulomb(bc):
+    x = B.gaussian(4096, (1e-3, 1e-3, 1e-3), 0)
+    if bc:
+        x = B.lift_to_plane(x, 0.0, 0.2e-3)
+    Fb, _ = O.coulomb_brute(x, O.Params(z_cathode=0.0), bc=bc)
+    errs = []
+    for n in (16, 32):
+        P = O.auto_mesh(x, n, rc_over_h=2.0, pm_bc=bc, z_cathode=0.0)
+        errs.append(O.rel_l2(O.forces(x, P).F, Fb))
+    assert errs[1] < 0.5 * errs[0]
+    assert errs[1] < 0.05
+
+
+def test_uniform_sphere_radial_field():
+    # Inside a uniformly charged sphere E(r) = k_e Q r / R^3; shell averages of F.r/(q r)
+    # must reproduce it (graininess averages out over a shell).
+    N, R = 40000, 1e-3
+    x = B.uniform_sphere(N, R, 11)
+    P = O.auto_mesh(x, 32, rc_over_h=2.0)
+    F = O.forces(x, P).F
+    r = np.linalg.norm(x, axis=1)
+    Er = np.einsum("ij,ij->i", F, x) / r / P.q
+    expect = KE * N * P.q / R ** 3
+    for a, b in ((0.3, 0.5), (0.5, 0.7), (0.7, 0.85)):
+        m = (r > a * R) & (r < b * R)
+        assert np.mean(Er[m] / r[m]) == pytest.approx(expect, rel=0.03)
+
+
+# ------------------------------------------------------------------------------------------
+# leapfrog (eq. (leapfrog))
+# ------------------------------------------------------------------------------------------
+def test_kdk_harmonic_closed_form():
+    # For F = -K x the kick-drift-kick map is linear with cos(theta) = 1 - w^2 dt^2 / 2 and
+    # x_n = x_0 cos(n theta) + (p_{1/2}-based) sin term; check against the closed form.
+    M, K, dt = 2.0, 3.0, 0.1
+    P = O.Params(mass=M)
+    w2 = K / M
+    th = math.acos(1 - 0.5 * w2 * dt * dt)
+    x0 = np.array([[0.7, -0.2, 0.1]])
+    p0 = np.array([[0.0, 0.5, -0.3]])
+    n = 37
+    xn, pn, _ = O.push(x0, p0, dt, n, P, force=lambda y: -K * y)
+    # closed form for the map A = [[1 - a, dt/M], [-K dt (1 - a/2), 1 - a]], a = w^2 dt^2 / 2
+    a = 0.5 * w2 * dt * dt
+    c12 = dt / M
+    xe = x0 * math.cos(n * th) + (x0 * (1 - a) + c12 * p0 - x0 * math.cos(th)) * math.sin(n * th) / math.sin(th)
+    np.testing.assert_allclose(xn, xe, rtol=1e-12, atol=1e-13)
+
+
+def test_push_time_reversible():
+    x = B.gaussian(256, (1e-3, 1e-3, 1e-3), 12)
+    p = B.thermal_momenta(256, 1e-4 * B.macro_mass() * B.SPEED_OF_LIGHT, 13)
+    P = O.auto_mesh(x, 8, rc_over_h=2.0)
+    kern = O.green_kernels(P)
+    f = lambda y: O.forces(y, P, kernels=kern).F
+    x1, p1, _ = O.push(x, p, 1e-12, 10, P, force=f)
+    x2, p2, _ = O.push(x1, -p1, 1e-12, 10, P, force=f)
+    np.testing.assert_allclose(x2, x, rtol=0, atol=1e-12 * np.abs(x).max())
+    np.testing.assert_allclose(-p2, p, rtol=0, atol=1e-9 * np.abs(p).max())
+
+
+# ------------------------------------------------------------------------------------------
+# emittance objective and adjoint
+# ------------------------------------------------------------------------------------------
+def test_emittance_matches_covariance_determinant():
+    x = B.gaussian(1000, (1e-3, 2e-3, 3e-3), 14)
+    p = B.thermal_momenta(1000, 1e-24, 15) + 1e-21 * x
+    P = O.Params()
+    eps = O.emittance(x, p, P)
+    for d in range(3):
+        C = np.cov(np.stack([x[:, d], p[:, d]]), bias=True)
+        assert eps[d] == pytest.approx(math.sqrt(np.linalg.det(C)) / (P.mass * O.SPEED_OF_LIGHT),
+                                       rel=1e-9)
+
+
+def test_emittance_gradient_fd():
+    x = B.gaussian(50, (1e-3, 2e-3, 3e-3), 16)
+    p = B.thermal_momenta(50, 1e-24, 17)
+    P = O.Params()
+    gx, gp = O.emittance_grad(x, p, P)
+    J = lambda a, b: O.emittance(a, b, P).sum()
+    rng = np.random.default_rng(0)
+    vx = rng.standard_normal(x.shape) * 1e-3
+    vp = rng.standard_normal(p.shape) * 1e-24
+    e = 1e-6
+    fd = (J(x + e * vx, p + e * vp) - J(x - e * vx, p - e * vp)) / (2 * e)
+    assert fd == pytest.approx(np.sum(gx * vx) + np.sum(gp * vp), rel=1e-7)
+
+
+@pytest.mark.parametrize("bc", [(0, 0), (1, 0), (1, 1)])
+def test_force_vjp_directional_fd(bc):
+    pm_bc, pp_bc = bc
+    x = B.lift_to_plane(B.gaussian(64, (1e-3, 1e-3, 1e-3), 18), 0.0, 0.1e-3)
+    P = O.auto_mesh(x, 8, rc_over_h=2.0, pm_bc=pm_bc, pp_bc=pp_bc, z_cathode=0.0)
+    kern = O.green_kernels(P)
+    rng = np.random.default_rng(1)
+    w = rng.standard_normal(x.shape)
+    v = rng.standard_normal(x.shape)
+    g = O.force_vjp(x, w, P, kern)
+    e = 1e-7 * min(P.h)
+    Fp = O.forces(x + e * v, P, kernels=kern).F
+    Fm = O.forces(x - e * v, P, kernels=kern).F
+    fd = np.sum(w * (Fp - Fm)) / (2 * e)
+    assert np.sum(g * v) == pytest.approx(fd, rel=1e-6)
+
+
+def test_backward_matches_fd_of_final_emittance():
+    x0 = B.gaussian(64, (1e-3, 1e-3, 2e-3), 19)
+    p0 = B.thermal_momenta(64, 1e-4 * B.macro_mass() * B.SPEED_OF_LIGHT, 20)
+    P = O.auto_mesh(x0, 8, rc_over_h=2.0)
+    kern = O.green_kernels(P)
+    dt, T = 2e-12, 6
+    f = lambda y: O.forces(y, P, kernels=kern).F
+
+    def J(a, b):
+        xT, pT, _ = O.push(a, b, dt, T, P, force=f)
+        return O.emittance(xT, pT, P).sum()
+
+    xT, pT, _ = O.push(x0, p0, dt, T, P, force=f)
+    gxT, gpT = O.emittance_grad(xT, pT, P)
+    gx0, gp0 = O.backward(x0, p0, dt, T, gxT, gpT, P, kern)
+    rng = np.random.default_rng(2)
+    vx = rng.standard_normal(x0.shape) * 1e-3
+    vp = rng.standard_normal(p0.shape) * np.abs(p0).mean()
+    e = 1e-7
+    fd = (J(x0 + e * vx, p0 + e * vp) - J(x0 - e * vx, p0 - e * vp)) / (2 * e)
+    assert np.sum(gx0 * vx) + np.sum(gp0 * vp) == pytest.approx(fd, rel=1e-5)
