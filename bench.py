@@ -1,0 +1,349 @@
+"""Benchmark of one P3M force evaluation (short range + long range) on a GB300.
+
+Workload (default): uniformly filled cold sphere, N = 16,777,216 particles, R = 1 mm,
+q = 1e-15 C, mesh 256^3 over the bounding box with two spacings of margin, r_c = 2h,
+kappa = 3, TSC, open boundaries; FP32 mixed path (FP64 positions, forces and reductions).
+A "step" is one force evaluation of all particles: bin + sort, short range, deposit,
+Green's-function solve, interpolation. Inputs (x: 403 MB, sorted records: 268 MB) are
+larger than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--rc K]
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank evaluates its own copy of
+the workload (replicas: the method has no exchange step on one bunch), timing is the max
+over ranks, and value is the total number of evaluations per second.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2103_02046_gb300 import bunches as B  # noqa: E402
+
+METRIC = "P3M force evals/s and PP pair-interactions/s at N=16M, FP32 vs FP64 at stated error"
+FLOPS_PER_PAIR = 37.0  # algorithmic FP32 flops per in-cutoff pair (FFMA = 2, incl. 3 MUFU)
+KERNELS_PER_EVAL = 9   # bin, 3 scan passes, scatter, short range, deposit, Green multiply, interp
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rc", type=float, default=2.0, help="r_c in mesh spacings")
+    ap.add_argument("--n", type=int, default=16_777_216)
+    ap.add_argument("--mesh", type=int, default=256)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"uniform cold sphere N={a.n:,} R=1mm q=1e-15C, mesh {a.mesh}^3 auto bbox+2h, "
+            f"r_c={a.rc:g}h kappa=3 TSC open BC")
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        self.dev = ids[device_index] if device_index < len(ids) else str(device_index)
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ------------------------------------------------------------------------------------------
+def cpu_baseline(x: np.ndarray, mesh: int, rc: float, budget_s: float = 25.0):
+    from oracle import oracle as O
+    O.build()
+    N = len(x)
+    P = O.auto_mesh(x, mesh, rc_over_h=rc)
+    kern = O.green_kernels(P)             # once per geometry, not part of an evaluation
+    t0 = time.perf_counter()
+    Q, _ = O.deposit(x, P)
+    t_dep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    phi = O.solve(Q, P, kern)
+    t_solve = time.perf_counter() - t0
+    # short range and interpolation on a sample of particles, scaled to N
+    S = 2048
+    idx = B.subsample(N, S, seed=12345)
+    t0 = time.perf_counter()
+    O.pp(x, P, sample=idx)
+    t_pp_s = time.perf_counter() - t0
+    if t_pp_s < 0.3 * budget_s and S < N:
+        S2 = int(min(N, S * max(1.0, 0.3 * budget_s / max(t_pp_s, 1e-3))))
+        idx = B.subsample(N, S2, seed=12345)
+        t0 = time.perf_counter()
+        O.pp(x, P, sample=idx)
+        t_pp_s = time.perf_counter() - t0
+        S = S2
+    t0 = time.perf_counter()
+    O.interp(x[idx], phi, P)
+    t_int_s = time.perf_counter() - t0
+    t_eval = t_dep + t_solve + (t_pp_s + t_int_s) * (N / S)
+    cores = os.cpu_count()
+    return {
+        "value": 1.0 / t_eval, "unit": "evals/s", "cores": cores, "kind": "oracle",
+        "sample": (f"full-N deposit ({t_dep:.2f}s) and full 512^3-class FFT solve ({t_solve:.2f}s); "
+                   f"short range ({t_pp_s:.2f}s) and interpolation ({t_int_s:.3f}s) on {S} sampled "
+                   f"particles scaled by N/{S}; Green spectra built once outside the timing"),
+        "seconds_per_eval": t_eval,
+    }
+
+
+# ------------------------------------------------------------------------------------------
+def run_ours(a, rank, world, local_rank):
+    import torch
+    from paper_2103_02046_gb300 import p3m as m
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    spec = dict(B.WORKLOADS["sphere16m"])
+    x_host = B.positions(spec, a.n)
+    xg = torch.from_numpy(x_host).to(dev)
+    prm = m.auto_mesh(xg, m.Params(n=(a.mesh,) * 3, rc_over_h=a.rc, precision=m.FP32_MIXED))
+    N = len(x_host)
+    ctx = m.Context(prm, N)
+    f = torch.empty_like(xg)
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(a.warmup):
+        ctx.forces(xg, out=f)
+    ctx.sync()
+    pairs, _ = ctx.pair_count()
+    K = a.steps
+    pp_ms = []
+    stage = np.zeros(6)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(K):
+            ctx.forces(xg, out=f)
+            t = ctx.timings()       # CUDA events recorded around each stage on its own stream
+            pp_ms.append(t[1])
+            stage += np.array(t)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    ctx.sync()
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt)
+    evals_per_s = K * world / (t_max / 1e3)
+    pp_avg_ms = float(np.mean(pp_ms))
+    pp_pairs_per_s = pairs / (pp_avg_ms / 1e3)
+    clocks = clk.summary()
+
+    # FP64 path on the same input, and the FP32-vs-FP64 force difference
+    prm64 = m.Params(**{**prm.__dict__, "precision": m.FP64})
+    ctx64 = m.Context(prm64, N)
+    f64 = torch.empty_like(xg)
+    ctx64.forces(xg, out=f64)
+    ctx64.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    K64 = max(1, a.fp64_steps)
+    e0.record(stream)
+    for _ in range(K64):
+        ctx64.forces(xg, out=f64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_evals = K64 / (e0.elapsed_time(e1) / 1e3)
+    t64 = ctx64.timings()
+    err32 = float(torch.linalg.norm(f - f64) / torch.linalg.norm(f64))
+    ctx64.close()
+    del f64
+
+    # end to end through the public API: pinned host input -> device -> forces -> host
+    xh = torch.from_numpy(x_host).pin_memory()
+    fh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(xg)
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        ctx.forces(xd, out=f)
+        fh.copy_(f, non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        xd.copy_(xh, non_blocking=True)
+        ctx.forces(xd, out=f)
+        fh.copy_(f, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    t_e2e = e2e_ms
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(tt)
+    e2e_value = K * world / (t_e2e / 1e3)
+
+    sm_mhz_max = 2070.0
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz_max * 1e6 / 1e12
+    achieved = FLOPS_PER_PAIR * pairs / (pp_avg_ms / 1e3) / 1e12
+    result = {
+        "metric": METRIC,
+        "value": evals_per_s,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": a.warmup,
+        "ms_per_step": t_max / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(a), "precision": "FP32 mixed (FP64 positions, "
+                   "forces, reductions)", "l2": "inputs larger than L2 (x 403 MB, sorted "
+                   "records 268 MB); no flush", "parallelism": f"replicas x{world}"},
+        "pp_pairs_per_s": pp_pairs_per_s,
+        "pp_pairs_per_eval": pairs,
+        "stage_ms": {k: v / K for k, v in zip(
+            ["bin_sort", "short_range", "deposit", "solve", "interp_combine", "total"], stage)},
+        "fp64": {"evals_per_s": fp64_evals, "stage_ms": dict(zip(
+            ["bin_sort", "short_range", "deposit", "solve", "interp_combine", "total"], t64))},
+        "error": {"fp32_vs_fp64_gpu_rel_l2": err32},
+        "roofline": {"bound": "alu", "kernel": "short range (k_pp<float>)", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": None,
+                     "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                                    f"{sm_mhz_max:.0f} MHz (max SM clock)",
+                     "flops_per_pair": FLOPS_PER_PAIR},
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": N * 24,
+                "d2h_bytes_per_step": N * 24},
+        "gpu_launches": KERNELS_PER_EVAL * K,
+        "clocks": clocks,
+    }
+    ctx.close()
+    return result, x_host
+
+
+def run_reference(a, rank, world):
+    x = B.positions(dict(B.WORKLOADS["sphere16m"]), a.n)
+    res = []
+    for _ in range(max(1, a.steps)):
+        res.append(cpu_baseline(x, a.mesh, a.rc, budget_s=8.0))
+    secs = [r["seconds_per_eval"] for r in res]
+    value = 1.0 / float(np.mean(secs))
+    cb = dict(res[-1])
+    cb["value"] = value
+    cb.pop("seconds_per_eval", None)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "precision": "FP64 oracle on host cores"},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(a, rank, world)), flush=True)
+        return
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    result, x_host = run_ours(a, rank, world, local_rank)
+    if rank == 0 and world == 1 and not a.no_cpu:
+        try:
+            result["cpu_baseline"] = cpu_baseline(x_host, a.mesh, a.rc)
+            result["cpu_baseline"].pop("seconds_per_eval", None)
+        except Exception as e:  # the baseline is a report, not part of the measurement
+            result["cpu_baseline"] = {"value": None, "unit": "evals/s", "kind": "oracle",
+                                      "error": str(e)[:200]}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * p3m.h -- C ABI of the GB300 (sm_103a) P3M space-charge library.
+ *
+ * The library evaluates the particle-particle-particle-mesh (P3M) space-charge force of
+ * Wyssling & Adelmann, "On Boundary Conditions in the sub-mesh interaction of the
+ * Particle-Particle-Particle-Mesh Algorithm" (arXiv 2103.02046), and pushes particles with
+ * the variational leapfrog of the same paper:
+ *
+ *   F_i = F^S_i + F^L_i                                   (eq. (eom_p3m_coord), right-hand side)
+ *   F^S_i = sum_{j != i, |xi_i - xi_j| < r_c} k_e q^2 [erfc(a r)/r + (2a/sqrt(pi)) e^{-a^2 r^2}]
+ *           (xi_i - xi_j)/r^2                             (eq. (summation_short), G^S of eq. (ewald_split))
+ *   F^L_i = -q sum_g phi_g grad_xi W(x_g - xi_i)          (eq. (eom_p3m_coord), first term)
+ *   phi_g = k_e sum_g' Q_g' [G^L(x_g - x_g') - G^L(x_g - S(x_g'))]
+ *                                                         (eq. (phi_L) with eq. (GreenFunc_planar_cathode))
+ *   Q_g   = q sum_i W(x_g - xi_i)                         (eq. (rho_L))
+ *
+ * with G^L(r) = erf(a r)/r, W the TSC (or cloud-in-cell) assignment function, S the mirror
+ * map at the cathode plane z = z_cathode, and k_e = 1/(4 pi eps0).
+ *
+ * Conventions for every entry point:
+ *   * Units are SI. Particle arrays are caller-owned, contiguous, row-major [n][3] float64
+ *     in DEVICE memory (positions x in m, momenta p in kg m/s, forces in N).
+ *   * The context owns all scratch memory. Only p3m_create allocates (mesh, spectra, sort
+ *     buffers, FFT plans, adjoint checkpoints). No other call allocates or frees.
+ *   * Every call is asynchronous and stream-ordered on the context's stream. Host-detectable
+ *     errors (null pointers, bad parameters, n > n_max) are returned at once. Errors found on
+ *     the device (a particle outside the mesh's valid range or below the cathode, a NaN
+ *     position, a bounded wait that ran out) are latched in a device-visible word and
+ *     returned by the next call or by p3m_sync. Nothing traps or aborts; after an error the
+ *     context stays usable.
+ *   * Status codes are p3m_status; p3m_last_error gives a message for the last failure.
+ */
+#ifndef P3M_H
+#define P3M_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  P3M_OK = 0,
+  P3M_EINVAL = 1,   /* bad argument or parameter */
+  P3M_ENOMEM = 2,   /* device allocation failed in p3m_create */
+  P3M_ECUDA = 3,    /* a CUDA runtime call failed */
+  P3M_ECUFFT = 4,   /* a cuFFT call failed */
+  P3M_ERANGE = 5,   /* a particle lies outside the mesh's valid range or below the cathode */
+  P3M_ETIMEOUT = 6, /* a bounded device-side wait ran out */
+  P3M_ESTATE = 7    /* call not valid in the context's current state */
+} p3m_status;
+
+typedef enum { P3M_FP64 = 0, P3M_FP32_MIXED = 1 } p3m_precision;
+
+/* Problem statement (Sec. 2.4: macro-particles, mesh; Sec. 2.2: split; Sec. 3.1: cathode). */
+typedef struct p3m_params {
+  int32_t n[3];          /* mesh nodes per axis, x, y, z (each >= 8) */
+  double lo[3];          /* position of node 0 [m]; node g sits at lo + g*h (Sec. 2.4.2) */
+  double h[3];           /* mesh spacing per axis [m] */
+  double rc_over_h;      /* short-range cutoff r_c = rc_over_h * max_d h_d */
+  double kappa;          /* Ewald parameter a = kappa / r_c (eq. (ewald_split)) unless alpha > 0 */
+  double alpha;          /* explicit Ewald parameter [1/m]; <= 0 selects kappa / r_c */
+  int32_t assign_order;  /* 1 = cloud-in-cell (eq. (interpolation_splines_b0)), 2 = TSC */
+  int32_t pm_bc;         /* 0 = open boundaries, 1 = grounded cathode in the long-range solve */
+  int32_t pp_bc;         /* 0 = short range in free space (the paper's prescription),
+                            1 = cathode images also in the short-range sum */
+  double z_cathode;      /* cathode plane z [m] (eq. (symmetry_planar_cathode) at z = z_cathode) */
+  int32_t influence;     /* 0 = sampled G^L, 1 = principal-alias optimal factor (Sec. 3.1.2) */
+  int32_t precision;     /* p3m_precision */
+  int32_t deterministic; /* reserved, must be 0 */
+  int32_t adj_slots;     /* checkpoint slots for p3m_backward (0 disables the reverse pass) */
+  int32_t adj_segment;   /* steps per checkpoint segment in p3m_backward */
+  double q;              /* macro-particle charge [C] (all particles equal) */
+  double mass;           /* macro-particle mass [kg] */
+} p3m_params;
+
+typedef struct p3m_ctx p3m_ctx; /* opaque; owns all scratch memory */
+
+/* Fills defaults: n = 64^3, TSC, rc_over_h = 2, kappa = 3, open boundaries, FP64,
+ * q = 1e-15 C, mass = (q/e) m_e, adj_slots = adj_segment = 0. Returns P3M_EINVAL on NULL. */
+p3m_status p3m_default_params(p3m_params* p);
+
+/* Mesh over the particles' bounding box (a reading: the paper leaves the mesh extent open):
+ * per axis, with [a_d, b_d] the bounding box of x (device [n][3] float64),
+ * h_d = (b_d - a_d)/(n_d - 5) and lo_d = a_d - 2 h_d, so every particle keeps two nodes of
+ * margin for TSC. Reads inout->n, writes inout->lo and inout->h. Synchronous on `stream`
+ * (a cudaStream_t, may be NULL for the legacy default stream); needs no context and uses a
+ * 64-byte device buffer that it allocates and frees itself. EINVAL if n < 1, any n_d < 8,
+ * or the box is degenerate or not finite. */
+p3m_status p3m_auto_mesh(const double* x, int64_t n, p3m_params* inout, void* stream);
+
+/* Validates params, allocates every buffer for up to n_max particles, creates the FFT
+ * plans and builds the Green's-function spectra (eq. (phi_L), eq. (GreenFunc_planar_cathode)).
+ * `stream` (cudaStream_t, may be NULL) becomes the context's stream. *out is set on success.
+ * EINVAL: bad params or n_max outside [1, 2^31 - 1]; ENOMEM / ECUFFT / ECUDA on failure
+ * (nothing is leaked). */
+p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m_ctx** out);
+
+/* Releases every resource of ctx (waits for its stream first). NULL is accepted. */
+p3m_status p3m_destroy(p3m_ctx* ctx);
+
+/* Sets the stream later calls are ordered on (cudaStream_t, may be NULL). */
+p3m_status p3m_set_stream(p3m_ctx* ctx, void* stream);
+
+/* Charge assignment, eq. (rho_L): node charges Q_g = q sum_i W(x_g - xi_i) for the n
+ * positions x (device [n][3] float64), kept in ctx. Bins and sorts the particles first. */
+p3m_status p3m_deposit(p3m_ctx* ctx, const double* x, int64_t n);
+
+/* Long-range mesh potential from the last deposit, eq. (phi_L): phi = k_e (K_f * Q - K_i * Q_rev)
+ * by doubled-mesh FFT convolution (K_i only with pm_bc = 1). ESTATE if nothing was deposited. */
+p3m_status p3m_solve(p3m_ctx* ctx);
+
+/* Copies a mesh quantity to caller device memory `out` (float64, n_z*n_y*n_x, x fastest):
+ * which = 0 node charges Q [C], which = 1 mesh potential phi [V]. ESTATE if not computed. */
+p3m_status p3m_get_mesh(p3m_ctx* ctx, int32_t which, double* out);
+
+/* One P3M force evaluation, eq. (eom_p3m_coord) right-hand side: f = F^S + F^L for the n
+ * positions x (device [n][3] float64), written to f (device [n][3] float64, caller-owned,
+ * may not alias x). energy (nullable, device float64[2]) receives the short-range energy
+ * (1/2) q sum_i phi^S_i and the long-range mesh energy (1/2) sum_g Q_g phi_g [J].
+ * parts selects the terms: 1 = short range only, 2 = long range only, 3 = both.
+ * Invalid particles get f = 0 and latch ERANGE. */
+p3m_status p3m_forces_ex(p3m_ctx* ctx, const double* x, int64_t n, double* f, double* energy,
+                         int32_t parts);
+p3m_status p3m_forces(p3m_ctx* ctx, const double* x, int64_t n, double* f, double* energy);
+
+/* In-cutoff ordered pair count (and short-range image pairs) of the last force evaluation
+ * that included the short range. Synchronises the context's stream. */
+p3m_status p3m_pair_count(p3m_ctx* ctx, int64_t* pairs, int64_t* image_pairs);
+
+/* Leapfrog, eq. (leapfrog) with the Stoermer form of eq. (eom_p3m_coord), as kick-drift-kick
+ * (a reading: the paper leaves the start-up open):
+ *   p += dt/2 F(x);  x += dt p / mass;  p += dt/2 F(x)   per step, nsteps >= 0 steps.
+ * x, p: device [n][3] float64, updated in place. f: device [n][3] float64; on entry F(x0)
+ * if f_valid != 0 (reused), else it is computed; on exit F(x_end). */
+p3m_status p3m_push(p3m_ctx* ctx, double* x, double* p, int64_t n, double dt, int32_t nsteps,
+                    double* f, int32_t f_valid);
+
+/* Vector-Jacobian product of the force map: out = (dF/dx)^T w for positions x and cotangent
+ * w (all device [n][3] float64). The long-range part uses the symmetry of the solve
+ * (both Green's functions are symmetric in their arguments), so it costs one extra solve. */
+p3m_status p3m_force_vjp(p3m_ctx* ctx, const double* x, int64_t n, const double* w, double* out);
+
+/* Reverse pass of p3m_push: given dJ/dx_T (gx_T) and dJ/dp_T (gp_T) for the state after
+ * nsteps steps from (x0, p0), writes dJ/dx_0 (gx0) and dJ/dp_0 (gp0). States are
+ * re-computed from checkpoints taken every adj_segment steps (needs
+ * adj_slots * adj_segment >= nsteps). All arrays device [n][3] float64. ESTATE if the
+ * context was created with adj_slots = 0; EINVAL if nsteps exceeds the checkpoint budget. */
+p3m_status p3m_backward(p3m_ctx* ctx, const double* x0, const double* p0, int64_t n, double dt,
+                        int32_t nsteps, const double* gx_T, const double* gp_T, double* gx0,
+                        double* gp0);
+
+/* Normalised rms emittance eps_u = sqrt(<du^2><dp_u^2> - <du dp_u>^2)/(mass c), u = x, y, z
+ * (a reading: the paper names emittance but does not define it). eps3: device float64[3].
+ * gx, gp (nullable, device [n][3]): gradient of eps_x + eps_y + eps_z. */
+p3m_status p3m_emittance(p3m_ctx* ctx, const double* x, const double* p, int64_t n, double* eps3,
+                         double* gx, double* gp);
+
+/* Waits for the context's stream and returns any latched device error (then clears it). */
+p3m_status p3m_sync(p3m_ctx* ctx);
+
+/* Stage times of the last force evaluation in ms (CUDA events; synchronises):
+ * [0] bin+sort, [1] short range, [2] deposit, [3] solve, [4] interpolation+combine, [5] total. */
+p3m_status p3m_get_timings(p3m_ctx* ctx, double* ms, int32_t cap, int32_t* count);
+
+/* Message for the last failure on ctx (never NULL; valid until the next call on ctx). */
+const char* p3m_last_error(const p3m_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* P3M_H */

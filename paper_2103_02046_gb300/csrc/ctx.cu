@@ -1,0 +1,664 @@
+// C ABI of the GB300 P3M library: parameter checks, the context (all scratch memory, FFT plans,
+// streams) and the orchestration of one force evaluation, the leapfrog push and its reverse pass.
+//
+// One force evaluation (eq. (eom_p3m_coord) right-hand side), all stream-ordered:
+//   bin + counting sort --(fork)--> short range on a side stream
+//                       \--> zero mesh, deposit, R2C, Green multiply, C2R (long range)
+//   join --> interpolation + combination, written in the caller's particle order.
+// The short range is ALU-bound and the FFTs are HBM-bound, so the two streams overlap.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "p3m_internal.cuh"
+
+using namespace p3m;
+
+namespace {
+
+constexpr double kEps0 = 8.8541878128e-12;  // F/m, CODATA 2018
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kElectronMass = 9.1093837015e-31;
+constexpr double kElementaryCharge = 1.602176634e-19;
+constexpr double kSpeedOfLight = 299792458.0;
+
+p3m_status fail(p3m_ctx* c, p3m_status s, const char* msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+p3m_status cuda_fail(p3m_ctx* c, cudaError_t e, const char* where) {
+  if (c) {
+    c->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  }
+  return P3M_ECUDA;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+p3m_status validate(const p3m_params* p, std::string* why) {
+  for (int d = 0; d < 3; ++d) {
+    if (p->n[d] < 8 || p->n[d] > 4096) { *why = "mesh n must be in [8, 4096] per axis"; return P3M_EINVAL; }
+    if (!finite_pos(p->h[d])) { *why = "mesh spacing h must be finite and > 0"; return P3M_EINVAL; }
+    if (!std::isfinite(p->lo[d])) { *why = "mesh origin lo must be finite"; return P3M_EINVAL; }
+  }
+  if (!finite_pos(p->rc_over_h)) { *why = "rc_over_h must be > 0"; return P3M_EINVAL; }
+  if (!(p->alpha > 0.0) && !finite_pos(p->kappa)) { *why = "kappa must be > 0 (or alpha > 0)"; return P3M_EINVAL; }
+  if (p->assign_order != 1 && p->assign_order != 2) { *why = "assign_order must be 1 or 2"; return P3M_EINVAL; }
+  if ((p->pm_bc != 0 && p->pm_bc != 1) || (p->pp_bc != 0 && p->pp_bc != 1)) { *why = "pm_bc/pp_bc must be 0 or 1"; return P3M_EINVAL; }
+  if (!std::isfinite(p->z_cathode)) { *why = "z_cathode must be finite"; return P3M_EINVAL; }
+  if (p->influence != 0 && p->influence != 1) { *why = "influence must be 0 or 1"; return P3M_EINVAL; }
+  if (p->precision != P3M_FP64 && p->precision != P3M_FP32_MIXED) { *why = "precision must be 0 or 1"; return P3M_EINVAL; }
+  if (p->deterministic != 0) { *why = "deterministic must be 0"; return P3M_EINVAL; }
+  if (p->adj_slots < 0 || p->adj_segment < 0 || (p->adj_slots > 0 && p->adj_segment < 1)) { *why = "adj_slots/adj_segment invalid"; return P3M_EINVAL; }
+  if (!std::isfinite(p->q) || p->q == 0.0) { *why = "q must be finite and nonzero"; return P3M_EINVAL; }
+  if (!finite_pos(p->mass)) { *why = "mass must be > 0"; return P3M_EINVAL; }
+  return P3M_OK;
+}
+
+Geom make_geom(const p3m_params* p) {
+  Geom g{};
+  double hmax = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = p->n[d];
+    g.M[d] = 2 * p->n[d];
+    g.lo[d] = p->lo[d];
+    g.h[d] = p->h[d];
+    hmax = std::max(hmax, p->h[d]);
+  }
+  g.rc = p->rc_over_h * hmax;
+  g.alpha = p->alpha > 0.0 ? p->alpha : p->kappa / g.rc;
+  g.kappa_eff = g.alpha * g.rc;
+  for (int d = 0; d < 3; ++d) {
+    int kc = static_cast<int>(std::ceil(g.rc / g.h[d]));
+    if (kc < 1) kc = 1;
+    while (kc * g.h[d] < g.rc) ++kc;  // cell edge must reach the cutoff
+    g.kc[d] = kc;
+    g.nc[d] = (g.n[d] - 2) / kc + 1;
+    g.nb[d] = (g.nc[d] + 3) / 4;
+    g.a[d] = g.h[d] / g.rc;
+  }
+  g.order = p->assign_order;
+  g.pm_bc = p->pm_bc;
+  g.pp_bc = p->pp_bc;
+  g.zc = p->z_cathode;
+  g.s_cath = (p->z_cathode - p->lo[2]) / p->h[2];
+  g.q = p->q;
+  g.mass = p->mass;
+  g.ke = 1.0 / (4.0 * kPi * kEps0);
+  return g;
+}
+
+template <typename T>
+cudaError_t alloc(T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(ptr), sizeof(T) * count);
+}
+
+void free_all(p3m_ctx* c) {
+  void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->skey, c->rec, c->fpp,
+                  c->acc, c->qpad, c->qhat, c->khat_f, c->khat_i, c->fhat, c->freal,
+                  c->phihat, c->phireal, c->dfac, c->energy_acc, c->pair_acc, c->err_dev,
+                  c->ckpt, c->seg, c->lam_x, c->lam_p, c->xw, c->pw, c->tmp3, c->tmp3b,
+                  c->f_work, c->red};
+  for (void* b : bufs) cudaFree(b);
+  if (c->err_host) cudaFreeHost(c->err_host);
+  if (c->have_r2c) cufftDestroy(c->plan_r2c);
+  if (c->have_c2r) cufftDestroy(c->plan_c2r);
+  if (c->have_c2r3) cufftDestroy(c->plan_c2r3);
+  if (c->s_pp) cudaStreamDestroy(c->s_pp);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (auto& e : c->tev)
+    if (e) cudaEventDestroy(e);
+}
+
+// Returns a device error latched by earlier calls (and clears it), from the pinned mirror that
+// every call refreshes asynchronously at its end.
+p3m_status take_deferred(p3m_ctx* c) {
+  const int e = *reinterpret_cast<volatile int*>(c->err_host);
+  if (!e) return P3M_OK;
+  *c->err_host = 0;
+  cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+  if (e & kErrTimeout) return fail(c, P3M_ETIMEOUT, "a bounded device wait ran out");
+  if (e & kErrNaN) return fail(c, P3M_EINVAL, "a particle position is NaN");
+  return fail(c, P3M_ERANGE, "a particle lies outside the mesh's valid range or below the cathode");
+}
+
+p3m_status finish(p3m_ctx* c) {
+  cudaMemcpyAsync(c->err_host, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  return P3M_OK;
+}
+
+p3m_status check_n(p3m_ctx* c, int64_t n) {
+  if (n < 0 || n > c->n_max) return fail(c, P3M_EINVAL, "n must be in [0, n_max]");
+  return P3M_OK;
+}
+
+void sort_particles(p3m_ctx* c, const double* x, int64_t n, double* f_zero) {
+  launch_bin(c, x, n, f_zero);
+  launch_scan(c);
+  launch_scatter(c, x, n);
+  c->last_n = n;
+}
+
+p3m_status fft_r2c(p3m_ctx* c) {
+  cufftResult r;
+  if (c->fp32)
+    r = cufftExecR2C(c->plan_r2c, static_cast<cufftReal*>(c->qpad),
+                     static_cast<cufftComplex*>(c->qhat));
+  else
+    r = cufftExecD2Z(c->plan_r2c, static_cast<cufftDoubleReal*>(c->qpad),
+                     static_cast<cufftDoubleComplex*>(c->qhat));
+  return r == CUFFT_SUCCESS ? P3M_OK : fail(c, P3M_ECUFFT, "cuFFT forward transform failed");
+}
+
+// Solve on the current qpad: FP64 -> potential; FP32 -> difference fields (and the potential
+// when want_phi).
+p3m_status mesh_solve(p3m_ctx* c, bool want_phi, bool want_diff, bool want_energy) {
+  p3m_status s = fft_r2c(c);
+  if (s != P3M_OK) return s;
+  if (!c->fp32) want_phi = true, want_diff = false;
+  launch_green_multiply(c, want_phi, want_diff, want_energy);
+  cufftResult r = CUFFT_SUCCESS;
+  if (want_phi) {
+    if (c->fp32)
+      r = cufftExecC2R(c->plan_c2r, static_cast<cufftComplex*>(c->phihat),
+                       static_cast<cufftReal*>(c->phireal));
+    else
+      r = cufftExecZ2D(c->plan_c2r, static_cast<cufftDoubleComplex*>(c->phihat),
+                       static_cast<cufftDoubleReal*>(c->phireal));
+    if (r != CUFFT_SUCCESS) return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
+    c->phi_valid = true;
+  }
+  if (want_diff) {
+    r = cufftExecC2R(c->plan_c2r3, static_cast<cufftComplex*>(c->fhat),
+                     static_cast<cufftReal*>(c->freal));
+    if (r != CUFFT_SUCCESS) return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
+  }
+  return P3M_OK;
+}
+
+p3m_status forces_impl(p3m_ctx* c, const double* x, int64_t n, double* f, double* energy,
+                       int parts) {
+  cudaStream_t st = c->stream;
+  cudaMemsetAsync(c->energy_acc, 0, 2 * sizeof(double), st);
+  cudaMemsetAsync(c->pair_acc, 0, 2 * sizeof(unsigned long long), st);
+  cudaEventRecord(c->tev[0], st);
+  sort_particles(c, x, n, f);
+  cudaEventRecord(c->tev[1], st);
+  if (parts & 1) {
+    cudaEventRecord(c->ev_fork, st);
+    cudaStreamWaitEvent(c->s_pp, c->ev_fork, 0);
+    cudaEventRecord(c->tev[6], c->s_pp);
+    launch_pp(c, n, c->s_pp);
+    cudaEventRecord(c->tev[7], c->s_pp);
+    cudaEventRecord(c->ev_join, c->s_pp);
+  }
+  cudaEventRecord(c->tev[2], st);
+  if (parts & 2) {
+    launch_zero_block(c);
+    launch_deposit(c, n);
+    c->deposited = true;
+    cudaEventRecord(c->tev[3], st);
+    p3m_status s = mesh_solve(c, false, true, true);
+    if (s != P3M_OK) return s;
+  } else {
+    cudaEventRecord(c->tev[3], st);
+  }
+  cudaEventRecord(c->tev[4], st);
+  if (parts & 1) cudaStreamWaitEvent(st, c->ev_join, 0);
+  launch_interp(c, n, f, parts);
+  cudaEventRecord(c->tev[5], st);
+  if (energy) launch_energy_out(c, energy);
+  c->last_parts = parts;
+  return P3M_OK;
+}
+
+// out = (dF/dx)^T w
+p3m_status vjp_impl(p3m_ctx* c, const double* x, int64_t n, const double* w, double* out) {
+  sort_particles(c, x, n, out);
+  launch_pp_vjp(c, n, w, c->stream);  // acc = short-range part
+  launch_zero_block(c);
+  launch_deposit(c, n);
+  p3m_status s = mesh_solve(c, false, true, false);
+  if (s != P3M_OK) return s;
+  launch_vjp_gather(c, n, 0, w, out);
+  launch_zero_block(c);
+  launch_dipole_deposit(c, n, w);
+  s = mesh_solve(c, false, true, false);
+  if (s != P3M_OK) return s;
+  launch_vjp_gather(c, n, 1, w, out);
+  c->deposited = false;  // the mesh now holds the dipole deposit
+  c->phi_valid = false;
+  return P3M_OK;
+}
+
+p3m_status push_impl(p3m_ctx* c, double* x, double* p, int64_t n, double dt, int32_t nsteps,
+                     double* f, bool f_valid) {
+  if (!f_valid) {
+    p3m_status s = forces_impl(c, x, n, f, nullptr, 3);
+    if (s != P3M_OK) return s;
+  }
+  for (int32_t k = 0; k < nsteps; ++k) {
+    launch_kick_drift(x, p, f, n, 0.5 * dt, dt / c->g.mass, c->stream);
+    p3m_status s = forces_impl(c, x, n, f, nullptr, 3);
+    if (s != P3M_OK) return s;
+    launch_kick_drift(x, p, f, n, 0.5 * dt, 0.0, c->stream);
+  }
+  return P3M_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+p3m_status p3m_default_params(p3m_params* p) {
+  if (!p) return P3M_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  for (int d = 0; d < 3; ++d) {
+    p->n[d] = 64;
+    p->lo[d] = 0.0;
+    p->h[d] = 1e-5;
+  }
+  p->rc_over_h = 2.0;
+  p->kappa = 3.0;
+  p->alpha = 0.0;
+  p->assign_order = 2;
+  p->pm_bc = 0;
+  p->pp_bc = 0;
+  p->z_cathode = 0.0;
+  p->influence = 0;
+  p->precision = P3M_FP64;
+  p->deterministic = 0;
+  p->adj_slots = 0;
+  p->adj_segment = 0;
+  p->q = 1e-15;
+  p->mass = p->q / kElementaryCharge * kElectronMass;
+  return P3M_OK;
+}
+
+p3m_status p3m_auto_mesh(const double* x, int64_t n, p3m_params* inout, void* stream) {
+  if (!x || !inout || n < 1) return P3M_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (inout->n[d] < 8) return P3M_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* red = nullptr;
+  if (cudaMalloc(&red, 8 * sizeof(double)) != cudaSuccess) return P3M_ENOMEM;
+  launch_bbox(x, n, red, st);
+  unsigned long long keys[6];
+  int bad = 0;
+  cudaError_t e = cudaMemcpyAsync(keys, red, sizeof(keys), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, red + 6, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(red);
+  if (e != cudaSuccess) return P3M_ECUDA;
+  if (bad) return P3M_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    auto unkey = [](unsigned long long k) {
+      const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+      double v;
+      std::memcpy(&v, &b, sizeof(v));
+      return v;
+    };
+    const double a = unkey(keys[d]), b = unkey(keys[3 + d]);
+    const double h = (b - a) / (inout->n[d] - 5);
+    if (!(h > 0.0) || !std::isfinite(h)) return P3M_EINVAL;
+    inout->h[d] = h;
+    inout->lo[d] = a - 2.0 * h;
+  }
+  return P3M_OK;
+}
+
+p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m_ctx** out) {
+  if (!params || !out) return P3M_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (validate(params, &why) != P3M_OK) {
+    std::fprintf(stderr, "p3m_create: %s\n", why.c_str());
+    return P3M_EINVAL;
+  }
+  if (n_max < 1 || n_max > 2147483647LL) return P3M_EINVAL;
+  auto* c = new p3m_ctx();
+  c->prm = *params;
+  c->g = make_geom(params);
+  c->n_max = n_max;
+  c->fp32 = params->precision == P3M_FP32_MIXED;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&c->device);
+  const Geom& g = c->g;
+  c->nkeys = static_cast<uint64_t>(g.nb[0]) * g.nb[1] * g.nb[2] * kBrickCells;
+  if (c->nkeys >= 0xFFFFFFF0ull) {
+    delete c;
+    return P3M_EINVAL;
+  }
+  c->n_real = static_cast<size_t>(g.M[0]) * g.M[1] * g.M[2];
+  c->n_cplx = static_cast<size_t>(g.M[0] / 2 + 1) * g.M[1] * g.M[2];
+  const size_t es = c->fp32 ? 4 : 8;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  const uint64_t tiles = (c->nkeys + 4095) / 4096;
+  A(alloc(&c->counts, c->nkeys));
+  A(alloc(&c->starts, c->nkeys + 1));
+  A(alloc(&c->bsum, tiles));
+  A(alloc(&c->keys, n_max));
+  A(alloc(&c->ranks, n_max));
+  A(alloc(&c->skey, n_max));
+  A(cudaMalloc(&c->rec, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
+  A(cudaMalloc(&c->fpp, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
+  A(alloc(&c->acc, 3 * n_max));
+  A(cudaMalloc(&c->qpad, es * c->n_real));
+  A(cudaMalloc(&c->qhat, 2 * es * c->n_cplx));
+  A(cudaMalloc(&c->khat_f, es * c->n_cplx));
+  if (g.pm_bc) A(cudaMalloc(&c->khat_i, 2 * es * c->n_cplx));
+  A(cudaMalloc(&c->phihat, 2 * es * c->n_cplx));
+  A(cudaMalloc(&c->phireal, es * c->n_real));
+  if (c->fp32) {
+    A(cudaMalloc(&c->fhat, 3 * 2 * es * c->n_cplx));
+    A(cudaMalloc(&c->freal, 3 * es * c->n_real));
+    A(alloc(&c->dfac, static_cast<size_t>(g.M[0] / 2 + 1 + g.M[1] + g.M[2])));
+  }
+  A(alloc(&c->energy_acc, 2));
+  A(alloc(&c->pair_acc, 2));
+  A(alloc(&c->err_dev, 1));
+  A(alloc(&c->red, 32));
+  A(alloc(&c->f_work, 3 * n_max));
+  if (params->adj_slots > 0) {
+    A(alloc(&c->ckpt, static_cast<size_t>(params->adj_slots) * 6 * n_max));
+    A(alloc(&c->seg, static_cast<size_t>(params->adj_segment + 1) * 3 * n_max));
+    A(alloc(&c->lam_x, 3 * n_max));
+    A(alloc(&c->lam_p, 3 * n_max));
+    A(alloc(&c->xw, 3 * n_max));
+    A(alloc(&c->pw, 3 * n_max));
+    A(alloc(&c->tmp3, 3 * n_max));
+    A(alloc(&c->tmp3b, 3 * n_max));
+  }
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&c->err_host), sizeof(int), 0);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_pp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  for (auto& ev : c->tev)
+    if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? P3M_ENOMEM : P3M_ECUDA;
+  }
+  *c->err_host = 0;
+  cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+  cudaMemsetAsync(c->qpad, 0, es * c->n_real, c->stream);
+  if (c->fp32) {
+    std::vector<float2> fac(g.M[0] / 2 + 1 + g.M[1] + g.M[2]);
+    size_t o = 0;
+    auto put = [&](int M, int count) {
+      for (int k = 0; k < count; ++k) {
+        const double s = std::sin(kPi * k / M), co = std::cos(kPi * k / M);
+        fac[o++] = make_float2(static_cast<float>(-2.0 * s * s), static_cast<float>(2.0 * s * co));
+      }
+    };
+    put(g.M[0], g.M[0] / 2 + 1);
+    put(g.M[1], g.M[1]);
+    put(g.M[2], g.M[2]);
+    cudaMemcpyAsync(c->dfac, fac.data(), sizeof(float2) * fac.size(), cudaMemcpyHostToDevice,
+                    c->stream);
+  }
+  // FFT plans
+  cufftResult r = cufftPlan3d(&c->plan_r2c, g.M[2], g.M[1], g.M[0], c->fp32 ? CUFFT_R2C : CUFFT_D2Z);
+  c->have_r2c = r == CUFFT_SUCCESS;
+  if (r == CUFFT_SUCCESS) {
+    r = cufftPlan3d(&c->plan_c2r, g.M[2], g.M[1], g.M[0], c->fp32 ? CUFFT_C2R : CUFFT_Z2D);
+    c->have_c2r = r == CUFFT_SUCCESS;
+  }
+  if (r == CUFFT_SUCCESS && c->fp32) {
+    int dims[3] = {g.M[2], g.M[1], g.M[0]};
+    r = cufftPlanMany(&c->plan_c2r3, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 3);
+    c->have_c2r3 = r == CUFFT_SUCCESS;
+  }
+  if (r != CUFFT_SUCCESS) {
+    free_all(c);
+    delete c;
+    return r == CUFFT_ALLOC_FAILED ? P3M_ENOMEM : P3M_ECUFFT;
+  }
+  cufftSetStream(c->plan_r2c, c->stream);
+  cufftSetStream(c->plan_c2r, c->stream);
+  if (c->have_c2r3) cufftSetStream(c->plan_c2r3, c->stream);
+  e = build_green(c);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? P3M_ENOMEM : P3M_ECUFFT;
+  }
+  *out = c;
+  return P3M_OK;
+}
+
+p3m_status p3m_destroy(p3m_ctx* c) {
+  if (!c) return P3M_OK;
+  cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->s_pp);
+  free_all(c);
+  delete c;
+  return P3M_OK;
+}
+
+p3m_status p3m_set_stream(p3m_ctx* c, void* stream) {
+  if (!c) return P3M_EINVAL;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cufftSetStream(c->plan_r2c, c->stream);
+  cufftSetStream(c->plan_c2r, c->stream);
+  if (c->have_c2r3) cufftSetStream(c->plan_c2r3, c->stream);
+  return P3M_OK;
+}
+
+p3m_status p3m_deposit(p3m_ctx* c, const double* x, int64_t n) {
+  if (!c) return P3M_EINVAL;
+  if (!x && n > 0) return fail(c, P3M_EINVAL, "x is NULL");
+  p3m_status s = take_deferred(c);
+  if (s != P3M_OK) return s;
+  if ((s = check_n(c, n)) != P3M_OK) return s;
+  sort_particles(c, x, n, nullptr);
+  launch_zero_block(c);
+  launch_deposit(c, n);
+  c->deposited = true;
+  c->phi_valid = false;
+  return finish(c);
+}
+
+p3m_status p3m_solve(p3m_ctx* c) {
+  if (!c) return P3M_EINVAL;
+  p3m_status s = take_deferred(c);
+  if (s != P3M_OK) return s;
+  if (!c->deposited) return fail(c, P3M_ESTATE, "p3m_solve needs a deposit first");
+  cudaMemsetAsync(c->energy_acc, 0, 2 * sizeof(double), c->stream);
+  s = mesh_solve(c, true, c->fp32, true);
+  if (s != P3M_OK) return s;
+  return finish(c);
+}
+
+p3m_status p3m_get_mesh(p3m_ctx* c, int32_t which, double* out) {
+  if (!c || !out || (which != 0 && which != 1)) return P3M_EINVAL;
+  if (which == 0 && !c->deposited) return fail(c, P3M_ESTATE, "no deposit");
+  if (which == 1 && !c->phi_valid) return fail(c, P3M_ESTATE, "no potential (call p3m_solve)");
+  launch_get_mesh(c, which, out);
+  return finish(c);
+}
+
+p3m_status p3m_forces_ex(p3m_ctx* c, const double* x, int64_t n, double* f, double* energy,
+                         int32_t parts) {
+  if (!c) return P3M_EINVAL;
+  if ((!x || !f) && n > 0) return fail(c, P3M_EINVAL, "x or f is NULL");
+  if (parts < 1 || parts > 3) return fail(c, P3M_EINVAL, "parts must be 1, 2 or 3");
+  if (x == f && n > 0) return fail(c, P3M_EINVAL, "f may not alias x");
+  p3m_status s = take_deferred(c);
+  if (s != P3M_OK) return s;
+  if ((s = check_n(c, n)) != P3M_OK) return s;
+  s = forces_impl(c, x, n, f, energy, parts);
+  if (s != P3M_OK) return s;
+  if (parts & 2) c->phi_valid = !c->fp32;
+  return finish(c);
+}
+
+p3m_status p3m_forces(p3m_ctx* c, const double* x, int64_t n, double* f, double* energy) {
+  return p3m_forces_ex(c, x, n, f, energy, 3);
+}
+
+p3m_status p3m_pair_count(p3m_ctx* c, int64_t* pairs, int64_t* image_pairs) {
+  if (!c || !pairs) return P3M_EINVAL;
+  unsigned long long v[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(v, c->pair_acc, sizeof(v), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "p3m_pair_count");
+  *pairs = static_cast<int64_t>(v[0]);
+  if (image_pairs) *image_pairs = static_cast<int64_t>(v[1]);
+  return P3M_OK;
+}
+
+p3m_status p3m_push(p3m_ctx* c, double* x, double* p, int64_t n, double dt, int32_t nsteps,
+                    double* f, int32_t f_valid) {
+  if (!c) return P3M_EINVAL;
+  if ((!x || !p || !f) && n > 0) return fail(c, P3M_EINVAL, "x, p or f is NULL");
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(c, P3M_EINVAL, "bad dt or nsteps");
+  p3m_status s = take_deferred(c);
+  if (s != P3M_OK) return s;
+  if ((s = check_n(c, n)) != P3M_OK) return s;
+  s = push_impl(c, x, p, n, dt, nsteps, f, f_valid != 0);
+  if (s != P3M_OK) return s;
+  return finish(c);
+}
+
+p3m_status p3m_force_vjp(p3m_ctx* c, const double* x, int64_t n, const double* w, double* out) {
+  if (!c) return P3M_EINVAL;
+  if ((!x || !w || !out) && n > 0) return fail(c, P3M_EINVAL, "NULL argument");
+  p3m_status s = take_deferred(c);
+  if (s != P3M_OK) return s;
+  if ((s = check_n(c, n)) != P3M_OK) return s;
+  s = vjp_impl(c, x, n, w, out);
+  if (s != P3M_OK) return s;
+  return finish(c);
+}
+
+p3m_status p3m_backward(p3m_ctx* c, const double* x0, const double* p0, int64_t n, double dt,
+                        int32_t nsteps, const double* gx_T, const double* gp_T, double* gx0,
+                        double* gp0) {
+  if (!c) return P3M_EINVAL;
+  if ((!x0 || !p0 || !gx_T || !gp_T || !gx0 || !gp0) && n > 0)
+    return fail(c, P3M_EINVAL, "NULL argument");
+  if (c->prm.adj_slots <= 0) return fail(c, P3M_ESTATE, "context created with adj_slots = 0");
+  const int C = c->prm.adj_segment;
+  if (nsteps < 1 || static_cast<int64_t>(c->prm.adj_slots) * C < nsteps || !std::isfinite(dt))
+    return fail(c, P3M_EINVAL, "nsteps must be in [1, adj_slots * adj_segment]");
+  p3m_status s = take_deferred(c);
+  if (s != P3M_OK) return s;
+  if ((s = check_n(c, n)) != P3M_OK) return s;
+  cudaStream_t st = c->stream;
+  const size_t n3 = 3 * static_cast<size_t>(n);
+  const size_t bytes = n3 * sizeof(double);
+  const size_t slot = 6 * static_cast<size_t>(c->n_max);
+  const int K = (nsteps + C - 1) / C;
+  // forward sweep: checkpoints of (x, p) at the start of every segment
+  cudaMemcpyAsync(c->xw, x0, bytes, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->pw, p0, bytes, cudaMemcpyDeviceToDevice, st);
+  bool f_valid = false;
+  for (int k = 0; k < K; ++k) {
+    cudaMemcpyAsync(c->ckpt + k * slot, c->xw, bytes, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(c->ckpt + k * slot + 3 * c->n_max, c->pw, bytes, cudaMemcpyDeviceToDevice, st);
+    const int steps = std::min(C, nsteps - k * C);
+    if (k < K - 1) {
+      if ((s = push_impl(c, c->xw, c->pw, n, dt, steps, c->f_work, f_valid)) != P3M_OK) return s;
+      f_valid = true;
+    }
+  }
+  // reverse sweep
+  cudaMemcpyAsync(c->lam_x, gx_T, bytes, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->lam_p, gp_T, bytes, cudaMemcpyDeviceToDevice, st);
+  bool first = true;
+  for (int k = K - 1; k >= 0; --k) {
+    const int steps = std::min(C, nsteps - k * C);
+    cudaMemcpyAsync(c->xw, c->ckpt + k * slot, bytes, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(c->pw, c->ckpt + k * slot + 3 * c->n_max, bytes, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(c->seg, c->xw, bytes, cudaMemcpyDeviceToDevice, st);
+    bool fv = false;
+    for (int t = 1; t <= steps; ++t) {
+      if ((s = push_impl(c, c->xw, c->pw, n, dt, 1, c->f_work, fv)) != P3M_OK) return s;
+      fv = true;
+      cudaMemcpyAsync(c->seg + t * 3 * c->n_max, c->xw, bytes, cudaMemcpyDeviceToDevice, st);
+    }
+    for (int t = steps - 1; t >= 0; --t) {
+      const int64_t gstep = static_cast<int64_t>(k) * C + t;
+      if (first) {  // end-of-step kick of the last step: lam_x += J(x_T)^T (dt/2 lam_p)
+        launch_scale(c->tmp3, c->lam_p, n3, 0.5 * dt, st);
+        if ((s = vjp_impl(c, c->seg + (t + 1) * 3 * c->n_max, n, c->tmp3, c->tmp3b)) != P3M_OK)
+          return s;
+        launch_axpy(c->lam_x, c->tmp3b, n3, 1.0, st);
+        first = false;
+      }
+      launch_axpy(c->lam_p, c->lam_x, n3, dt / c->g.mass, st);  // drift
+      // start-of-step kick of this step merged with the end-of-step kick of the previous one
+      const double coef = gstep > 0 ? dt : 0.5 * dt;
+      launch_scale(c->tmp3, c->lam_p, n3, coef, st);
+      if ((s = vjp_impl(c, c->seg + t * 3 * c->n_max, n, c->tmp3, c->tmp3b)) != P3M_OK) return s;
+      launch_axpy(c->lam_x, c->tmp3b, n3, 1.0, st);
+    }
+  }
+  cudaMemcpyAsync(gx0, c->lam_x, bytes, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(gp0, c->lam_p, bytes, cudaMemcpyDeviceToDevice, st);
+  return finish(c);
+}
+
+p3m_status p3m_emittance(p3m_ctx* c, const double* x, const double* p, int64_t n, double* eps3,
+                         double* gx, double* gp) {
+  if (!c) return P3M_EINVAL;
+  if (!x || !p || !eps3 || n < 2) return fail(c, P3M_EINVAL, "bad argument");
+  p3m_status s = take_deferred(c);
+  if (s != P3M_OK) return s;
+  launch_emittance(x, p, n, c->g.mass * kSpeedOfLight, eps3, gx, gp, c->red, c->stream);
+  return finish(c);
+}
+
+p3m_status p3m_sync(p3m_ctx* c) {
+  if (!c) return P3M_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_pp);
+  if (e != cudaSuccess) return cuda_fail(c, e, "p3m_sync");
+  int v = 0;
+  e = cudaMemcpy(&v, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "p3m_sync");
+  *c->err_host = v;
+  return take_deferred(c);
+}
+
+p3m_status p3m_get_timings(p3m_ctx* c, double* ms, int32_t cap, int32_t* count) {
+  if (!c || !ms || cap < 0) return P3M_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "p3m_get_timings");
+  float t[6] = {0, 0, 0, 0, 0, 0};
+  cudaEventElapsedTime(&t[0], c->tev[0], c->tev[1]);
+  if (c->last_parts & 1) cudaEventElapsedTime(&t[1], c->tev[6], c->tev[7]);
+  if (c->last_parts & 2) {
+    cudaEventElapsedTime(&t[2], c->tev[2], c->tev[3]);
+    cudaEventElapsedTime(&t[3], c->tev[3], c->tev[4]);
+  }
+  cudaEventElapsedTime(&t[4], c->tev[4], c->tev[5]);
+  cudaEventElapsedTime(&t[5], c->tev[0], c->tev[5]);
+  cudaGetLastError();
+  const int k = std::min<int32_t>(cap, 6);
+  for (int i = 0; i < k; ++i) ms[i] = t[i];
+  if (count) *count = 6;
+  return P3M_OK;
+}
+
+const char* p3m_last_error(const p3m_ctx* c) {
+  if (!c) return "null context";
+  return c->last_error.c_str();
+}
+
+}  // extern "C"

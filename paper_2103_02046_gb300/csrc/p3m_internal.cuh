@@ -1,0 +1,202 @@
+// Internal declarations of the GB300 P3M library (not part of the C ABI).
+//
+// Data layout in HBM (one context, up to n_max particles, mesh n = (nx, ny, nz)):
+//   * particles are binned into cells of kc_d mesh spacings per axis (kc_d h_d >= r_c), cells
+//     grouped into 4x4x4 bricks; the cell key is brick-major so that a brick's particles are
+//     contiguous after the counting sort.
+//   * sorted records: FP32 float4 {u_x, u_y, u_z, bits(original index)} or FP64
+//     {u_x, u_y, u_z, original index}, where u_d is the position in mesh units relative to the
+//     cell's first node (u_d in [0, kc_d)). Cell-local offsets keep FP32 positions accurate
+//     to ~1e-7 of a mesh spacing wherever the bunch sits.
+//   * mesh arrays use the doubled (2n)^3 layout of the FFT convolution, x fastest:
+//     index (gz * My + gy) * Mx + gx; half spectra have Mx/2 + 1 entries along x.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <string>
+
+#include "p3m.h"
+
+namespace p3m {
+
+constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
+constexpr int kBrickShift = 2;  // 4 cells per brick edge
+constexpr int kBrickCells = 64;
+
+enum ErrBits : int { kErrRange = 1, kErrNaN = 2, kErrTimeout = 4 };
+
+// Geometry, passed by value to kernels.
+struct Geom {
+  int n[3];      // mesh nodes per axis
+  int M[3];      // doubled mesh 2 n
+  int kc[3];     // cell edge in mesh spacings
+  int nc[3];     // cells per axis
+  int nb[3];     // bricks per axis
+  int order;     // 1 CIC, 2 TSC
+  int pm_bc, pp_bc;
+  double lo[3], h[3];
+  double rc, alpha, zc;
+  double s_cath;  // cathode plane in mesh units along z: (zc - lo_z) / h_z
+  double q, mass, ke;
+  double a[3];    // h_d / r_c: mesh units -> cutoff units
+  double kappa_eff;  // alpha * r_c
+};
+
+__host__ __device__ inline uint32_t cell_key(const Geom& g, int cx, int cy, int cz) {
+  const uint32_t b = (static_cast<uint32_t>(cz >> kBrickShift) * g.nb[1] + (cy >> kBrickShift)) *
+                         g.nb[0] + (cx >> kBrickShift);
+  return b * kBrickCells + static_cast<uint32_t>(((cz & 3) * 4 + (cy & 3)) * 4 + (cx & 3));
+}
+
+__host__ __device__ inline void cell_decode(const Geom& g, uint32_t key, int& cx, int& cy,
+                                            int& cz) {
+  const uint32_t b = key >> 6, l = key & 63u;
+  const uint32_t bx = b % g.nb[0], t = b / g.nb[0];
+  const uint32_t by = t % g.nb[1], bz = t / g.nb[1];
+  cx = static_cast<int>(bx * 4 + (l & 3u));
+  cy = static_cast<int>(by * 4 + ((l >> 2) & 3u));
+  cz = static_cast<int>(bz * 4 + (l >> 4));
+}
+
+struct Rec64 {
+  double u[3];
+  long long idx;
+};
+
+// FP64 short-range result per sorted particle: force (x, y, z) and potential (w)
+struct alignas(32) D4 {
+  double x, y, z, w;
+};
+
+template <typename T>
+struct RecT;
+template <>
+struct RecT<float> {
+  using type = float4;
+};
+template <>
+struct RecT<double> {
+  using type = Rec64;
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void load_rec(const float4* rec, uint32_t i, float u[3],
+                                         long long& idx) {
+  const float4 r = rec[i];
+  u[0] = r.x;
+  u[1] = r.y;
+  u[2] = r.z;
+  idx = __float_as_int(r.w);
+}
+__device__ __forceinline__ void load_rec(const Rec64* rec, uint32_t i, double u[3],
+                                         long long& idx) {
+  const Rec64 r = rec[i];
+  u[0] = r.u[0];
+  u[1] = r.u[1];
+  u[2] = r.u[2];
+  idx = r.idx;
+}
+#endif
+
+}  // namespace p3m
+
+// The opaque context of the C ABI.
+struct p3m_ctx {
+  p3m_params prm{};
+  p3m::Geom g{};
+  int64_t n_max = 0;
+  int device = 0;
+  bool fp32 = false;
+  cudaStream_t stream = nullptr;  // caller's stream (not owned)
+  cudaStream_t s_pp = nullptr;    // owned side stream for the short range
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t tev[8] = {};
+
+  // binning / counting sort
+  uint64_t nkeys = 0;
+  uint32_t* counts = nullptr;   // [nkeys]
+  uint32_t* starts = nullptr;   // [nkeys + 1]
+  uint32_t* bsum = nullptr;     // scan block sums
+  uint32_t* keys = nullptr;     // [n_max] key of each input particle
+  uint32_t* ranks = nullptr;    // [n_max] rank within its cell
+  uint32_t* skey = nullptr;     // [n_max] key of each sorted particle
+  void* rec = nullptr;          // [n_max] sorted records (float4 or Rec64)
+  void* fpp = nullptr;          // [n_max] short-range force + potential, sorted (float4/double4)
+  double* acc = nullptr;        // [3 n_max] adjoint accumulator, sorted order
+
+  // mesh
+  size_t n_real = 0;            // Mx My Mz
+  size_t n_cplx = 0;            // Mz My (Mx/2 + 1)
+  void* qpad = nullptr;         // real, doubled mesh, zero outside the n^3 block
+  void* qhat = nullptr;         // spectrum of qpad
+  void* khat_f = nullptr;       // real spectrum of the free kernel (scaled)
+  void* khat_i = nullptr;       // complex spectrum of the image kernel (scaled, phase folded)
+  void* fhat = nullptr;         // FP32: 3 difference spectra; FP64: unused
+  void* freal = nullptr;        // FP32: 3 forward-difference fields
+  void* phihat = nullptr;       // potential spectrum
+  void* phireal = nullptr;      // potential on the doubled mesh
+  float2* dfac = nullptr;       // FP32: difference factors e^{2 pi i k/M} - 1 per axis (Mx/2+1 + My + Mz)
+  cufftHandle plan_r2c = 0, plan_c2r = 0, plan_c2r3 = 0;
+  bool have_r2c = false, have_c2r = false, have_c2r3 = false;
+
+  // diagnostics
+  double* energy_acc = nullptr;              // device [2]
+  unsigned long long* pair_acc = nullptr;    // device [2]
+  int* err_dev = nullptr;                    // device error bits
+  int* err_host = nullptr;                   // pinned mirror of err_dev
+
+  // adjoint checkpoints: adj_slots (x, p) states + adj_segment + 1 positions
+  double* ckpt = nullptr;
+  double* seg = nullptr;
+  double* lam_x = nullptr;
+  double* lam_p = nullptr;
+  double* xw = nullptr;                     // [3 n_max] working state of the reverse pass
+  double* pw = nullptr;
+  double* tmp3 = nullptr;                   // [3 n_max] scratch cotangent
+  double* tmp3b = nullptr;                  // [3 n_max] scratch product
+  double* f_work = nullptr;                 // [3 n_max]
+  double* red = nullptr;                    // device reduction scratch [32]
+
+  // state
+  bool deposited = false, solved = false, phi_valid = false;
+  int64_t last_n = 0;
+  int last_parts = 0;
+  std::string last_error;
+};
+
+namespace p3m {
+
+// ---- launch helpers (defined in the .cu files) ----
+// binning and sort (sort.cu)
+void launch_bin(const p3m_ctx* c, const double* x, int64_t n, double* f_zero);
+void launch_scan(const p3m_ctx* c);
+void launch_scatter(const p3m_ctx* c, const double* x, int64_t n);
+
+// mesh (pm.cu)
+cudaError_t build_green(p3m_ctx* c);
+void launch_zero_block(const p3m_ctx* c);
+void launch_deposit(const p3m_ctx* c, int64_t n);
+void launch_dipole_deposit(const p3m_ctx* c, int64_t n, const double* w);
+void launch_green_multiply(const p3m_ctx* c, bool want_phi, bool want_diff, bool want_energy);
+void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts);
+void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, double* out);
+void launch_get_mesh(const p3m_ctx* c, int which, double* out);
+
+// short range (pp.cu)
+void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s);
+void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s);
+
+// particles (particles.cu)
+void launch_bbox(const double* x, int64_t n, double* red, cudaStream_t s);
+void launch_kick_drift(double* x, double* p, const double* f, int64_t n, double kick, double drift,
+                       cudaStream_t s);
+void launch_axpy(double* y, const double* x, int64_t n3, double a, cudaStream_t s);
+void launch_scale(double* y, const double* x, int64_t n3, double a, cudaStream_t s);
+void launch_emittance(const double* x, const double* p, int64_t n, double mc, double* eps3,
+                      double* gx, double* gp, double* red, cudaStream_t s);
+void launch_energy_out(const p3m_ctx* c, double* energy);
+
+}  // namespace p3m

@@ -1,0 +1,190 @@
+// Per-particle kernels: bounding box, leapfrog kick/drift, emittance reductions, and small
+// helpers. All particle state here is FP64 [n][3] in caller memory.
+#include <algorithm>
+
+#include "p3m_internal.cuh"
+
+namespace p3m {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(int64_t n, int t = kThreads) {
+  return static_cast<unsigned>((n + t - 1) / t);
+}
+
+// order-preserving map of finite doubles to unsigned 64-bit keys
+__device__ __forceinline__ unsigned long long ordered_key(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__global__ void k_bbox(const double* __restrict__ x, int64_t n3, unsigned long long* __restrict__ mn,
+                       unsigned long long* __restrict__ mx, int* __restrict__ bad) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n3) return;
+  const double v = x[t];
+  const int d = static_cast<int>(t % 3);
+  if (!isfinite(v)) {
+    atomicOr(bad, 1);
+    return;
+  }
+  const unsigned long long k = ordered_key(v);
+  atomicMin(mn + d, k);
+  atomicMax(mx + d, k);
+}
+
+__global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ p,
+                             const double* __restrict__ f, int64_t n3, double kick, double drift) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n3) return;
+  const double pn = p[t] + kick * f[t];
+  p[t] = pn;
+  if (drift != 0.0) x[t] += drift * pn;
+}
+
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int64_t n3, double a) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t < n3) y[t] += a * x[t];
+}
+
+__global__ void k_scale(double* __restrict__ y, const double* __restrict__ x, int64_t n3, double a) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t < n3) y[t] = a * x[t];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// sums of k values per particle row into red[0..k)
+template <int K, typename F>
+__device__ void block_sums(F get, int64_t n, double* __restrict__ red) {
+  double s[K];
+  for (int k = 0; k < K; ++k) s[k] = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    get(i, s);
+  __shared__ double ws[K][kThreads / 32];
+  for (int k = 0; k < K; ++k) {
+    const double v = warp_sum(s[k]);
+    if ((threadIdx.x & 31) == 0) ws[k][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int k = 0; k < K; ++k) {
+      double v = threadIdx.x < kThreads / 32 ? ws[k][threadIdx.x] : 0.0;
+      v = warp_sum(v);
+      if (threadIdx.x == 0) atomicAdd(red + k, v);
+    }
+  }
+}
+
+__global__ void k_mom_first(const double* __restrict__ x, const double* __restrict__ p, int64_t n,
+                            double* __restrict__ red) {
+  block_sums<6>(
+      [&](int64_t i, double* s) {
+        for (int d = 0; d < 3; ++d) {
+          s[d] += x[3 * i + d];
+          s[3 + d] += p[3 * i + d];
+        }
+      },
+      n, red);
+}
+
+// centred second moments <du^2>, <dp^2>, <du dp> per axis into red[6..15)
+__global__ void k_mom_second(const double* __restrict__ x, const double* __restrict__ p, int64_t n,
+                             double* __restrict__ red) {
+  const double inv = 1.0 / static_cast<double>(n);
+  const double mx[3] = {red[0] * inv, red[1] * inv, red[2] * inv};
+  const double mp[3] = {red[3] * inv, red[4] * inv, red[5] * inv};
+  block_sums<9>(
+      [&](int64_t i, double* s) {
+        for (int d = 0; d < 3; ++d) {
+          const double du = x[3 * i + d] - mx[d], dp = p[3 * i + d] - mp[d];
+          s[3 * d] += du * du;
+          s[3 * d + 1] += dp * dp;
+          s[3 * d + 2] += du * dp;
+        }
+      },
+      n, red + 6);
+}
+
+__global__ void k_emit_finish(const double* __restrict__ red, int64_t n, double mc,
+                              double* __restrict__ eps3) {
+  const int d = threadIdx.x;
+  if (d >= 3) return;
+  const double inv = 1.0 / static_cast<double>(n);
+  const double a = red[6 + 3 * d] * inv, b = red[7 + 3 * d] * inv, c = red[8 + 3 * d] * inv;
+  eps3[d] = sqrt(fmax(a * b - c * c, 0.0)) / mc;
+}
+
+// gradient of sum_u eps_u: (du <dp^2> - dp <du dp>) / (N (M c)^2 eps) and the p counterpart
+__global__ void k_emit_grad(const double* __restrict__ x, const double* __restrict__ p, int64_t n,
+                            const double* __restrict__ red, double mc, double* __restrict__ gx,
+                            double* __restrict__ gp) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= 3 * n) return;
+  const int d = static_cast<int>(t % 3);
+  const double inv = 1.0 / static_cast<double>(n);
+  const double a = red[6 + 3 * d] * inv, b = red[7 + 3 * d] * inv, c = red[8 + 3 * d] * inv;
+  const double eps = sqrt(fmax(a * b - c * c, 0.0)) / mc;
+  const double den = static_cast<double>(n) * mc * mc * eps;
+  const double du = x[t] - red[d] * inv, dp = p[t] - red[3 + d] * inv;
+  if (gx) gx[t] = den > 0.0 ? (du * b - dp * c) / den : 0.0;
+  if (gp) gp[t] = den > 0.0 ? (dp * a - du * c) / den : 0.0;
+}
+
+__global__ void k_energy_out(const double* __restrict__ acc, double pp_scale, double pm_scale,
+                             double* __restrict__ energy) {
+  if (threadIdx.x == 0) {
+    energy[0] = pp_scale * acc[0];
+    energy[1] = pm_scale * acc[1];
+  }
+}
+
+}  // namespace
+
+void launch_bbox(const double* x, int64_t n, double* red, cudaStream_t s) {
+  auto* mn = reinterpret_cast<unsigned long long*>(red);
+  auto* mx = mn + 3;
+  int* bad = reinterpret_cast<int*>(red + 6);
+  cudaMemsetAsync(mn, 0xff, 3 * sizeof(unsigned long long), s);
+  cudaMemsetAsync(mx, 0x00, 3 * sizeof(unsigned long long), s);
+  cudaMemsetAsync(bad, 0, sizeof(int), s);
+  if (n > 0) k_bbox<<<blocks_for(3 * n), kThreads, 0, s>>>(x, 3 * n, mn, mx, bad);
+}
+
+void launch_kick_drift(double* x, double* p, const double* f, int64_t n, double kick, double drift,
+                       cudaStream_t s) {
+  if (n > 0) k_kick_drift<<<blocks_for(3 * n), kThreads, 0, s>>>(x, p, f, 3 * n, kick, drift);
+}
+
+void launch_axpy(double* y, const double* x, int64_t n3, double a, cudaStream_t s) {
+  if (n3 > 0) k_axpy<<<blocks_for(n3), kThreads, 0, s>>>(y, x, n3, a);
+}
+
+void launch_scale(double* y, const double* x, int64_t n3, double a, cudaStream_t s) {
+  if (n3 > 0) k_scale<<<blocks_for(n3), kThreads, 0, s>>>(y, x, n3, a);
+}
+
+void launch_emittance(const double* x, const double* p, int64_t n, double mc, double* eps3,
+                      double* gx, double* gp, double* red, cudaStream_t s) {
+  cudaMemsetAsync(red, 0, 16 * sizeof(double), s);
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(blocks_for(n), 1216));
+  k_mom_first<<<blocks, kThreads, 0, s>>>(x, p, n, red);
+  k_mom_second<<<blocks, kThreads, 0, s>>>(x, p, n, red);
+  if (eps3) k_emit_finish<<<1, 32, 0, s>>>(red, n, mc, eps3);
+  if (gx || gp) k_emit_grad<<<blocks_for(3 * n), kThreads, 0, s>>>(x, p, n, red, mc, gx, gp);
+}
+
+void launch_energy_out(const p3m_ctx* c, double* energy) {
+  // short range: (1/2) q sum_i phi^S_i with phi^S in units k_e q / r_c;
+  // long range: (1/2) q sum_m W[m] phi[m] (W = assignment weights, phi in volts)
+  const double pp_scale = 0.5 * c->g.ke * c->g.q * c->g.q / c->g.rc;
+  const double pm_scale = 0.5 * c->g.q;
+  k_energy_out<<<1, 32, 0, c->stream>>>(c->energy_acc, pp_scale, pm_scale, energy);
+}
+
+}  // namespace p3m

@@ -1,0 +1,645 @@
+// Long-range (particle-mesh) half of P3M: charge assignment, Green's-function convolution on the
+// doubled mesh (free space plus the planar-cathode image term), and interpolation of the force.
+//
+//  * assignment (eq. (rho_L), W = W^L): TSC (one order above the paper's cloud-in-cell
+//    example, eq. (interpolation_splines_b0)) or CIC, accumulated with atomics;
+//  * solve (eq. (phi_L) with eq. (GreenFunc_planar_cathode)):
+//      phi = k_e [ K_f (*) Q  -  K_i (*) Q_rev ],  Q_rev[., ., j] = Q[., ., n_z - 1 - j],
+//    where K_i samples G^L at the image offsets (x_g - S(x_g')); in Fourier space the reversed
+//    charge is a phase times the spectrum at -k_z, so both terms share one forward transform;
+//  * force (eq. (eom_p3m_coord), first term) with the analytic derivative of W.
+//
+// FP32 path: the mesh potential of a bunch is a few hundred times larger than its differences
+// between neighbouring nodes, so differencing an FP32 potential would lose ~1e-5 of the force.
+// The FP32 path therefore convolves Q with the three forward-difference kernels
+// K(m + e_d) - K(m) (a factor e^{2 pi i k_d / M_d} - 1 in Fourier space) and assembles the
+// analytic-derivative force from the difference fields D_d = phi(g + e_d) - phi(g) by
+// summation by parts:
+//   sum_a phi_a dw(a) = (1/2 - u) D_{c-1} + (1/2 + u) D_c   (TSC),   = D_c   (CIC).
+// This is the same discrete force; only the rounding moves from phi to its differences.
+#include <cmath>
+#include <type_traits>
+
+#include "p3m_internal.cuh"
+
+namespace p3m {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(uint64_t n, int t = kThreads) {
+  return static_cast<unsigned>((n + t - 1) / t);
+}
+
+__device__ __forceinline__ size_t real_index(const Geom& g, int x, int y, int z) {
+  return (static_cast<size_t>(z) * g.M[1] + y) * g.M[0] + x;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Green's-function spectra (built once per geometry, in FP64)
+// ---------------------------------------------------------------------------------------------
+__global__ void k_sample_kernel(Geom g, double* __restrict__ out, int image) {
+  const size_t total = static_cast<size_t>(g.M[0]) * g.M[1] * g.M[2];
+  const size_t idx = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (idx >= total) return;
+  const int ix = static_cast<int>(idx % g.M[0]);
+  const int iy = static_cast<int>((idx / g.M[0]) % g.M[1]);
+  const int iz = static_cast<int>(idx / (static_cast<size_t>(g.M[0]) * g.M[1]));
+  if (ix == g.n[0] || iy == g.n[1] || iz == g.n[2]) {  // the one offset never used
+    out[idx] = 0.0;
+    return;
+  }
+  const int mx = ix < g.n[0] ? ix : ix - g.M[0];
+  const int my = iy < g.n[1] ? iy : iy - g.M[1];
+  const int mz = iz < g.n[2] ? iz : iz - g.M[2];
+  const double X = mx * g.h[0], Y = my * g.h[1];
+  double Z;
+  if (image) {
+    const double d = g.lo[2] - g.zc;
+    Z = 2.0 * d + static_cast<double>(mz + g.n[2] - 1) * g.h[2];
+  } else {
+    Z = mz * g.h[2];
+  }
+  const double r = sqrt(X * X + Y * Y + Z * Z);
+  out[idx] = r > 0.0 ? erf(g.alpha * r) / r : 2.0 * g.alpha * 0.56418958354775628695;  // 1/sqrt(pi)
+}
+
+__device__ double infl_factor(const Geom& g, int kx, int ky, int kz) {
+  // 1 / U(k)^2 with U = prod_d sinc(pi kappa_d / M_d)^(order + 1)
+  const int kk[3] = {kx, ky < g.M[1] / 2 + 1 ? ky : ky - g.M[1], kz < g.M[2] / 2 + 1 ? kz : kz - g.M[2]};
+  double U = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    const double t = static_cast<double>(kk[d]) / g.M[d];
+    const double s = (kk[d] == 0) ? 1.0 : sinpi(t) / (3.14159265358979323846 * t);
+    double p = 1.0;
+    for (int o = 0; o <= g.order; ++o) p *= s;
+    U *= p;
+  }
+  return 1.0 / (U * U);
+}
+
+template <typename T>
+__global__ void k_finish_kernels(Geom g, const double2* __restrict__ Sf,
+                                 const double2* __restrict__ Si, T* __restrict__ kf,
+                                 typename std::conditional<sizeof(T) == 4, float2, double2>::type* __restrict__ ki,
+                                 double scale, int influence) {
+  const int Hx = g.M[0] / 2 + 1;
+  const size_t total = static_cast<size_t>(Hx) * g.M[1] * g.M[2];
+  const size_t idx = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (idx >= total) return;
+  const int kx = static_cast<int>(idx % Hx);
+  const int ky = static_cast<int>((idx / Hx) % g.M[1]);
+  const int kz = static_cast<int>(idx / (static_cast<size_t>(Hx) * g.M[1]));
+  double sc = scale;
+  if (influence) sc *= infl_factor(g, kx, ky, kz);
+  kf[idx] = static_cast<T>(Sf[idx].x * sc);  // the free kernel is even in every axis: real spectrum
+  if (Si) {
+    // fold the phase of the z-reversal: Qrev^(k) = e^{-2 pi i kz (nz - 1)/Mz} Q^(kx, ky, -kz)
+    const long long t = (2LL * kz * (g.n[2] - 1)) % (2LL * g.M[2]);
+    double sn, cs;
+    sincospi(-static_cast<double>(t) / g.M[2], &sn, &cs);
+    const double2 a = Si[idx];
+    ki[idx].x = static_cast<T>((a.x * cs - a.y * sn) * sc);
+    ki[idx].y = static_cast<T>((a.x * sn + a.y * cs) * sc);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Charge assignment
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct Axis {
+  int c;     // first node of the weight support
+  T w[3];    // weights on nodes c .. c+S-1
+  T dw[3];   // d/ds of the weights
+  T gl, gr;  // coefficients of D_{c0-1} and D_{c0} in sum_a phi_a dw(a) (TSC: c0 = c+1)
+};
+
+template <typename T>
+__device__ __forceinline__ Axis<T> axis_weights(int order, int cell_node, T u) {
+  Axis<T> a;
+  if (order == 2) {
+    const T t = floor(u + T(0.5));
+    const T f = u - t;
+    a.c = cell_node + static_cast<int>(t) - 1;
+    const T l = T(0.5) - f, r = T(0.5) + f;
+    a.w[0] = T(0.5) * l * l;
+    a.w[1] = T(0.75) - f * f;
+    a.w[2] = T(0.5) * r * r;
+    a.dw[0] = -l;
+    a.dw[1] = T(-2) * f;
+    a.dw[2] = r;
+    a.gl = l;
+    a.gr = r;
+  } else {
+    const T t = floor(u);
+    const T f = u - t;
+    a.c = cell_node + static_cast<int>(t);
+    a.w[0] = T(1) - f;
+    a.w[1] = f;
+    a.w[2] = T(0);
+    a.dw[0] = T(-1);
+    a.dw[1] = T(1);
+    a.dw[2] = T(0);
+    a.gl = T(0);
+    a.gr = T(1);
+  }
+  return a;
+}
+
+template <typename T>
+__device__ __forceinline__ void particle_axes(const Geom& g, const typename RecT<T>::type* rec,
+                                              const uint32_t* skey, uint32_t i, Axis<T> ax[3],
+                                              long long& idx) {
+  T u[3];
+  load_rec(rec, i, u, idx);
+  int cx, cy, cz;
+  cell_decode(g, skey[i], cx, cy, cz);
+  ax[0] = axis_weights<T>(g.order, cx * g.kc[0], u[0]);
+  ax[1] = axis_weights<T>(g.order, cy * g.kc[1], u[1]);
+  ax[2] = axis_weights<T>(g.order, cz * g.kc[2], u[2]);
+}
+
+template <typename T>
+__global__ void k_deposit(Geom g, const uint32_t* __restrict__ total,
+                          const typename RecT<T>::type* __restrict__ rec,
+                          const uint32_t* __restrict__ skey, T* __restrict__ qpad) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *total) return;
+  Axis<T> ax[3];
+  long long idx;
+  particle_axes<T>(g, rec, skey, i, ax, idx);
+  const int S = g.order == 2 ? 3 : 2;
+  for (int c = 0; c < S; ++c)
+    for (int b = 0; b < S; ++b) {
+      const T wyz = ax[1].w[b] * ax[2].w[c];
+      T* row = qpad + real_index(g, ax[0].c, ax[1].c + b, ax[2].c + c);
+      for (int a = 0; a < S; ++a) atomicAdd(row + a, ax[0].w[a] * wyz);
+    }
+}
+
+// psi_g = sum_i grad_xi W(x_g - xi_i) . w_i  (adjoint of the assignment feeding the solve)
+template <typename T>
+__global__ void k_dipole_deposit(Geom g, const uint32_t* __restrict__ total,
+                                 const typename RecT<T>::type* __restrict__ rec,
+                                 const uint32_t* __restrict__ skey, const double* __restrict__ w,
+                                 T* __restrict__ qpad) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *total) return;
+  Axis<T> ax[3];
+  long long idx;
+  particle_axes<T>(g, rec, skey, i, ax, idx);
+  const T w0 = static_cast<T>(w[3 * idx] / g.h[0]);
+  const T w1 = static_cast<T>(w[3 * idx + 1] / g.h[1]);
+  const T w2 = static_cast<T>(w[3 * idx + 2] / g.h[2]);
+  const int S = g.order == 2 ? 3 : 2;
+  for (int c = 0; c < S; ++c)
+    for (int b = 0; b < S; ++b) {
+      T* row = qpad + real_index(g, ax[0].c, ax[1].c + b, ax[2].c + c);
+      for (int a = 0; a < S; ++a) {
+        const T v = w0 * ax[0].dw[a] * ax[1].w[b] * ax[2].w[c] +
+                    w1 * ax[0].w[a] * ax[1].dw[b] * ax[2].w[c] +
+                    w2 * ax[0].w[a] * ax[1].w[b] * ax[2].dw[c];
+        atomicAdd(row + a, v);
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Spectral multiply: base(k) = Kf(k) Q(k) - Ki(k) Q(kx, ky, -kz); outputs the potential
+// spectrum and/or the three difference spectra; accumulates sum_m W[m] phi[m] by Parseval.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+
+template <typename T>
+__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  C2<T> r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+template <typename T>
+__global__ void k_green_multiply(Geom g, const C2<T>* __restrict__ qhat, const T* __restrict__ kf,
+                                 const C2<T>* __restrict__ ki, const float2* __restrict__ dfac,
+                                 C2<T>* __restrict__ dhat, C2<T>* __restrict__ phihat,
+                                 double* __restrict__ energy, size_t ncplx) {
+  const int Hx = g.M[0] / 2 + 1;
+  const int Mz = g.M[2];
+  const size_t total = static_cast<size_t>(Hx) * g.M[1] * (Mz / 2 + 1);
+  const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  double e = 0.0;
+  if (t < total) {
+    const int kx = static_cast<int>(t % Hx);
+    const int ky = static_cast<int>((t / Hx) % g.M[1]);
+    const int kz = static_cast<int>(t / (static_cast<size_t>(Hx) * g.M[1]));
+    const int kz2 = (Mz - kz) % Mz;
+    const size_t ia = (static_cast<size_t>(kz) * g.M[1] + ky) * Hx + kx;
+    const size_t ib = (static_cast<size_t>(kz2) * g.M[1] + ky) * Hx + kx;
+    const C2<T> a = qhat[ia], b = qhat[ib];
+    C2<T> ba, bb;
+    ba.x = kf[ia] * a.x;
+    ba.y = kf[ia] * a.y;
+    bb.x = kf[ib] * b.x;
+    bb.y = kf[ib] * b.y;
+    if (ki) {
+      const C2<T> ta = cmul<T>(ki[ia], b), tb = cmul<T>(ki[ib], a);
+      ba.x -= ta.x;
+      ba.y -= ta.y;
+      bb.x -= tb.x;
+      bb.y -= tb.y;
+    }
+    const double wx = (kx == 0 || 2 * kx == g.M[0]) ? 1.0 : 2.0;
+    e = wx * (static_cast<double>(a.x) * ba.x + static_cast<double>(a.y) * ba.y);
+    if (kz2 != kz) e += wx * (static_cast<double>(b.x) * bb.x + static_cast<double>(b.y) * bb.y);
+    if (phihat) {
+      phihat[ia] = ba;
+      if (kz2 != kz) phihat[ib] = bb;
+    }
+    if (dhat) {
+      const float2* fx = dfac;
+      const float2* fy = dfac + Hx;
+      const float2* fz = dfac + Hx + g.M[1];
+      C2<T> f;
+      f.x = fx[kx].x; f.y = fx[kx].y;
+      dhat[ia] = cmul<T>(ba, f);
+      f.x = fy[ky].x; f.y = fy[ky].y;
+      dhat[ncplx + ia] = cmul<T>(ba, f);
+      f.x = fz[kz].x; f.y = fz[kz].y;
+      dhat[2 * ncplx + ia] = cmul<T>(ba, f);
+      if (kz2 != kz) {
+        f.x = fx[kx].x; f.y = fx[kx].y;
+        dhat[ib] = cmul<T>(bb, f);
+        f.x = fy[ky].x; f.y = fy[ky].y;
+        dhat[ncplx + ib] = cmul<T>(bb, f);
+        f.x = fz[kz2].x; f.y = fz[kz2].y;
+        dhat[2 * ncplx + ib] = cmul<T>(bb, f);
+      }
+    }
+  }
+  if (energy) {
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    __shared__ double ws[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double v = threadIdx.x < kThreads / 32 ? ws[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (threadIdx.x == 0) atomicAdd(energy, v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Interpolation of the long-range force and combination with the short-range force
+// ---------------------------------------------------------------------------------------------
+// FP32: from the forward-difference fields D_d (volts).
+__device__ __forceinline__ void grad_from_diff(const Geom& g, const float* __restrict__ D,
+                                               size_t nreal, const Axis<float> ax[3], float G[3]) {
+  const int S = g.order == 2 ? 3 : 2;
+  const int off = g.order == 2 ? 0 : 1;  // TSC: D nodes c, c+1 (= c0-1, c0); CIC: node c only
+  // x derivative
+  {
+    const float* Dx = D;
+    float acc = 0.f;
+    for (int c = 0; c < S; ++c)
+      for (int b = 0; b < S; ++b) {
+        const float wyz = ax[1].w[b] * ax[2].w[c];
+        const size_t r = real_index(g, ax[0].c, ax[1].c + b, ax[2].c + c);
+        acc += wyz * (ax[0].gl * Dx[r] * (1 - off) + ax[0].gr * Dx[r + 1 - off]);
+      }
+    G[0] = acc;
+  }
+  {
+    const float* Dy = D + nreal;
+    float acc = 0.f;
+    for (int c = 0; c < S; ++c)
+      for (int a = 0; a < S; ++a) {
+        const float wxz = ax[0].w[a] * ax[2].w[c];
+        const float lo = off ? 0.f : Dy[real_index(g, ax[0].c + a, ax[1].c, ax[2].c + c)];
+        const float hi = Dy[real_index(g, ax[0].c + a, ax[1].c + 1 - off, ax[2].c + c)];
+        acc += wxz * (ax[1].gl * lo + ax[1].gr * hi);
+      }
+    G[1] = acc;
+  }
+  {
+    const float* Dz = D + 2 * nreal;
+    float acc = 0.f;
+    for (int b = 0; b < S; ++b)
+      for (int a = 0; a < S; ++a) {
+        const float wxy = ax[0].w[a] * ax[1].w[b];
+        const float lo = off ? 0.f : Dz[real_index(g, ax[0].c + a, ax[1].c + b, ax[2].c)];
+        const float hi = Dz[real_index(g, ax[0].c + a, ax[1].c + b, ax[2].c + 1 - off)];
+        acc += wxy * (ax[2].gl * lo + ax[2].gr * hi);
+      }
+    G[2] = acc;
+  }
+}
+
+// FP64: from the potential phi (volts), analytic derivative of W.
+__device__ __forceinline__ void grad_from_phi(const Geom& g, const double* __restrict__ phi,
+                                              const Axis<double> ax[3], double G[3]) {
+  const int S = g.order == 2 ? 3 : 2;
+  G[0] = G[1] = G[2] = 0.0;
+  for (int c = 0; c < S; ++c)
+    for (int b = 0; b < S; ++b) {
+      const double* row = phi + real_index(g, ax[0].c, ax[1].c + b, ax[2].c + c);
+      for (int a = 0; a < S; ++a) {
+        const double p = row[a];
+        G[0] += p * ax[0].dw[a] * ax[1].w[b] * ax[2].w[c];
+        G[1] += p * ax[0].w[a] * ax[1].dw[b] * ax[2].w[c];
+        G[2] += p * ax[0].w[a] * ax[1].w[b] * ax[2].dw[c];
+      }
+    }
+}
+
+template <typename T>
+__global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
+                         const typename RecT<T>::type* __restrict__ rec,
+                         const uint32_t* __restrict__ skey, const T* __restrict__ field,
+                         size_t nreal, const void* __restrict__ fpp, double* __restrict__ f,
+                         int parts, double pp_scale) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *total) return;
+  Axis<T> ax[3];
+  long long idx;
+  particle_axes<T>(g, rec, skey, i, ax, idx);
+  double F[3] = {0.0, 0.0, 0.0};
+  if (parts & 2) {
+    T G[3];
+    if constexpr (sizeof(T) == 4)
+      grad_from_diff(g, field, nreal, ax, G);
+    else
+      grad_from_phi(g, field, ax, G);
+    for (int d = 0; d < 3; ++d) F[d] = -g.q / g.h[d] * static_cast<double>(G[d]);
+  }
+  if (parts & 1) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 s = reinterpret_cast<const float4*>(fpp)[i];
+      F[0] += pp_scale * s.x;
+      F[1] += pp_scale * s.y;
+      F[2] += pp_scale * s.z;
+    } else {
+      const D4 s = reinterpret_cast<const D4*>(fpp)[i];
+      F[0] += pp_scale * s.x;
+      F[1] += pp_scale * s.y;
+      F[2] += pp_scale * s.z;
+    }
+  }
+  f[3 * idx] = F[0];
+  f[3 * idx + 1] = F[1];
+  f[3 * idx + 2] = F[2];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Adjoint gather. pass 0: acc += -q (grad grad sum_g phi_g W) w_k   (phi of the charges)
+//                 pass 1: out_k = acc - q sum_g chi_g grad W          (chi of the dipoles),
+// where chi carries the factor q of the stored kernel, so -q^2 sum chi_true grad W appears as
+// -q sum chi grad W.
+// ---------------------------------------------------------------------------------------------
+// Hessian sum_g phi_g d2W/dxi_d dxi_e in mesh units (no 1/h factors) from the difference fields.
+__device__ void hess_from_diff(const Geom& g, const float* __restrict__ D, size_t nreal,
+                               const Axis<float> ax[3], float H[3][3]) {
+  const int S = g.order == 2 ? 3 : 2;
+  const bool tsc = g.order == 2;
+  for (int d = 0; d < 3; ++d)
+    for (int e = 0; e < 3; ++e) H[d][e] = 0.f;
+  for (int d = 0; d < 3; ++d) {
+    const float* Dd = D + d * nreal;
+    const int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+    // values of the d-derivative sum along the other axes' nodes
+    for (int j2 = 0; j2 < S; ++j2)
+      for (int j1 = 0; j1 < S; ++j1) {
+        int node[3];
+        node[o1] = ax[o1].c + j1;
+        node[o2] = ax[o2].c + j2;
+        node[d] = ax[d].c;  // TSC: c0 - 1; CIC: c
+        const float D0 = Dd[real_index(g, node[0], node[1], node[2])];
+        node[d] = ax[d].c + 1;
+        const float D1 = tsc ? Dd[real_index(g, node[0], node[1], node[2])] : 0.f;
+        const float grad = tsc ? ax[d].gl * D0 + ax[d].gr * D1 : D0;
+        const float secd = tsc ? D1 - D0 : 0.f;  // phi_{c-1} - 2 phi_c + phi_{c+1}
+        const float w1 = ax[o1].w[j1], w2 = ax[o2].w[j2];
+        H[d][d] += secd * w1 * w2;
+        H[d][o1] += grad * ax[o1].dw[j1] * w2;
+        H[d][o2] += grad * w1 * ax[o2].dw[j2];
+      }
+  }
+  // symmetrise the mixed terms (each was accumulated from both axes' difference fields)
+  for (int d = 0; d < 3; ++d)
+    for (int e = d + 1; e < 3; ++e) {
+      const float m = 0.5f * (H[d][e] + H[e][d]);
+      H[d][e] = H[e][d] = m;
+    }
+}
+
+__device__ void hess_from_phi(const Geom& g, const double* __restrict__ phi,
+                              const Axis<double> ax[3], double H[3][3]) {
+  const int S = g.order == 2 ? 3 : 2;
+  // second derivative of the 1D weights: TSC {1, -2, 1}, CIC 0
+  const double d2[3] = {1.0, -2.0, 1.0};
+  const bool tsc = g.order == 2;
+  for (int d = 0; d < 3; ++d)
+    for (int e = 0; e < 3; ++e) H[d][e] = 0.0;
+  for (int c = 0; c < S; ++c)
+    for (int b = 0; b < S; ++b) {
+      const double* row = phi + real_index(g, ax[0].c, ax[1].c + b, ax[2].c + c);
+      for (int a = 0; a < S; ++a) {
+        const double p = row[a];
+        if (tsc) {
+          H[0][0] += p * d2[a] * ax[1].w[b] * ax[2].w[c];
+          H[1][1] += p * ax[0].w[a] * d2[b] * ax[2].w[c];
+          H[2][2] += p * ax[0].w[a] * ax[1].w[b] * d2[c];
+        }
+        H[0][1] += p * ax[0].dw[a] * ax[1].dw[b] * ax[2].w[c];
+        H[0][2] += p * ax[0].dw[a] * ax[1].w[b] * ax[2].dw[c];
+        H[1][2] += p * ax[0].w[a] * ax[1].dw[b] * ax[2].dw[c];
+      }
+    }
+  H[1][0] = H[0][1];
+  H[2][0] = H[0][2];
+  H[2][1] = H[1][2];
+}
+
+template <typename T>
+__global__ void k_vjp_gather(Geom g, const uint32_t* __restrict__ total,
+                             const typename RecT<T>::type* __restrict__ rec,
+                             const uint32_t* __restrict__ skey, const T* __restrict__ field,
+                             size_t nreal, const double* __restrict__ w, double* __restrict__ acc,
+                             double* __restrict__ out, int pass) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *total) return;
+  Axis<T> ax[3];
+  long long idx;
+  particle_axes<T>(g, rec, skey, i, ax, idx);
+  if (pass == 0) {
+    T H[3][3];
+    if constexpr (sizeof(T) == 4)
+      hess_from_diff(g, field, nreal, ax, H);
+    else
+      hess_from_phi(g, field, ax, H);
+    const double wv[3] = {w[3 * idx], w[3 * idx + 1], w[3 * idx + 2]};
+    for (int d = 0; d < 3; ++d) {
+      double hw = 0.0;
+      for (int e = 0; e < 3; ++e) hw += static_cast<double>(H[d][e]) / (g.h[d] * g.h[e]) * wv[e];
+      acc[3 * i + d] += -g.q * hw;
+    }
+  } else {
+    T G[3];
+    if constexpr (sizeof(T) == 4)
+      grad_from_diff(g, field, nreal, ax, G);
+    else
+      grad_from_phi(g, field, ax, G);
+    for (int d = 0; d < 3; ++d)
+      out[3 * idx + d] = acc[3 * i + d] - g.q * static_cast<double>(G[d]) / g.h[d];
+  }
+}
+
+template <typename T>
+__global__ void k_get_mesh(Geom g, const T* __restrict__ src, double scale,
+                           double* __restrict__ out) {
+  const size_t total = static_cast<size_t>(g.n[0]) * g.n[1] * g.n[2];
+  const size_t idx = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (idx >= total) return;
+  const int x = static_cast<int>(idx % g.n[0]);
+  const int y = static_cast<int>((idx / g.n[0]) % g.n[1]);
+  const int z = static_cast<int>(idx / (static_cast<size_t>(g.n[0]) * g.n[1]));
+  out[idx] = scale * static_cast<double>(src[real_index(g, x, y, z)]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+cudaError_t build_green(p3m_ctx* c) {
+  const Geom& g = c->g;
+  const size_t nreal = c->n_real, ncplx = c->n_cplx;
+  double* samp = nullptr;
+  double2* sf = nullptr;
+  double2* si = nullptr;
+  cufftHandle plan = 0;
+  bool have_plan = false;
+  cudaError_t err = cudaSuccess;
+  auto fail = [&](cudaError_t e) {
+    if (have_plan) cufftDestroy(plan);
+    cudaFree(samp);
+    cudaFree(sf);
+    cudaFree(si);
+    return e;
+  };
+  if ((err = cudaMalloc(&samp, sizeof(double) * nreal)) != cudaSuccess) return fail(err);
+  if ((err = cudaMalloc(&sf, sizeof(double2) * ncplx)) != cudaSuccess) return fail(err);
+  if (g.pm_bc && (err = cudaMalloc(&si, sizeof(double2) * ncplx)) != cudaSuccess) return fail(err);
+  if (cufftPlan3d(&plan, g.M[2], g.M[1], g.M[0], CUFFT_D2Z) != CUFFT_SUCCESS)
+    return fail(cudaErrorUnknown);
+  have_plan = true;
+  cufftSetStream(plan, c->stream);
+  k_sample_kernel<<<blocks_for(nreal), kThreads, 0, c->stream>>>(g, samp, 0);
+  if (cufftExecD2Z(plan, samp, reinterpret_cast<cufftDoubleComplex*>(sf)) != CUFFT_SUCCESS)
+    return fail(cudaErrorUnknown);
+  if (g.pm_bc) {
+    k_sample_kernel<<<blocks_for(nreal), kThreads, 0, c->stream>>>(g, samp, 1);
+    if (cufftExecD2Z(plan, samp, reinterpret_cast<cufftDoubleComplex*>(si)) != CUFFT_SUCCESS)
+      return fail(cudaErrorUnknown);
+  }
+  // scale: k_e q / (Mx My Mz); the mesh holds assignment weights, the inverse FFT is unnormalised
+  const double scale = g.ke * g.q / static_cast<double>(nreal);
+  if (c->fp32)
+    k_finish_kernels<float><<<blocks_for(ncplx), kThreads, 0, c->stream>>>(
+        g, sf, si, static_cast<float*>(c->khat_f), static_cast<float2*>(c->khat_i), scale,
+        c->prm.influence);
+  else
+    k_finish_kernels<double><<<blocks_for(ncplx), kThreads, 0, c->stream>>>(
+        g, sf, si, static_cast<double*>(c->khat_f), static_cast<double2*>(c->khat_i), scale,
+        c->prm.influence);
+  err = cudaStreamSynchronize(c->stream);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  return fail(err);
+}
+
+void launch_zero_block(const p3m_ctx* c) {
+  const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
+  cudaPitchedPtr pp = make_cudaPitchedPtr(c->qpad, es * c->g.M[0], es * c->g.M[0], c->g.M[1]);
+  cudaMemset3DAsync(pp, 0, make_cudaExtent(es * c->g.n[0], c->g.n[1], c->g.n[2]), c->stream);
+}
+
+void launch_deposit(const p3m_ctx* c, int64_t n) {
+  if (n == 0) return;
+  const uint32_t* total = c->starts + c->nkeys;
+  if (c->fp32)
+    k_deposit<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const float4*>(c->rec), c->skey, static_cast<float*>(c->qpad));
+  else
+    k_deposit<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const Rec64*>(c->rec), c->skey, static_cast<double*>(c->qpad));
+}
+
+void launch_dipole_deposit(const p3m_ctx* c, int64_t n, const double* w) {
+  if (n == 0) return;
+  const uint32_t* total = c->starts + c->nkeys;
+  if (c->fp32)
+    k_dipole_deposit<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const float4*>(c->rec), c->skey, w, static_cast<float*>(c->qpad));
+  else
+    k_dipole_deposit<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const Rec64*>(c->rec), c->skey, w,
+        static_cast<double*>(c->qpad));
+}
+
+void launch_green_multiply(const p3m_ctx* c, bool want_phi, bool want_diff, bool want_energy) {
+  const Geom& g = c->g;
+  const size_t total = static_cast<size_t>(g.M[0] / 2 + 1) * g.M[1] * (g.M[2] / 2 + 1);
+  double* en = want_energy ? c->energy_acc + 1 : nullptr;
+  if (c->fp32)
+    k_green_multiply<float><<<blocks_for(total), kThreads, 0, c->stream>>>(
+        g, static_cast<const float2*>(c->qhat), static_cast<const float*>(c->khat_f),
+        static_cast<const float2*>(c->khat_i), c->dfac,
+        want_diff ? static_cast<float2*>(c->fhat) : nullptr,
+        want_phi ? static_cast<float2*>(c->phihat) : nullptr, en, c->n_cplx);
+  else
+    k_green_multiply<double><<<blocks_for(total), kThreads, 0, c->stream>>>(
+        g, static_cast<const double2*>(c->qhat), static_cast<const double*>(c->khat_f),
+        static_cast<const double2*>(c->khat_i), nullptr, nullptr,
+        want_phi ? static_cast<double2*>(c->phihat) : nullptr, en, c->n_cplx);
+}
+
+void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts) {
+  if (n == 0) return;
+  const uint32_t* total = c->starts + c->nkeys;
+  const double pp_scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc);
+  if (c->fp32)
+    k_interp<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const float4*>(c->rec), c->skey,
+        static_cast<const float*>(c->freal), c->n_real, c->fpp, f, parts, pp_scale);
+  else
+    k_interp<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const Rec64*>(c->rec), c->skey,
+        static_cast<const double*>(c->phireal), c->n_real, c->fpp, f, parts, pp_scale);
+}
+
+void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, double* out) {
+  if (n == 0) return;
+  const uint32_t* total = c->starts + c->nkeys;
+  if (c->fp32)
+    k_vjp_gather<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const float4*>(c->rec), c->skey,
+        static_cast<const float*>(c->freal), c->n_real, w, c->acc, out, pass);
+  else
+    k_vjp_gather<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const Rec64*>(c->rec), c->skey,
+        static_cast<const double*>(c->phireal), c->n_real, w, c->acc, out, pass);
+}
+
+void launch_get_mesh(const p3m_ctx* c, int which, double* out) {
+  const size_t total = static_cast<size_t>(c->g.n[0]) * c->g.n[1] * c->g.n[2];
+  const void* src = which == 0 ? c->qpad : c->phireal;
+  const double scale = which == 0 ? c->g.q : 1.0;
+  if (c->fp32)
+    k_get_mesh<float><<<blocks_for(total), kThreads, 0, c->stream>>>(
+        c->g, static_cast<const float*>(src), scale, out);
+  else
+    k_get_mesh<double><<<blocks_for(total), kThreads, 0, c->stream>>>(
+        c->g, static_cast<const double*>(src), scale, out);
+}
+
+}  // namespace p3m

@@ -1,0 +1,220 @@
+// Binning of particles into cutoff cells and a counting sort by cell.
+//
+// The short-range sum of eq. (summation_short) needs, for each particle, the particles
+// "close to" it (within r_c, Sec. 3.1.1, fig. ShortError). Cells of edge kc_d h_d >= r_c
+// turn that search into the 27 neighbouring cells. The sort is a counting sort in three
+// passes: histogram with in-cell ranks (atomics), exclusive scan of the cell counts, scatter.
+// No pass waits on another block, so no inter-block spin is needed.
+#include "p3m_internal.cuh"
+
+namespace p3m {
+namespace {
+
+constexpr int kBinThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;  // per thread
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Mesh coordinate s_d = (x_d - lo_d) / h_d and validity of one particle.
+// Valid: the assignment support lies inside the mesh (TSC: floor(s + 1/2) in [1, n - 2];
+// CIC: floor(s) in [0, n - 2]) and, with the cathode in the long-range solve, z > z_cathode.
+// Returns 0 if valid, else an error bit.
+__device__ __forceinline__ int particle_cell(const Geom& g, const double* __restrict__ xi,
+                                             double s[3], int cell[3]) {
+  int err = 0;
+  for (int d = 0; d < 3; ++d) {
+    const double v = xi[d];
+    s[d] = (v - g.lo[d]) / g.h[d];
+    if (!(s[d] == s[d])) return kErrNaN;
+    const double c = (g.order == 2) ? floor(s[d] + 0.5) : floor(s[d]);
+    const double cmin = (g.order == 2) ? 1.0 : 0.0;
+    if (!(c >= cmin && c <= static_cast<double>(g.n[d] - 2))) err = kErrRange;
+  }
+  if (g.pm_bc && !(xi[2] > g.zc)) err = kErrRange;
+  if (err) return err;
+  for (int d = 0; d < 3; ++d) cell[d] = static_cast<int>(floor(s[d])) / g.kc[d];
+  return 0;
+}
+
+__global__ void k_bin(Geom g, const double* __restrict__ x, int64_t n,
+                      uint32_t* __restrict__ counts, uint32_t* __restrict__ keys,
+                      uint32_t* __restrict__ ranks, int* __restrict__ err,
+                      double* __restrict__ f_zero) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  double s[3];
+  int cell[3];
+  const int e = particle_cell(g, x + 3 * i, s, cell);
+  if (e) {
+    keys[i] = kInvalidKey;
+    atomicOr(err, e);
+    if (f_zero) {
+      f_zero[3 * i] = 0.0;
+      f_zero[3 * i + 1] = 0.0;
+      f_zero[3 * i + 2] = 0.0;
+    }
+    return;
+  }
+  const uint32_t key = cell_key(g, cell[0], cell[1], cell[2]);
+  keys[i] = key;
+  ranks[i] = atomicAdd(counts + key, 1u);
+}
+
+// Exclusive scan, level 1: each block scans kScanTile counts and records its total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t* __restrict__ in,
+                                                             uint32_t* __restrict__ out,
+                                                             uint32_t* __restrict__ bsum,
+                                                             uint64_t n) {
+  __shared__ uint32_t warp_tot[kScanThreads / 32];
+  const uint64_t base = blockIdx.x * static_cast<uint64_t>(kScanTile) +
+                        threadIdx.x * static_cast<uint64_t>(kScanItems);
+  uint32_t v[kScanItems];
+  uint32_t run = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    const uint32_t t = v[k];
+    v[k] = run;
+    run += t;
+  }
+  // block-wide exclusive scan of the per-thread totals
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = (lane < kScanThreads / 32) ? warp_tot[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = wi - w;  // exclusive
+    if (lane == 31) bsum[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  const uint32_t pre = warp_tot[wid] + incl - run;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) out[base + k] = v[k] + pre;
+}
+
+// Level 2: one block scans the tile totals in chunks with a running carry; writes the grand
+// total to out_total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint32_t* __restrict__ bsum,
+                                                            uint64_t nb,
+                                                            uint32_t* __restrict__ out_total) {
+  __shared__ uint32_t warp_tot[kScanThreads / 32];
+  __shared__ uint32_t carry_s;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint64_t c0 = 0; c0 < nb; c0 += kScanThreads) {
+    const uint64_t i = c0 + threadIdx.x;
+    const uint32_t v = (i < nb) ? bsum[i] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const uint32_t w = warp_tot[lane];
+      uint32_t wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      warp_tot[lane] = wi - w;
+    }
+    __syncthreads();
+    const uint32_t carry = carry_s;
+    if (i < nb) bsum[i] = carry + warp_tot[wid] + incl - v;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry_s = carry + warp_tot[wid] + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out_total = carry_s;
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, const uint32_t* __restrict__ bsum,
+                           uint64_t n) {
+  const uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (i < n) out[i] += bsum[i / kScanTile];
+}
+
+template <bool kFP32>
+__global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
+                          const uint32_t* __restrict__ keys, const uint32_t* __restrict__ ranks,
+                          const uint32_t* __restrict__ starts, void* __restrict__ rec,
+                          uint32_t* __restrict__ skey) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t key = keys[i];
+  if (key == kInvalidKey) return;
+  double s[3];
+  int cell[3];
+  particle_cell(g, x + 3 * i, s, cell);
+  const uint32_t pos = starts[key] + ranks[i];
+  // offset from the cell's first node; exact in FP64 (both terms within a factor 2 or cell 0)
+  const double u0 = s[0] - static_cast<double>(cell[0] * g.kc[0]);
+  const double u1 = s[1] - static_cast<double>(cell[1] * g.kc[1]);
+  const double u2 = s[2] - static_cast<double>(cell[2] * g.kc[2]);
+  if (kFP32) {
+    reinterpret_cast<float4*>(rec)[pos] =
+        make_float4(static_cast<float>(u0), static_cast<float>(u1), static_cast<float>(u2),
+                    __int_as_float(static_cast<int>(i)));
+  } else {
+    Rec64 r;
+    r.u[0] = u0;
+    r.u[1] = u1;
+    r.u[2] = u2;
+    r.idx = static_cast<long long>(i);
+    reinterpret_cast<Rec64*>(rec)[pos] = r;
+  }
+  skey[pos] = key;
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+  return static_cast<unsigned>((n + threads - 1) / threads);
+}
+
+}  // namespace
+
+void launch_bin(const p3m_ctx* c, const double* x, int64_t n, double* f_zero) {
+  cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * c->nkeys, c->stream);
+  if (n == 0) return;
+  k_bin<<<grid_for(n, kBinThreads), kBinThreads, 0, c->stream>>>(c->g, x, n, c->counts, c->keys,
+                                                                  c->ranks, c->err_dev, f_zero);
+}
+
+void launch_scan(const p3m_ctx* c) {
+  const uint64_t n = c->nkeys;
+  const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<static_cast<unsigned>(tiles), kScanThreads, 0, c->stream>>>(c->counts, c->starts,
+                                                                             c->bsum, n);
+  k_scan_sums<<<1, kScanThreads, 0, c->stream>>>(c->bsum, tiles, c->starts + n);
+  k_scan_add<<<static_cast<unsigned>((n + 255) / 256), 256, 0, c->stream>>>(c->starts, c->bsum,
+                                                                            n);
+}
+
+void launch_scatter(const p3m_ctx* c, const double* x, int64_t n) {
+  if (n == 0) return;
+  if (c->fp32)
+    k_scatter<true><<<grid_for(n, kBinThreads), kBinThreads, 0, c->stream>>>(
+        c->g, x, n, c->keys, c->ranks, c->starts, c->rec, c->skey);
+  else
+    k_scatter<false><<<grid_for(n, kBinThreads), kBinThreads, 0, c->stream>>>(
+        c->g, x, n, c->keys, c->ranks, c->starts, c->rec, c->skey);
+}
+
+}  // namespace p3m

@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element,
+on the same seeded inputs.
+
+Tolerances (relative L2 over all components): FP64 path 1e-12, FP32 mixed path 1e-5; the
+in-cutoff pair count is an integer decided in FP64 on both sides and must match exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2103_02046_gb300 import bunches as B
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+def p3m():
+    from paper_2103_02046_gb300 import p3m as m
+    return m
+
+
+def gpu_params(P: O.Params, precision: int, **kw):
+    m = p3m()
+    return m.Params(n=P.n, lo=P.lo, h=P.h, rc_over_h=P.rc_over_h, kappa=P.kappa, alpha=P.alpha,
+                    assign_order=P.assign_order, pm_bc=P.pm_bc, pp_bc=P.pp_bc,
+                    z_cathode=P.z_cathode, influence=P.influence, precision=precision,
+                    q=P.q, mass=P.mass, **kw)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def rel(a, b):
+    return O.rel_l2(a.cpu().numpy() if torch.is_tensor(a) else a, b)
+
+
+def bunch_4k(cathode: bool):
+    x = B.gaussian(4096, (1e-3, 1e-3, 1e-3), 0)
+    if cathode:
+        x = B.lift_to_plane(x, 0.0, 0.15e-3)
+    return x
+
+
+CASES = [
+    # (name, n, pm_bc, pp_bc, order, influence)
+    ("open_tsc", 16, 0, 0, 2, 0),
+    ("cathode_tsc", 16, 1, 0, 2, 0),
+    ("cathode_pp_bc", 16, 1, 1, 2, 0),
+    ("open_cic", 16, 0, 0, 1, 0),
+    ("cathode_influence", 16, 1, 0, 2, 1),
+    ("aniso_ragged", (16, 20, 24), 1, 1, 2, 0),
+]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_forces_parity(case, precision):
+    name, n, pm_bc, pp_bc, order, infl = case
+    x = bunch_4k(pm_bc == 1)
+    if name == "aniso_ragged":
+        x = x[:3001] * np.array([1.0, 1.3, 0.7])
+    P = O.auto_mesh(x, n, rc_over_h=2.0, pm_bc=pm_bc, pp_bc=pp_bc, assign_order=order,
+                    influence=infl, z_cathode=0.0)
+    ref = O.forces(x, P)
+    ctx = p3m().Context(gpu_params(P, precision), len(x))
+    xg = cuda(x)
+    f_pp = ctx.forces(xg, parts=1)
+    np_gpu, ni_gpu = ctx.pair_count()
+    f_pm = ctx.forces(xg, parts=2)
+    f, e = ctx.forces(xg, energy=True)
+    ctx.sync()
+    tol = TOL[precision]
+    assert rel(f_pp, ref.F_pp) <= tol
+    assert rel(f_pm, ref.F_pm) <= tol
+    assert rel(f, ref.F) <= tol
+    if precision == 0:
+        assert (np_gpu, ni_gpu) == (ref.pairs, ref.image_pairs)
+    else:
+        assert abs(np_gpu - ref.pairs) <= max(2, 1e-5 * ref.pairs)
+    e = e.cpu().numpy()
+    assert e[0] == pytest.approx(ref.U_pp, rel=10 * tol)
+    assert e[1] == pytest.approx(ref.U_pm, rel=10 * tol)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mesh_charge_and_potential(precision):
+    x = bunch_4k(True)
+    P = O.auto_mesh(x, 16, pm_bc=1, z_cathode=0.0)
+    Q, _ = O.deposit(x, P)
+    phi = O.solve(Q, P)
+    ctx = p3m().Context(gpu_params(P, precision), len(x))
+    ctx.deposit(cuda(x))
+    Qg = ctx.get_mesh(0)
+    ctx.solve()
+    phig = ctx.get_mesh(1)
+    ctx.sync()
+    assert rel(Qg, Q) <= (1e-14 if precision == 0 else 1e-6)
+    assert rel(phig, phi) <= (1e-13 if precision == 0 else 1e-5)
+    assert float(Qg.sum()) == pytest.approx(len(x) * P.q, rel=1e-12 if precision == 0 else 1e-6)
+
+
+def test_auto_mesh_matches_oracle():
+    m = p3m()
+    x = B.gaussian(5000, (1e-3, 2e-3, 3e-3), 21)
+    for n in (16, (16, 24, 32)):
+        P = O.auto_mesh(x, n)
+        g = m.auto_mesh(cuda(x), m.Params(n=P.n))
+        assert tuple(g.h) == P.h and tuple(g.lo) == P.lo
+
+
+def test_edge_cases():
+    m = p3m()
+    x = bunch_4k(True)
+    P = O.auto_mesh(x, 16, pm_bc=1, z_cathode=0.0)
+    ctx = m.Context(gpu_params(P, 0), 100)
+    # empty input
+    f0 = ctx.forces(torch.zeros((0, 3), dtype=torch.float64, device="cuda"))
+    assert f0.shape == (0, 3)
+    # a single particle: no pairs; long-range self force only
+    x1 = x[:1]
+    f1 = ctx.forces(cuda(x1))
+    ref = O.forces(x1, P)
+    assert rel(f1, ref.F) <= 1e-12
+    # n > n_max is refused on the host
+    with pytest.raises(m.P3MError) as ei:
+        ctx.forces(cuda(x[:101]))
+    assert ei.value.status == m.P3M_EINVAL
+    # a particle outside the mesh: its force is zero and the error surfaces on sync
+    xb = x[:50].copy()
+    xb[7, 0] = P.lo[0] - 1e-3
+    fb = ctx.forces(cuda(xb))
+    with pytest.raises(m.P3MError) as ei:
+        ctx.sync()
+    assert ei.value.status == m.P3M_ERANGE
+    assert torch.all(fb[7] == 0)
+    good = np.delete(xb, 7, axis=0)
+    ref = O.forces(good, P)
+    assert rel(torch.cat([fb[:7], fb[8:]]), ref.F) <= 1e-12
+    # the context stays usable
+    f2 = ctx.forces(cuda(x[:64]))
+    ctx.sync()
+    assert rel(f2, O.forces(x[:64], P).F) <= 1e-12
+    # a particle below the cathode plane is out of range too
+    xc = x[:10].copy()
+    xc[3, 2] = -0.01e-3
+    ctx.forces(cuda(xc))
+    with pytest.raises(m.P3MError):
+        ctx.sync()
+    # NaN positions
+    xn = x[:10].copy()
+    xn[2, 1] = np.nan
+    ctx.forces(cuda(xn))
+    with pytest.raises(m.P3MError) as ei:
+        ctx.sync()
+    assert ei.value.status == m.P3M_EINVAL
+
+
+def test_invalid_params_refused():
+    m = p3m()
+    for bad in (dict(n=(4, 16, 16)), dict(assign_order=3), dict(h=(0.0, 1e-5, 1e-5)),
+                dict(precision=7), dict(q=0.0)):
+        with pytest.raises(m.P3MError) as ei:
+            m.Context(m.Params(**bad), 10)
+        assert ei.value.status == m.P3M_EINVAL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_push_parity(precision):
+    x = B.gaussian(2048, (1e-3, 1e-3, 2e-3), 22)
+    p = B.thermal_momenta(2048, 1e-4 * B.macro_mass() * B.SPEED_OF_LIGHT, 23)
+    P = O.auto_mesh(x * 1.2, 16, rc_over_h=2.0)
+    kern = O.green_kernels(P)
+    xT, pT, fT = O.push(x, p, 1e-12, 10, P, force=lambda y: O.forces(y, P, kernels=kern).F)
+    ctx = p3m().Context(gpu_params(P, precision), len(x))
+    xg, pg = cuda(x), cuda(p)
+    fg = ctx.push(xg, pg, 1e-12, 10)
+    ctx.sync()
+    tol = TOL[precision]
+    assert rel(xg - cuda(x), xT - x) <= 10 * tol
+    assert rel(pg, pT) <= 10 * tol
+    assert rel(fg, fT) <= 10 * tol
+
+
+def test_emittance_parity():
+    x = B.gaussian(3000, (1e-3, 2e-3, 3e-3), 24)
+    p = B.thermal_momenta(3000, 1e-24, 25) + 1e-21 * x
+    P = O.Params()
+    ctx = p3m().Context(p3m().Params(n=(8, 8, 8), h=(1e-3,) * 3), 3000)
+    eps, gx, gp = ctx.emittance(cuda(x), cuda(p), grad=True)
+    ogx, ogp = O.emittance_grad(x, p, P)
+    assert rel(eps, O.emittance(x, p, P)) <= 1e-12
+    assert rel(gx, ogx) <= 1e-11
+    assert rel(gp, ogp) <= 1e-11
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("bc", [(0, 0), (1, 1)])
+def test_force_vjp_parity(precision, bc):
+    pm_bc, pp_bc = bc
+    x = B.lift_to_plane(B.gaussian(1024, (1e-3, 1e-3, 1e-3), 26), 0.0, 0.1e-3)
+    P = O.auto_mesh(x, 16, rc_over_h=2.0, pm_bc=pm_bc, pp_bc=pp_bc, z_cathode=0.0)
+    w = np.random.default_rng(27).standard_normal(x.shape)
+    ref = O.force_vjp(x, w, P)
+    ctx = p3m().Context(gpu_params(P, precision), len(x))
+    g = ctx.force_vjp(cuda(x), cuda(w))
+    ctx.sync()
+    assert rel(g, ref) <= (1e-11 if precision == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_backward_parity(precision):
+    x0 = B.gaussian(512, (1e-3, 1e-3, 2e-3), 28)
+    p0 = B.thermal_momenta(512, 1e-4 * B.macro_mass() * B.SPEED_OF_LIGHT, 29)
+    P = O.auto_mesh(x0 * 1.3, 16, rc_over_h=2.0)
+    kern = O.green_kernels(P)
+    dt, T = 2e-12, 7
+    xT, pT, _ = O.push(x0, p0, dt, T, P, force=lambda y: O.forces(y, P, kernels=kern).F)
+    gxT, gpT = O.emittance_grad(xT, pT, P)
+    ogx, ogp = O.backward(x0, p0, dt, T, gxT, gpT, P, kern)
+    ctx = p3m().Context(gpu_params(P, precision, adj_slots=3, adj_segment=3), len(x0))
+    gx0, gp0 = ctx.backward(cuda(x0), cuda(p0), dt, T, cuda(gxT), cuda(gpT))
+    ctx.sync()
+    tol = 1e-10 if precision == 0 else 1e-4
+    assert rel(gx0, ogx) <= tol
+    assert rel(gp0, ogp) <= tol
+
+
+def test_autograd_emittance_gradient():
+    m = p3m()
+    x0 = B.gaussian(256, (1e-3, 1e-3, 2e-3), 30)
+    p0 = B.thermal_momenta(256, 1e-4 * B.macro_mass() * B.SPEED_OF_LIGHT, 31)
+    P = O.auto_mesh(x0 * 1.3, 16, rc_over_h=2.0)
+    kern = O.green_kernels(P)
+    dt, T = 2e-12, 4
+    ctx = m.Context(gpu_params(P, 0, adj_slots=2, adj_segment=2), len(x0))
+    xg = cuda(x0).requires_grad_(True)
+    pg = cuda(p0).requires_grad_(True)
+    xT, pT = m.P3MRun.apply(xg, pg, ctx, dt, T)
+    J = m.Emittance.apply(xT, pT, ctx)
+    J.backward()
+    xT_o, pT_o, _ = O.push(x0, p0, dt, T, P, force=lambda y: O.forces(y, P, kernels=kern).F)
+    gxT, gpT = O.emittance_grad(xT_o, pT_o, P)
+    ogx, ogp = O.backward(x0, p0, dt, T, gxT, gpT, P, kern)
+    assert float(J) == pytest.approx(O.emittance(xT_o, pT_o, P).sum(), rel=1e-12)
+    assert rel(xg.grad, ogx) <= 1e-10
+    assert rel(pg.grad, ogp) <= 1e-10
