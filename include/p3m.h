@@ -54,7 +54,7 @@ typedef enum { P3M_FP64 = 0, P3M_FP32_MIXED = 1 } p3m_precision;
 
 /* Problem statement (Sec. 2.4: macro-particles, mesh; Sec. 2.2: split; Sec. 3.1: cathode). */
 typedef struct p3m_params {
-  int32_t n[3];          /* mesh nodes per axis, x, y, z (each >= 8) */
+  int32_t n[3];          /* mesh nodes per axis, x, y, z (each in [8, 1024]) */
   double lo[3];          /* position of node 0 [m]; node g sits at lo + g*h (Sec. 2.4.2) */
   double h[3];           /* mesh spacing per axis [m] */
   double rc_over_h;      /* short-range cutoff r_c = rc_over_h * max_d h_d */

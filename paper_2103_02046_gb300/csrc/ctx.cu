@@ -40,7 +40,7 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 p3m_status validate(const p3m_params* p, std::string* why) {
   for (int d = 0; d < 3; ++d) {
-    if (p->n[d] < 8 || p->n[d] > 4096) { *why = "mesh n must be in [8, 4096] per axis"; return P3M_EINVAL; }
+    if (p->n[d] < 8 || p->n[d] > kMaxMesh) { *why = "mesh n must be in [8, 1024] per axis"; return P3M_EINVAL; }
     if (!finite_pos(p->h[d])) { *why = "mesh spacing h must be finite and > 0"; return P3M_EINVAL; }
     if (!std::isfinite(p->lo[d])) { *why = "mesh origin lo must be finite"; return P3M_EINVAL; }
   }
@@ -58,7 +58,7 @@ p3m_status validate(const p3m_params* p, std::string* why) {
   return P3M_OK;
 }
 
-Geom make_geom(const p3m_params* p) {
+Geom make_geom(const p3m_params* p, int64_t n_max) {
   Geom g{};
   double hmax = 0.0;
   for (int d = 0; d < 3; ++d) {
@@ -71,20 +71,33 @@ Geom make_geom(const p3m_params* p) {
   g.rc = p->rc_over_h * hmax;
   g.alpha = p->alpha > 0.0 ? p->alpha : p->kappa / g.rc;
   g.kappa_eff = g.alpha * g.rc;
+  // cells: y and z edges a hair above r_c (so a pair closer than r_c is never two cells apart
+  // after rounding); x edges r_c / nsub, nsub = 4 unless that makes too many cells
+  const double edge = 1.0 + 1e-9;
+  double ext[3];
   for (int d = 0; d < 3; ++d) {
-    int kc = static_cast<int>(std::ceil(g.rc / g.h[d]));
-    if (kc < 1) kc = 1;
-    while (kc * g.h[d] < g.rc) ++kc;  // cell edge must reach the cutoff
-    g.kc[d] = kc;
-    g.nc[d] = (g.n[d] - 2) / kc + 1;
-    g.nb[d] = (g.nc[d] + 3) / 4;
     g.a[d] = g.h[d] / g.rc;
+    ext[d] = (g.n[d] - 1) * g.a[d];
+  }
+  int nsub = 4;
+  const double cap = std::max<double>(4.0 * static_cast<double>(n_max), 1 << 20);
+  for (;;) {
+    g.cw[0] = edge / nsub;
+    g.cw[1] = g.cw[2] = edge;
+    double cells = 1.0;
+    for (int d = 0; d < 3; ++d) {
+      g.inv_cw[d] = 1.0 / g.cw[d];
+      g.nc[d] = static_cast<int>(std::floor(ext[d] * g.inv_cw[d])) + 1;
+      cells *= g.nc[d];
+    }
+    if (cells <= cap || nsub == 1) break;
+    nsub /= 2;
   }
   g.order = p->assign_order;
   g.pm_bc = p->pm_bc;
   g.pp_bc = p->pp_bc;
   g.zc = p->z_cathode;
-  g.s_cath = (p->z_cathode - p->lo[2]) / p->h[2];
+  g.img_c = 2.0 * (p->z_cathode - p->lo[2]) / g.rc;
   g.q = p->q;
   g.mass = p->mass;
   g.ke = 1.0 / (4.0 * kPi * kEps0);
@@ -99,7 +112,7 @@ cudaError_t alloc(T** ptr, size_t count) {
 }
 
 void free_all(p3m_ctx* c) {
-  void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->skey, c->rec, c->fpp,
+  void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recl, c->recm, c->fpp,
                   c->acc, c->qpad, c->qhat, c->khat_f, c->khat_i, c->fhat, c->freal,
                   c->phihat, c->phireal, c->dfac, c->energy_acc, c->pair_acc, c->err_dev,
                   c->ckpt, c->seg, c->lam_x, c->lam_p, c->xw, c->pw, c->tmp3, c->tmp3b,
@@ -326,13 +339,13 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   if (n_max < 1 || n_max > 2147483647LL) return P3M_EINVAL;
   auto* c = new p3m_ctx();
   c->prm = *params;
-  c->g = make_geom(params);
+  c->g = make_geom(params, n_max);
   c->n_max = n_max;
   c->fp32 = params->precision == P3M_FP32_MIXED;
   c->stream = static_cast<cudaStream_t>(stream);
   cudaGetDevice(&c->device);
   const Geom& g = c->g;
-  c->nkeys = static_cast<uint64_t>(g.nb[0]) * g.nb[1] * g.nb[2] * kBrickCells;
+  c->nkeys = static_cast<uint64_t>(g.nc[0]) * g.nc[1] * g.nc[2];
   if (c->nkeys >= 0xFFFFFFF0ull) {
     delete c;
     return P3M_EINVAL;
@@ -350,8 +363,9 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   A(alloc(&c->bsum, tiles));
   A(alloc(&c->keys, n_max));
   A(alloc(&c->ranks, n_max));
-  A(alloc(&c->skey, n_max));
-  A(cudaMalloc(&c->rec, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
+  A(cudaMalloc(&c->recp, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
+  A(cudaMalloc(&c->recm, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
+  if (c->fp32) A(alloc(&c->recl, n_max));
   A(cudaMalloc(&c->fpp, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
   A(alloc(&c->acc, 3 * n_max));
   A(cudaMalloc(&c->qpad, es * c->n_real));

@@ -1,14 +1,19 @@
 // Internal declarations of the GB300 P3M library (not part of the C ABI).
 //
-// Data layout in HBM (one context, up to n_max particles, mesh n = (nx, ny, nz)):
-//   * particles are binned into cells of kc_d mesh spacings per axis (kc_d h_d >= r_c), cells
-//     grouped into 4x4x4 bricks; the cell key is brick-major so that a brick's particles are
-//     contiguous after the counting sort.
-//   * sorted records: FP32 float4 {u_x, u_y, u_z, bits(original index)} or FP64
-//     {u_x, u_y, u_z, original index}, where u_d is the position in mesh units relative to the
-//     cell's first node (u_d in [0, kc_d)). Cell-local offsets keep FP32 positions accurate
-//     to ~1e-7 of a mesh spacing wherever the bunch sits.
-//   * mesh arrays use the doubled (2n)^3 layout of the FFT convolution, x fastest:
+// Data layout in HBM (one context, up to n_max particles, mesh n = (nx, ny, nz), n_d <= 1024):
+//   * Cells for the short-range search are rows along x: edge >= r_c in y and z, r_c / nsub in x,
+//     keys x-fastest, so the cells of one (y, z) row within any x-interval hold a contiguous run
+//     of sorted particles. Each neighbour row of a particle is then one pruned index range.
+//   * Sorted records (counting sort by cell key):
+//       recp  positions in cutoff units from the mesh origin, (x - lo) / r_c:
+//             FP32 float4 {hi_x, hi_y, hi_z, bits(original index)}, FP64 {x, y, z, index};
+//       recl  FP32 only: float4 {lo_x, lo_y, lo_z, 0}, the rounding remainders, so that
+//             (hi_i - hi_j) + (lo_i - lo_j) is the separation to FP32 relative accuracy
+//             however close the pair is;
+//       recm  assignment data in mesh units: the node c = floor(s + 1/2) (TSC) or floor(s)
+//             (CIC) packed 10 bits per axis, and the offset u = s - c, s = (x - lo) / h, computed
+//             in FP64 exactly as the definition reads (FP32 float4 or FP64 {u, node}).
+//   * Mesh arrays use the doubled (2n)^3 layout of the FFT convolution, x fastest:
 //     index (gz * My + gy) * Mx + gx; half spectra have Mx/2 + 1 entries along x.
 #pragma once
 
@@ -23,8 +28,7 @@
 namespace p3m {
 
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
-constexpr int kBrickShift = 2;  // 4 cells per brick edge
-constexpr int kBrickCells = 64;
+constexpr int kMaxMesh = 1024;
 
 enum ErrBits : int { kErrRange = 1, kErrNaN = 2, kErrTimeout = 4 };
 
@@ -32,33 +36,26 @@ enum ErrBits : int { kErrRange = 1, kErrNaN = 2, kErrTimeout = 4 };
 struct Geom {
   int n[3];      // mesh nodes per axis
   int M[3];      // doubled mesh 2 n
-  int kc[3];     // cell edge in mesh spacings
   int nc[3];     // cells per axis
-  int nb[3];     // bricks per axis
   int order;     // 1 CIC, 2 TSC
   int pm_bc, pp_bc;
   double lo[3], h[3];
   double rc, alpha, zc;
-  double s_cath;  // cathode plane in mesh units along z: (zc - lo_z) / h_z
   double q, mass, ke;
-  double a[3];    // h_d / r_c: mesh units -> cutoff units
+  double a[3];       // h_d / r_c
+  double cw[3];      // cell edges in cutoff units (y, z: >= 1; x: 1 / nsub)
+  double inv_cw[3];
+  double img_c;      // 2 (z_c - lo_z) / r_c: the image of z (cutoff units) is img_c - z
   double kappa_eff;  // alpha * r_c
 };
 
 __host__ __device__ inline uint32_t cell_key(const Geom& g, int cx, int cy, int cz) {
-  const uint32_t b = (static_cast<uint32_t>(cz >> kBrickShift) * g.nb[1] + (cy >> kBrickShift)) *
-                         g.nb[0] + (cx >> kBrickShift);
-  return b * kBrickCells + static_cast<uint32_t>(((cz & 3) * 4 + (cy & 3)) * 4 + (cx & 3));
+  return (static_cast<uint32_t>(cz) * g.nc[1] + cy) * g.nc[0] + cx;
 }
 
-__host__ __device__ inline void cell_decode(const Geom& g, uint32_t key, int& cx, int& cy,
-                                            int& cz) {
-  const uint32_t b = key >> 6, l = key & 63u;
-  const uint32_t bx = b % g.nb[0], t = b / g.nb[0];
-  const uint32_t by = t % g.nb[1], bz = t / g.nb[1];
-  cx = static_cast<int>(bx * 4 + (l & 3u));
-  cy = static_cast<int>(by * 4 + ((l >> 2) & 3u));
-  cz = static_cast<int>(bz * 4 + (l >> 4));
+__host__ __device__ inline uint32_t pack_node(int cx, int cy, int cz) {
+  return static_cast<uint32_t>(cx) | (static_cast<uint32_t>(cy) << 10) |
+         (static_cast<uint32_t>(cz) << 20);
 }
 
 struct Rec64 {
@@ -122,8 +119,9 @@ struct p3m_ctx {
   uint32_t* bsum = nullptr;     // scan block sums
   uint32_t* keys = nullptr;     // [n_max] key of each input particle
   uint32_t* ranks = nullptr;    // [n_max] rank within its cell
-  uint32_t* skey = nullptr;     // [n_max] key of each sorted particle
-  void* rec = nullptr;          // [n_max] sorted records (float4 or Rec64)
+  void* recp = nullptr;         // [n_max] sorted positions, cutoff units (float4 hi / Rec64)
+  float4* recl = nullptr;       // [n_max] FP32: rounding remainders of recp
+  void* recm = nullptr;         // [n_max] sorted assignment records (float4 / Rec64)
   void* fpp = nullptr;          // [n_max] short-range force + potential, sorted (float4/double4)
   double* acc = nullptr;        // [3 n_max] adjoint accumulator, sorted order
 

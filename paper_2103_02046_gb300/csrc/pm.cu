@@ -116,12 +116,11 @@ struct Axis {
 };
 
 template <typename T>
-__device__ __forceinline__ Axis<T> axis_weights(int order, int cell_node, T u) {
+__device__ __forceinline__ Axis<T> axis_weights(int order, int c, T f) {
+  // c: TSC nearest node (f = s - c in [-1/2, 1/2]) or CIC lower node (f in [0, 1))
   Axis<T> a;
   if (order == 2) {
-    const T t = floor(u + T(0.5));
-    const T f = u - t;
-    a.c = cell_node + static_cast<int>(t) - 1;
+    a.c = c - 1;
     const T l = T(0.5) - f, r = T(0.5) + f;
     a.w[0] = T(0.5) * l * l;
     a.w[1] = T(0.75) - f * f;
@@ -132,9 +131,7 @@ __device__ __forceinline__ Axis<T> axis_weights(int order, int cell_node, T u) {
     a.gl = l;
     a.gr = r;
   } else {
-    const T t = floor(u);
-    const T f = u - t;
-    a.c = cell_node + static_cast<int>(t);
+    a.c = c;
     a.w[0] = T(1) - f;
     a.w[1] = f;
     a.w[2] = T(0);
@@ -147,62 +144,135 @@ __device__ __forceinline__ Axis<T> axis_weights(int order, int cell_node, T u) {
   return a;
 }
 
+__device__ __forceinline__ void load_m(const float4* recm, uint32_t i, float u[3], uint32_t& node) {
+  const float4 r = recm[i];
+  u[0] = r.x;
+  u[1] = r.y;
+  u[2] = r.z;
+  node = __float_as_uint(r.w);
+}
+__device__ __forceinline__ void load_m(const Rec64* recm, uint32_t i, double u[3], uint32_t& node) {
+  const Rec64 r = recm[i];
+  u[0] = r.u[0];
+  u[1] = r.u[1];
+  u[2] = r.u[2];
+  node = static_cast<uint32_t>(r.idx);
+}
+
 template <typename T>
-__device__ __forceinline__ void particle_axes(const Geom& g, const typename RecT<T>::type* rec,
-                                              const uint32_t* skey, uint32_t i, Axis<T> ax[3],
-                                              long long& idx) {
+__device__ __forceinline__ void particle_axes(const Geom& g, const typename RecT<T>::type* recm,
+                                              uint32_t i, Axis<T> ax[3]) {
   T u[3];
-  load_rec(rec, i, u, idx);
-  int cx, cy, cz;
-  cell_decode(g, skey[i], cx, cy, cz);
-  ax[0] = axis_weights<T>(g.order, cx * g.kc[0], u[0]);
-  ax[1] = axis_weights<T>(g.order, cy * g.kc[1], u[1]);
-  ax[2] = axis_weights<T>(g.order, cz * g.kc[2], u[2]);
+  uint32_t node;
+  load_m(recm, i, u, node);
+  ax[0] = axis_weights<T>(g.order, static_cast<int>(node & 1023u), u[0]);
+  ax[1] = axis_weights<T>(g.order, static_cast<int>((node >> 10) & 1023u), u[1]);
+  ax[2] = axis_weights<T>(g.order, static_cast<int>(node >> 20), u[2]);
 }
 
-template <typename T>
-__global__ void k_deposit(Geom g, const uint32_t* __restrict__ total,
-                          const typename RecT<T>::type* __restrict__ rec,
-                          const uint32_t* __restrict__ skey, T* __restrict__ qpad) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *total) return;
-  Axis<T> ax[3];
-  long long idx;
-  particle_axes<T>(g, rec, skey, i, ax, idx);
-  const int S = g.order == 2 ? 3 : 2;
-  for (int c = 0; c < S; ++c)
-    for (int b = 0; b < S; ++b) {
-      const T wyz = ax[1].w[b] * ax[2].w[c];
-      T* row = qpad + real_index(g, ax[0].c, ax[1].c + b, ax[2].c + c);
-      for (int a = 0; a < S; ++a) atomicAdd(row + a, ax[0].w[a] * wyz);
-    }
+__device__ __forceinline__ long long orig_index(const float4* recp, uint32_t i) {
+  return __float_as_int(recp[i].w);
+}
+__device__ __forceinline__ long long orig_index(const Rec64* recp, uint32_t i) {
+  return recp[i].idx;
 }
 
-// psi_g = sum_i grad_xi W(x_g - xi_i) . w_i  (adjoint of the assignment feeding the solve)
-template <typename T>
-__global__ void k_dipole_deposit(Geom g, const uint32_t* __restrict__ total,
-                                 const typename RecT<T>::type* __restrict__ rec,
-                                 const uint32_t* __restrict__ skey, const double* __restrict__ w,
-                                 T* __restrict__ qpad) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *total) return;
-  Axis<T> ax[3];
-  long long idx;
-  particle_axes<T>(g, rec, skey, i, ax, idx);
-  const T w0 = static_cast<T>(w[3 * idx] / g.h[0]);
-  const T w1 = static_cast<T>(w[3 * idx + 1] / g.h[1]);
-  const T w2 = static_cast<T>(w[3 * idx + 2] / g.h[2]);
+// ---------------------------------------------------------------------------------------------
+// Charge assignment with a shared-memory tile: a block takes kDepPerBlock consecutive sorted
+// particles (one stretch of an x-row of cells, so their supports overlap heavily), sums their
+// weights into a tile of the mesh covering the block's bounding box, then adds the non-zero tile
+// entries to the mesh with one global atomic each. Blocks whose box does not fit the tile fall
+// back to global atomics per weight.
+// ---------------------------------------------------------------------------------------------
+constexpr int kDepThreads = 256;
+constexpr int kDepItems = 4;
+constexpr int kDepPerBlock = kDepThreads * kDepItems;
+constexpr int kTileBytes = 32768;
+
+template <typename T, bool kDipole>
+__global__ void __launch_bounds__(kDepThreads)
+    k_deposit_tiled(Geom g, const uint32_t* __restrict__ total,
+                    const typename RecT<T>::type* __restrict__ recm,
+                    const typename RecT<T>::type* __restrict__ recp,
+                    const double* __restrict__ w, T* __restrict__ qpad) {
+  constexpr int kTile = kTileBytes / sizeof(T);
+  __shared__ T tile[kTile];
+  __shared__ int bmin[3], bmax[3];
+  const uint32_t N = *total;
+  const uint32_t b0 = blockIdx.x * kDepPerBlock;
+  if (b0 >= N) return;
   const int S = g.order == 2 ? 3 : 2;
-  for (int c = 0; c < S; ++c)
-    for (int b = 0; b < S; ++b) {
-      T* row = qpad + real_index(g, ax[0].c, ax[1].c + b, ax[2].c + c);
-      for (int a = 0; a < S; ++a) {
-        const T v = w0 * ax[0].dw[a] * ax[1].w[b] * ax[2].w[c] +
-                    w1 * ax[0].w[a] * ax[1].dw[b] * ax[2].w[c] +
-                    w2 * ax[0].w[a] * ax[1].w[b] * ax[2].dw[c];
-        atomicAdd(row + a, v);
+  if (threadIdx.x < 3) {
+    bmin[threadIdx.x] = 1 << 30;
+    bmax[threadIdx.x] = -1;
+  }
+  __syncthreads();
+  int lmin[3] = {1 << 30, 1 << 30, 1 << 30}, lmax[3] = {-1, -1, -1};
+#pragma unroll
+  for (int k = 0; k < kDepItems; ++k) {
+    const uint32_t i = b0 + k * kDepThreads + threadIdx.x;
+    if (i < N) {
+      Axis<T> ax[3];
+      particle_axes<T>(g, recm, i, ax);
+      for (int d = 0; d < 3; ++d) {
+        lmin[d] = min(lmin[d], ax[d].c);
+        lmax[d] = max(lmax[d], ax[d].c + S - 1);
       }
     }
+  }
+  for (int d = 0; d < 3; ++d) {
+    int a = lmin[d], b = lmax[d];
+    for (int o = 16; o > 0; o >>= 1) {
+      a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&bmin[d], a);
+      atomicMax(&bmax[d], b);
+    }
+  }
+  __syncthreads();
+  const int ex = bmax[0] - bmin[0] + 1, ey = bmax[1] - bmin[1] + 1, ez = bmax[2] - bmin[2] + 1;
+  const bool use_tile = static_cast<long long>(ex) * ey * ez <= kTile;
+  if (use_tile)
+    for (int t = threadIdx.x; t < ex * ey * ez; t += kDepThreads) tile[t] = T(0);
+  __syncthreads();
+  for (int k = 0; k < kDepItems; ++k) {
+    const uint32_t i = b0 + k * kDepThreads + threadIdx.x;
+    if (i >= N) continue;
+    Axis<T> A[3];
+    particle_axes<T>(g, recm, i, A);
+    T wv[3] = {T(0), T(0), T(0)};
+    if (kDipole) {
+      const long long idx = orig_index(recp, i);
+      for (int d = 0; d < 3; ++d) wv[d] = static_cast<T>(w[3 * idx + d] / g.h[d]);
+    }
+    for (int c = 0; c < S; ++c)
+      for (int b = 0; b < S; ++b)
+        for (int a = 0; a < S; ++a) {
+          T v;
+          if (kDipole)
+            v = wv[0] * A[0].dw[a] * A[1].w[b] * A[2].w[c] +
+                wv[1] * A[0].w[a] * A[1].dw[b] * A[2].w[c] +
+                wv[2] * A[0].w[a] * A[1].w[b] * A[2].dw[c];
+          else
+            v = A[0].w[a] * A[1].w[b] * A[2].w[c];
+          const int gx = A[0].c + a, gy = A[1].c + b, gz = A[2].c + c;
+          if (use_tile)
+            atomicAdd(&tile[((gz - bmin[2]) * ey + (gy - bmin[1])) * ex + (gx - bmin[0])], v);
+          else
+            atomicAdd(qpad + real_index(g, gx, gy, gz), v);
+        }
+  }
+  if (!use_tile) return;
+  __syncthreads();
+  for (int t = threadIdx.x; t < ex * ey * ez; t += kDepThreads) {
+    const T v = tile[t];
+    if (v != T(0)) {
+      const int gx = bmin[0] + t % ex, gy = bmin[1] + (t / ex) % ey, gz = bmin[2] + t / (ex * ey);
+      atomicAdd(qpad + real_index(g, gx, gy, gz), v);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -356,15 +426,15 @@ __device__ __forceinline__ void grad_from_phi(const Geom& g, const double* __res
 
 template <typename T>
 __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
-                         const typename RecT<T>::type* __restrict__ rec,
-                         const uint32_t* __restrict__ skey, const T* __restrict__ field,
+                         const typename RecT<T>::type* __restrict__ recm,
+                         const typename RecT<T>::type* __restrict__ recp, const T* __restrict__ field,
                          size_t nreal, const void* __restrict__ fpp, double* __restrict__ f,
                          int parts, double pp_scale) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
   Axis<T> ax[3];
-  long long idx;
-  particle_axes<T>(g, rec, skey, i, ax, idx);
+  particle_axes<T>(g, recm, i, ax);
+  const long long idx = orig_index(recp, i);
   double F[3] = {0.0, 0.0, 0.0};
   if (parts & 2) {
     T G[3];
@@ -464,15 +534,16 @@ __device__ void hess_from_phi(const Geom& g, const double* __restrict__ phi,
 
 template <typename T>
 __global__ void k_vjp_gather(Geom g, const uint32_t* __restrict__ total,
-                             const typename RecT<T>::type* __restrict__ rec,
-                             const uint32_t* __restrict__ skey, const T* __restrict__ field,
-                             size_t nreal, const double* __restrict__ w, double* __restrict__ acc,
+                             const typename RecT<T>::type* __restrict__ recm,
+                             const typename RecT<T>::type* __restrict__ recp,
+                             const T* __restrict__ field, size_t nreal,
+                             const double* __restrict__ w, double* __restrict__ acc,
                              double* __restrict__ out, int pass) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
   Axis<T> ax[3];
-  long long idx;
-  particle_axes<T>(g, rec, skey, i, ax, idx);
+  particle_axes<T>(g, recm, i, ax);
+  const long long idx = orig_index(recp, i);
   if (pass == 0) {
     T H[3][3];
     if constexpr (sizeof(T) == 4)
@@ -566,23 +637,28 @@ void launch_zero_block(const p3m_ctx* c) {
 void launch_deposit(const p3m_ctx* c, int64_t n) {
   if (n == 0) return;
   const uint32_t* total = c->starts + c->nkeys;
+  const unsigned blocks = static_cast<unsigned>((n + kDepPerBlock - 1) / kDepPerBlock);
   if (c->fp32)
-    k_deposit<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
-        c->g, total, static_cast<const float4*>(c->rec), c->skey, static_cast<float*>(c->qpad));
+    k_deposit_tiled<float, false><<<blocks, kDepThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp),
+        nullptr, static_cast<float*>(c->qpad));
   else
-    k_deposit<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
-        c->g, total, static_cast<const Rec64*>(c->rec), c->skey, static_cast<double*>(c->qpad));
+    k_deposit_tiled<double, false><<<blocks, kDepThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp),
+        nullptr, static_cast<double*>(c->qpad));
 }
 
 void launch_dipole_deposit(const p3m_ctx* c, int64_t n, const double* w) {
   if (n == 0) return;
   const uint32_t* total = c->starts + c->nkeys;
+  const unsigned blocks = static_cast<unsigned>((n + kDepPerBlock - 1) / kDepPerBlock);
   if (c->fp32)
-    k_dipole_deposit<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
-        c->g, total, static_cast<const float4*>(c->rec), c->skey, w, static_cast<float*>(c->qpad));
+    k_deposit_tiled<float, true><<<blocks, kDepThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp), w,
+        static_cast<float*>(c->qpad));
   else
-    k_dipole_deposit<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
-        c->g, total, static_cast<const Rec64*>(c->rec), c->skey, w,
+    k_deposit_tiled<double, true><<<blocks, kDepThreads, 0, c->stream>>>(
+        c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp), w,
         static_cast<double*>(c->qpad));
 }
 
@@ -609,11 +685,11 @@ void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts) {
   const double pp_scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc);
   if (c->fp32)
     k_interp<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
-        c->g, total, static_cast<const float4*>(c->rec), c->skey,
+        c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp),
         static_cast<const float*>(c->freal), c->n_real, c->fpp, f, parts, pp_scale);
   else
     k_interp<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
-        c->g, total, static_cast<const Rec64*>(c->rec), c->skey,
+        c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp),
         static_cast<const double*>(c->phireal), c->n_real, c->fpp, f, parts, pp_scale);
 }
 
@@ -622,11 +698,11 @@ void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, d
   const uint32_t* total = c->starts + c->nkeys;
   if (c->fp32)
     k_vjp_gather<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
-        c->g, total, static_cast<const float4*>(c->rec), c->skey,
+        c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp),
         static_cast<const float*>(c->freal), c->n_real, w, c->acc, out, pass);
   else
     k_vjp_gather<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
-        c->g, total, static_cast<const Rec64*>(c->rec), c->skey,
+        c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp),
         static_cast<const double*>(c->phireal), c->n_real, w, c->acc, out, pass);
 }
 

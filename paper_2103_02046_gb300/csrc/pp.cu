@@ -6,11 +6,18 @@
 // image of charge -q at S(xi_j) (its own image included) that acts through the same kernel.
 //
 // Work is in cutoff units (rho = r / r_c, kappa = a r_c): the force is
-// (k_e q^2 / r_c^2) P(kappa rho) rho_vec / rho^3 with P(x) = erfc(x) + (2x/sqrt(pi)) e^{-x^2}.
-// Positions are cell-local offsets, so FP32 differences keep ~1e-7 of r_c absolute accuracy.
-// The FP32 path sums each row of three neighbour cells in FP32 and folds the row sums into a
-// two-float (TwoSum) accumulator, which keeps the per-particle sum compensated at the cost of a
-// few additions per row instead of per pair.
+// (k_e q^2 / r_c^2) [erfc(kappa rho)/rho + (2 kappa/sqrt(pi)) e^{-kappa^2 rho^2}] rho_vec / rho^2.
+//
+// Search: cells are rows along x (>= r_c wide in y and z, r_c / nsub in x, keys x-fastest). For
+// particle i and each of the 3 x 3 neighbour rows, the distance d from i to the row's (y, z)
+// rectangle bounds |dx| < sqrt(1 - d^2), which selects one contiguous run of sorted particles.
+// Rows with d >= 1 are skipped. This visits about 13 r_c^3 of volume per particle instead of
+// the 27 r_c^3 of a plain 27-cell stencil.
+//
+// FP32: candidates are tested with the hi parts of the cutoff-unit positions; in-cutoff pairs
+// recompute the separation as (hi_i - hi_j) + (lo_i - lo_j), exact to FP32 relative rounding at
+// any distance. Row sums are accumulated in FP32 and folded into a two-float (TwoSum)
+// accumulator per row, so the per-particle sum is compensated at a few additions per row.
 #include <cmath>
 
 #include "p3m_internal.cuh"
@@ -19,11 +26,7 @@ namespace p3m {
 namespace {
 
 constexpr int kThreads = 128;
-
-template <typename T>
-struct Vec3 {
-  T x, y, z;
-};
+constexpr float kFilterSlack = 1e-4f;   // hi-only separations err by < 1e-5 r_c
 
 // two-float accumulator (hi + lo) with Knuth's TwoSum
 struct Acc2 {
@@ -83,7 +86,6 @@ struct SumT<double> {
   __device__ double get(int k) const { return v[k]; }
 };
 
-template <typename T>
 __device__ __forceinline__ void block_reduce_add(double v, double* dst) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __shared__ double ws[kThreads / 32];
@@ -101,113 +103,150 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long v, unsigned long
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
 }
 
-// One thread per sorted particle; the 27 neighbour cells are read through L1/L2.
-template <typename T>
+// Calls visit(j0, j1) for every neighbour row of the query point (px, py, pz) (cutoff units)
+// that can hold particles within distance 1, with [j0, j1) the sorted range of its cells whose
+// x-extent meets (px - w, px + w), w = sqrt(1 - d^2) (+ slack), d the point's distance to the
+// row's (y, z) rectangle.
+template <typename T, typename V>
+__device__ __forceinline__ void for_rows(const Geom& g, const uint32_t* __restrict__ starts, T px,
+                                         T py, T pz, V&& visit) {
+  const T slack = T(kFilterSlack);
+  const T cwy = static_cast<T>(g.cw[1]), cwz = static_cast<T>(g.cw[2]);
+  const T iwx = static_cast<T>(g.inv_cw[0]), iwy = static_cast<T>(g.inv_cw[1]),
+          iwz = static_cast<T>(g.inv_cw[2]);
+  const int y0 = max(static_cast<int>(floor((py - T(1) - slack) * iwy)), 0);
+  const int y1 = min(static_cast<int>(floor((py + T(1) + slack) * iwy)), g.nc[1] - 1);
+  const int z0 = max(static_cast<int>(floor((pz - T(1) - slack) * iwz)), 0);
+  const int z1 = min(static_cast<int>(floor((pz + T(1) + slack) * iwz)), g.nc[2] - 1);
+  for (int rz = z0; rz <= z1; ++rz) {
+    const T zl = static_cast<T>(rz) * cwz, zh = zl + cwz;
+    const T dz = pz < zl ? zl - pz : (pz > zh ? pz - zh : T(0));
+    for (int ry = y0; ry <= y1; ++ry) {
+      const T yl = static_cast<T>(ry) * cwy, yh = yl + cwy;
+      const T dy = py < yl ? yl - py : (py > yh ? py - yh : T(0));
+      const T d2 = dy * dy + dz * dz;
+      if (d2 >= T(1) + slack) continue;
+      const T w = sqrt(max(T(1) - d2, T(0))) + slack;
+      const int c0 = max(static_cast<int>(floor((px - w) * iwx)), 0);
+      const int c1 = min(static_cast<int>(floor((px + w) * iwx)), g.nc[0] - 1);
+      if (c0 > c1) continue;
+      const uint32_t base = (static_cast<uint32_t>(rz) * g.nc[1] + ry) * g.nc[0];
+      visit(starts[base + c0], starts[base + c1 + 1]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Position access: FP32 hi (+ lo remainder on demand), FP64 exact.
+// ------------------------------------------------------------------------------------------
+struct PosF {
+  const float4* __restrict__ hi;
+  const float4* __restrict__ lo;
+};
+struct PosD {
+  const Rec64* __restrict__ r;
+};
+
+// Short-range forces: one thread per sorted particle.
+template <typename T, typename Pos>
 __global__ void __launch_bounds__(kThreads)
-    k_pp(Geom g, const uint32_t* __restrict__ total, const typename RecT<T>::type* __restrict__ rec,
-         const uint32_t* __restrict__ skey, const uint32_t* __restrict__ starts,
+    k_pp(Geom g, const uint32_t* __restrict__ total, Pos pos, const uint32_t* __restrict__ starts,
          void* __restrict__ fpp, double* __restrict__ energy,
          unsigned long long* __restrict__ pairs) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t N = *total;
   const T kappa = static_cast<T>(g.kappa_eff);
   const T c2k = static_cast<T>(2.0 * g.kappa_eff * 0.56418958354775628695);
-  const T ax = static_cast<T>(g.a[0]), ay = static_cast<T>(g.a[1]), az = static_cast<T>(g.a[2]);
   double pot_out = 0.0;
   unsigned long long np = 0, ni = 0;
   if (i < N) {
-    T ui[3];
-    long long idx;
-    load_rec(rec + 0, i, ui, idx);
-    int cx, cy, cz;
-    cell_decode(g, skey[i], cx, cy, cz);
-    const T px = ui[0] * ax, py = ui[1] * ay, pz = ui[2] * az;
+    T pi[3], li[3] = {T(0), T(0), T(0)};
+    if constexpr (sizeof(T) == 4) {
+      const float4 h = pos.hi[i], l = pos.lo[i];
+      pi[0] = h.x; pi[1] = h.y; pi[2] = h.z;
+      li[0] = l.x; li[1] = l.y; li[2] = l.z;
+    } else {
+      const Rec64 r = pos.r[i];
+      pi[0] = r.u[0]; pi[1] = r.u[1]; pi[2] = r.u[2];
+    }
     SumT<T> sum;
     sum.zero();
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int nz = cz + dz;
-      if (nz < 0 || nz >= g.nc[2]) continue;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int ny = cy + dy;
-        if (ny < 0 || ny >= g.nc[1]) continue;
-        T row[4] = {T(0), T(0), T(0), T(0)};
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int nx = cx + dx;
-          if (nx < 0 || nx >= g.nc[0]) continue;
-          const uint32_t key = cell_key(g, nx, ny, nz);
-          const uint32_t j0 = starts[key], j1 = starts[key + 1];
-          const T sx = static_cast<T>(dx * g.kc[0]) * ax;
-          const T sy = static_cast<T>(dy * g.kc[1]) * ay;
-          const T sz = static_cast<T>(dz * g.kc[2]) * az;
+    for_rows<T>(g, starts, pi[0], pi[1], pi[2], [&](uint32_t j0, uint32_t j1) {
+      T row[4] = {T(0), T(0), T(0), T(0)};
+      for (uint32_t j = j0; j < j1; ++j) {
+        if (j == i) continue;
+        T rx, ry, rz, r2;
+        if constexpr (sizeof(T) == 4) {
+          const float4 hj = pos.hi[j];
+          rx = pi[0] - hj.x;
+          ry = pi[1] - hj.y;
+          rz = pi[2] - hj.z;
+          r2 = rx * rx + ry * ry + rz * rz;
+          if (!(r2 < T(1) + T(kFilterSlack))) continue;
+          const float4 lj = pos.lo[j];
+          rx += li[0] - lj.x;
+          ry += li[1] - lj.y;
+          rz += li[2] - lj.z;
+          r2 = rx * rx + ry * ry + rz * rz;
+        } else {
+          const Rec64 rj = pos.r[j];
+          rx = pi[0] - rj.u[0];
+          ry = pi[1] - rj.u[1];
+          rz = pi[2] - rj.u[2];
+          r2 = rx * rx + ry * ry + rz * rz;
+        }
+        if (r2 < T(1) && r2 > T(0)) {
+          T fco, pot;
+          pair_terms(r2, kappa, c2k, fco, pot);
+          row[0] += fco * rx;
+          row[1] += fco * ry;
+          row[2] += fco * rz;
+          row[3] += pot;
+          ++np;
+        }
+      }
+      sum.fold(row);
+    });
+    if (g.pp_bc) {
+      // images of the sources within r_c: the image of z_j is img_c - z_j; only particles less
+      // than r_c above the cathode can meet one
+      const double zi = static_cast<double>(pi[2]) + static_cast<double>(li[2]);
+      if (zi - 0.5 * g.img_c < 1.0) {
+        const T mz = static_cast<T>(g.img_c - zi);  // mirrored query point
+        const float ch = static_cast<float>(g.img_c);
+        const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
+        for_rows<T>(g, starts, pi[0], pi[1], mz, [&](uint32_t j0, uint32_t j1) {
+          T row[4] = {T(0), T(0), T(0), T(0)};
           for (uint32_t j = j0; j < j1; ++j) {
-            if (j == i) continue;
-            T uj[3];
-            long long jdx;
-            load_rec(rec, j, uj, jdx);
-            const T rx = px - (uj[0] * ax + sx);
-            const T ry = py - (uj[1] * ay + sy);
-            const T rz = pz - (uj[2] * az + sz);
+            T rx, ry, rz;
+            if constexpr (sizeof(T) == 4) {
+              const float4 hj = pos.hi[j], lj = pos.lo[j];
+              rx = (pi[0] - hj.x) + (li[0] - lj.x);
+              ry = (pi[1] - hj.y) + (li[1] - lj.y);
+              // z_i - (img_c - z_j) with an exact two-sum of the hi parts
+              const float s = pi[2] + hj.z;
+              const float bp = s - pi[2];
+              const float e = (pi[2] - (s - bp)) + (hj.z - bp);
+              rz = ((s - ch) + e) + ((li[2] + lj.z) - cl);
+            } else {
+              const Rec64 rj = pos.r[j];
+              rx = pi[0] - rj.u[0];
+              ry = pi[1] - rj.u[1];
+              rz = pi[2] + rj.u[2] - static_cast<T>(g.img_c);
+            }
             const T r2 = rx * rx + ry * ry + rz * rz;
             if (r2 < T(1) && r2 > T(0)) {
               T fco, pot;
               pair_terms(r2, kappa, c2k, fco, pot);
-              row[0] += fco * rx;
-              row[1] += fco * ry;
-              row[2] += fco * rz;
-              row[3] += pot;
-              ++np;
+              row[0] -= fco * rx;
+              row[1] -= fco * ry;
+              row[2] -= fco * rz;
+              row[3] -= pot;
+              ++ni;
             }
           }
-        }
-        sum.fold(row);
-      }
-    }
-    if (g.pp_bc) {
-      // images of the sources within r_c: only particles less than r_c above the cathode
-      const double szi = static_cast<double>(cz * g.kc[2]) + static_cast<double>(ui[2]);
-      const double above = (szi - g.s_cath) * g.h[2];
-      if (above < g.rc) {
-        const double mz = 2.0 * g.s_cath - szi;  // mirrored query point, mesh units
-        const double reach = g.rc / g.h[2];
-        int z0 = static_cast<int>(floor((mz - reach) / g.kc[2]));
-        int z1 = static_cast<int>(floor((mz + reach) / g.kc[2]));
-        z0 = max(z0, 0);
-        z1 = min(z1, g.nc[2] - 1);
-        for (int nz = z0; nz <= z1; ++nz) {
-          const T base = static_cast<T>(static_cast<double>((cz + nz) * g.kc[2]) - 2.0 * g.s_cath);
-          for (int dy = -1; dy <= 1; ++dy) {
-            const int ny = cy + dy;
-            if (ny < 0 || ny >= g.nc[1]) continue;
-            T row[4] = {T(0), T(0), T(0), T(0)};
-            for (int dx = -1; dx <= 1; ++dx) {
-              const int nx = cx + dx;
-              if (nx < 0 || nx >= g.nc[0]) continue;
-              const uint32_t key = cell_key(g, nx, ny, nz);
-              const uint32_t j0 = starts[key], j1 = starts[key + 1];
-              const T sx = static_cast<T>(dx * g.kc[0]) * ax;
-              const T sy = static_cast<T>(dy * g.kc[1]) * ay;
-              for (uint32_t j = j0; j < j1; ++j) {
-                T uj[3];
-                long long jdx;
-                load_rec(rec, j, uj, jdx);
-                const T rx = px - (uj[0] * ax + sx);
-                const T ry = py - (uj[1] * ay + sy);
-                const T rz = (base + ui[2] + uj[2]) * az;  // z_i - (2 z_c - z_j)
-                const T r2 = rx * rx + ry * ry + rz * rz;
-                if (r2 < T(1) && r2 > T(0)) {
-                  T fco, pot;
-                  pair_terms(r2, kappa, c2k, fco, pot);
-                  row[0] -= fco * rx;
-                  row[1] -= fco * ry;
-                  row[2] -= fco * rz;
-                  row[3] -= pot;
-                  ++ni;
-                }
-              }
-            }
-            sum.fold(row);
-          }
-        }
+          sum.fold(row);
+        });
       }
     }
     if constexpr (sizeof(T) == 4) {
@@ -218,16 +257,16 @@ __global__ void __launch_bounds__(kThreads)
     }
     pot_out = static_cast<double>(sum.get(3));
   }
-  if (energy) block_reduce_add<T>(pot_out, energy);
+  if (energy) block_reduce_add(pot_out, energy);
   warp_add_u64(np, pairs);
   warp_add_u64(ni, pairs + 1);
 }
 
-// Vector-Jacobian product of the short-range force map, accumulated into acc (sorted order):
+// Vector-Jacobian product of the short-range force map, into acc (sorted order):
 //   free pairs:  acc_i += H(d_ij) (w_i - w_j)
-//   image pairs: acc_i += H'(d_ij) (w_i - S w_j)   (H' of the -q image; S = diag(1, 1, -1))
-// H(d) = C [phi(rho) I + (phi'(rho)/rho) d d^T]; the force map is the gradient of an energy,
-// so its Jacobian is symmetric and this gather form equals the transpose product.
+//   image pairs: acc_i -= H(d_ij) (w_i - S w_j)   (S = diag(1, 1, -1), image charge -q)
+// H(d) = [phi(rho) I + (phi'(rho)/rho) d d^T] (times k_e q^2 / r_c^3). The force map is the
+// gradient of an energy, so its Jacobian is symmetric and this gather equals J^T w.
 template <typename T>
 __device__ __forceinline__ void pair_hess(T r2, T kappa, T c2k, T& fco, T& dfr) {
   const T r = sqrt(r2);
@@ -240,106 +279,101 @@ __device__ __forceinline__ void pair_hess(T r2, T kappa, T c2k, T& fco, T& dfr) 
   dfr = (dA / r2 - T(2) * A / (r2 * r)) / r;
 }
 
-template <typename T>
+template <typename T, typename Pos>
 __global__ void __launch_bounds__(kThreads)
-    k_pp_vjp(Geom g, const uint32_t* __restrict__ total,
-             const typename RecT<T>::type* __restrict__ rec, const uint32_t* __restrict__ skey,
+    k_pp_vjp(Geom g, const uint32_t* __restrict__ total, Pos pos,
              const uint32_t* __restrict__ starts, const double* __restrict__ w,
              double* __restrict__ acc, double scale) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
   const T kappa = static_cast<T>(g.kappa_eff);
   const T c2k = static_cast<T>(2.0 * g.kappa_eff * 0.56418958354775628695);
-  const T ax = static_cast<T>(g.a[0]), ay = static_cast<T>(g.a[1]), az = static_cast<T>(g.a[2]);
-  T ui[3];
+  T pi[3], li[3] = {T(0), T(0), T(0)};
   long long idx;
-  load_rec(rec, i, ui, idx);
-  int cx, cy, cz;
-  cell_decode(g, skey[i], cx, cy, cz);
-  const T px = ui[0] * ax, py = ui[1] * ay, pz = ui[2] * az;
+  if constexpr (sizeof(T) == 4) {
+    const float4 h = pos.hi[i], l = pos.lo[i];
+    pi[0] = h.x; pi[1] = h.y; pi[2] = h.z;
+    li[0] = l.x; li[1] = l.y; li[2] = l.z;
+    idx = __float_as_int(h.w);
+  } else {
+    const Rec64 r = pos.r[i];
+    pi[0] = r.u[0]; pi[1] = r.u[1]; pi[2] = r.u[2];
+    idx = r.idx;
+  }
   const T wi[3] = {static_cast<T>(w[3 * idx]), static_cast<T>(w[3 * idx + 1]),
                    static_cast<T>(w[3 * idx + 2])};
   double out[3] = {0.0, 0.0, 0.0};
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int nz = cz + dz;
-    if (nz < 0 || nz >= g.nc[2]) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int ny = cy + dy;
-      if (ny < 0 || ny >= g.nc[1]) continue;
-      T row[3] = {T(0), T(0), T(0)};
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int nx = cx + dx;
-        if (nx < 0 || nx >= g.nc[0]) continue;
-        const uint32_t key = cell_key(g, nx, ny, nz);
-        const T sx = static_cast<T>(dx * g.kc[0]) * ax;
-        const T sy = static_cast<T>(dy * g.kc[1]) * ay;
-        const T sz = static_cast<T>(dz * g.kc[2]) * az;
-        for (uint32_t j = starts[key]; j < starts[key + 1]; ++j) {
-          if (j == i) continue;
-          T uj[3];
+  auto sep = [&](uint32_t j, bool image, T& rx, T& ry, T& rz, long long& jdx) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 hj = pos.hi[j], lj = pos.lo[j];
+      jdx = __float_as_int(hj.w);
+      rx = (pi[0] - hj.x) + (li[0] - lj.x);
+      ry = (pi[1] - hj.y) + (li[1] - lj.y);
+      if (!image) {
+        rz = (pi[2] - hj.z) + (li[2] - lj.z);
+      } else {
+        const float ch = static_cast<float>(g.img_c);
+        const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
+        const float s = pi[2] + hj.z;
+        const float bp = s - pi[2];
+        const float e = (pi[2] - (s - bp)) + (hj.z - bp);
+        rz = ((s - ch) + e) + ((li[2] + lj.z) - cl);
+      }
+    } else {
+      const Rec64 rj = pos.r[j];
+      jdx = rj.idx;
+      rx = pi[0] - rj.u[0];
+      ry = pi[1] - rj.u[1];
+      rz = image ? pi[2] + rj.u[2] - static_cast<T>(g.img_c) : pi[2] - rj.u[2];
+    }
+  };
+  for_rows<T>(g, starts, pi[0], pi[1], pi[2], [&](uint32_t j0, uint32_t j1) {
+    T row[3] = {T(0), T(0), T(0)};
+    for (uint32_t j = j0; j < j1; ++j) {
+      if (j == i) continue;
+      T rx, ry, rz;
+      long long jdx;
+      sep(j, false, rx, ry, rz, jdx);
+      const T r2 = rx * rx + ry * ry + rz * rz;
+      if (r2 < T(1) && r2 > T(0)) {
+        T fco, dfr;
+        pair_hess(r2, kappa, c2k, fco, dfr);
+        const T v0 = wi[0] - static_cast<T>(w[3 * jdx]);
+        const T v1 = wi[1] - static_cast<T>(w[3 * jdx + 1]);
+        const T v2 = wi[2] - static_cast<T>(w[3 * jdx + 2]);
+        const T dv = rx * v0 + ry * v1 + rz * v2;
+        row[0] += fco * v0 + dfr * dv * rx;
+        row[1] += fco * v1 + dfr * dv * ry;
+        row[2] += fco * v2 + dfr * dv * rz;
+      }
+    }
+    for (int d = 0; d < 3; ++d) out[d] += static_cast<double>(row[d]);
+  });
+  if (g.pp_bc) {
+    const double zi = static_cast<double>(pi[2]) + static_cast<double>(li[2]);
+    if (zi - 0.5 * g.img_c < 1.0) {
+      const T mz = static_cast<T>(g.img_c - zi);
+      for_rows<T>(g, starts, pi[0], pi[1], mz, [&](uint32_t j0, uint32_t j1) {
+        T row[3] = {T(0), T(0), T(0)};
+        for (uint32_t j = j0; j < j1; ++j) {
+          T rx, ry, rz;
           long long jdx;
-          load_rec(rec, j, uj, jdx);
-          const T rx = px - (uj[0] * ax + sx);
-          const T ry = py - (uj[1] * ay + sy);
-          const T rz = pz - (uj[2] * az + sz);
+          sep(j, true, rx, ry, rz, jdx);
           const T r2 = rx * rx + ry * ry + rz * rz;
           if (r2 < T(1) && r2 > T(0)) {
             T fco, dfr;
             pair_hess(r2, kappa, c2k, fco, dfr);
             const T v0 = wi[0] - static_cast<T>(w[3 * jdx]);
             const T v1 = wi[1] - static_cast<T>(w[3 * jdx + 1]);
-            const T v2 = wi[2] - static_cast<T>(w[3 * jdx + 2]);
+            const T v2 = wi[2] + static_cast<T>(w[3 * jdx + 2]);  // w_i - S w_j
             const T dv = rx * v0 + ry * v1 + rz * v2;
-            row[0] += fco * v0 + dfr * dv * rx;
-            row[1] += fco * v1 + dfr * dv * ry;
-            row[2] += fco * v2 + dfr * dv * rz;
+            row[0] -= fco * v0 + dfr * dv * rx;
+            row[1] -= fco * v1 + dfr * dv * ry;
+            row[2] -= fco * v2 + dfr * dv * rz;
           }
         }
-      }
-      for (int d = 0; d < 3; ++d) out[d] += static_cast<double>(row[d]);
-    }
-  }
-  if (g.pp_bc) {
-    const double szi = static_cast<double>(cz * g.kc[2]) + static_cast<double>(ui[2]);
-    if ((szi - g.s_cath) * g.h[2] < g.rc) {
-      const double mz = 2.0 * g.s_cath - szi;
-      const double reach = g.rc / g.h[2];
-      const int z0 = max(static_cast<int>(floor((mz - reach) / g.kc[2])), 0);
-      const int z1 = min(static_cast<int>(floor((mz + reach) / g.kc[2])), g.nc[2] - 1);
-      for (int nz = z0; nz <= z1; ++nz) {
-        const T base = static_cast<T>(static_cast<double>((cz + nz) * g.kc[2]) - 2.0 * g.s_cath);
-        for (int dy = -1; dy <= 1; ++dy) {
-          const int ny = cy + dy;
-          if (ny < 0 || ny >= g.nc[1]) continue;
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int nx = cx + dx;
-            if (nx < 0 || nx >= g.nc[0]) continue;
-            const uint32_t key = cell_key(g, nx, ny, nz);
-            const T sx = static_cast<T>(dx * g.kc[0]) * ax;
-            const T sy = static_cast<T>(dy * g.kc[1]) * ay;
-            for (uint32_t j = starts[key]; j < starts[key + 1]; ++j) {
-              T uj[3];
-              long long jdx;
-              load_rec(rec, j, uj, jdx);
-              const T rx = px - (uj[0] * ax + sx);
-              const T ry = py - (uj[1] * ay + sy);
-              const T rz = (base + ui[2] + uj[2]) * az;
-              const T r2 = rx * rx + ry * ry + rz * rz;
-              if (r2 < T(1) && r2 > T(0)) {
-                T fco, dfr;
-                pair_hess(r2, kappa, c2k, fco, dfr);
-                const T v0 = wi[0] - static_cast<T>(w[3 * jdx]);
-                const T v1 = wi[1] - static_cast<T>(w[3 * jdx + 1]);
-                const T v2 = wi[2] + static_cast<T>(w[3 * jdx + 2]);  // w_i - S w_j
-                const T dv = rx * v0 + ry * v1 + rz * v2;
-                out[0] -= static_cast<double>(fco * v0 + dfr * dv * rx);
-                out[1] -= static_cast<double>(fco * v1 + dfr * dv * ry);
-                out[2] -= static_cast<double>(fco * v2 + dfr * dv * rz);
-              }
-            }
-          }
-        }
-      }
+        for (int d = 0; d < 3; ++d) out[d] += static_cast<double>(row[d]);
+      });
     }
   }
   acc[3 * i] = scale * out[0];
@@ -354,13 +388,13 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   const uint32_t* total = c->starts + c->nkeys;
   if (c->fp32)
-    k_pp<float><<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const float4*>(c->rec),
-                                            c->skey, c->starts, c->fpp, c->energy_acc,
-                                            c->pair_acc);
+    k_pp<float, PosF><<<blocks, kThreads, 0, s>>>(
+        c->g, total, PosF{static_cast<const float4*>(c->recp), c->recl}, c->starts, c->fpp,
+        c->energy_acc, c->pair_acc);
   else
-    k_pp<double><<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const Rec64*>(c->rec),
-                                             c->skey, c->starts, c->fpp, c->energy_acc,
-                                             c->pair_acc);
+    k_pp<double, PosD><<<blocks, kThreads, 0, s>>>(
+        c->g, total, PosD{static_cast<const Rec64*>(c->recp)}, c->starts, c->fpp, c->energy_acc,
+        c->pair_acc);
 }
 
 void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s) {
@@ -370,11 +404,12 @@ void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s)
   // d/dxi of (k_e q^2 / r_c^2) f(rho): one more factor 1/r_c
   const double scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc * c->g.rc);
   if (c->fp32)
-    k_pp_vjp<float><<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const float4*>(c->rec),
-                                                c->skey, c->starts, w, c->acc, scale);
+    k_pp_vjp<float, PosF><<<blocks, kThreads, 0, s>>>(
+        c->g, total, PosF{static_cast<const float4*>(c->recp), c->recl}, c->starts, w, c->acc,
+        scale);
   else
-    k_pp_vjp<double><<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const Rec64*>(c->rec),
-                                                 c->skey, c->starts, w, c->acc, scale);
+    k_pp_vjp<double, PosD><<<blocks, kThreads, 0, s>>>(
+        c->g, total, PosD{static_cast<const Rec64*>(c->recp)}, c->starts, w, c->acc, scale);
 }
 
 }  // namespace p3m

@@ -1,8 +1,8 @@
 // Binning of particles into cutoff cells and a counting sort by cell.
 //
 // The short-range sum of eq. (summation_short) needs, for each particle, the particles
-// "close to" it (within r_c, Sec. 3.1.1, fig. ShortError). Cells of edge kc_d h_d >= r_c
-// turn that search into the 27 neighbouring cells. The sort is a counting sort in three
+// "close to" it (within r_c, Sec. 3.1.1, fig. ShortError). Cells at least r_c wide in y and z
+// turn that search into 3 x 3 rows of cells along x. The sort is a counting sort in three
 // passes: histogram with in-cell ranks (atomics), exclusive scan of the cell counts, scatter.
 // No pass waits on another block, so no inter-block spin is needed.
 #include "p3m_internal.cuh"
@@ -15,24 +15,26 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;  // per thread
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-// Mesh coordinate s_d = (x_d - lo_d) / h_d and validity of one particle.
-// Valid: the assignment support lies inside the mesh (TSC: floor(s + 1/2) in [1, n - 2];
-// CIC: floor(s) in [0, n - 2]) and, with the cathode in the long-range solve, z > z_cathode.
-// Returns 0 if valid, else an error bit.
+// Validity of one particle and its cell. Valid: the assignment support lies inside the mesh
+// (TSC: floor(s + 1/2) in [1, n - 2]; CIC: floor(s) in [0, n - 2]) with s = (x - lo) / h and,
+// with the cathode in the long-range solve, z > z_cathode. Returns 0 if valid, else an error bit.
 __device__ __forceinline__ int particle_cell(const Geom& g, const double* __restrict__ xi,
-                                             double s[3], int cell[3]) {
+                                             int cell[3]) {
   int err = 0;
   for (int d = 0; d < 3; ++d) {
-    const double v = xi[d];
-    s[d] = (v - g.lo[d]) / g.h[d];
-    if (!(s[d] == s[d])) return kErrNaN;
-    const double c = (g.order == 2) ? floor(s[d] + 0.5) : floor(s[d]);
+    const double s = (xi[d] - g.lo[d]) / g.h[d];
+    if (!(s == s)) return kErrNaN;
+    const double c = (g.order == 2) ? floor(s + 0.5) : floor(s);
     const double cmin = (g.order == 2) ? 1.0 : 0.0;
     if (!(c >= cmin && c <= static_cast<double>(g.n[d] - 2))) err = kErrRange;
   }
   if (g.pm_bc && !(xi[2] > g.zc)) err = kErrRange;
   if (err) return err;
-  for (int d = 0; d < 3; ++d) cell[d] = static_cast<int>(floor(s[d])) / g.kc[d];
+  for (int d = 0; d < 3; ++d) {
+    const double xr = (xi[d] - g.lo[d]) / g.rc;
+    const int c = static_cast<int>(floor(xr * g.inv_cw[d]));
+    cell[d] = min(max(c, 0), g.nc[d] - 1);
+  }
   return 0;
 }
 
@@ -42,9 +44,8 @@ __global__ void k_bin(Geom g, const double* __restrict__ x, int64_t n,
                       double* __restrict__ f_zero) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n) return;
-  double s[3];
   int cell[3];
-  const int e = particle_cell(g, x + 3 * i, s, cell);
+  const int e = particle_cell(g, x + 3 * i, cell);
   if (e) {
     keys[i] = kInvalidKey;
     atomicOr(err, e);
@@ -155,33 +156,50 @@ __global__ void k_scan_add(uint32_t* __restrict__ out, const uint32_t* __restric
 template <bool kFP32>
 __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
                           const uint32_t* __restrict__ keys, const uint32_t* __restrict__ ranks,
-                          const uint32_t* __restrict__ starts, void* __restrict__ rec,
-                          uint32_t* __restrict__ skey) {
+                          const uint32_t* __restrict__ starts, void* __restrict__ recp,
+                          float4* __restrict__ recl, void* __restrict__ recm) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n) return;
   const uint32_t key = keys[i];
   if (key == kInvalidKey) return;
-  double s[3];
-  int cell[3];
-  particle_cell(g, x + 3 * i, s, cell);
   const uint32_t pos = starts[key] + ranks[i];
-  // offset from the cell's first node; exact in FP64 (both terms within a factor 2 or cell 0)
-  const double u0 = s[0] - static_cast<double>(cell[0] * g.kc[0]);
-  const double u1 = s[1] - static_cast<double>(cell[1] * g.kc[1]);
-  const double u2 = s[2] - static_cast<double>(cell[2] * g.kc[2]);
+  double xr[3], u[3];
+  int c[3];
+  for (int d = 0; d < 3; ++d) {
+    const double v = x[3 * i + d];
+    xr[d] = (v - g.lo[d]) / g.rc;
+    const double s = (v - g.lo[d]) / g.h[d];
+    const double cn = (g.order == 2) ? floor(s + 0.5) : floor(s);
+    u[d] = s - cn;
+    c[d] = static_cast<int>(cn);
+  }
+  const uint32_t node = pack_node(c[0], c[1], c[2]);
   if (kFP32) {
-    reinterpret_cast<float4*>(rec)[pos] =
-        make_float4(static_cast<float>(u0), static_cast<float>(u1), static_cast<float>(u2),
-                    __int_as_float(static_cast<int>(i)));
+    float hi[3], lo[3];
+    for (int d = 0; d < 3; ++d) {
+      hi[d] = static_cast<float>(xr[d]);
+      lo[d] = static_cast<float>(xr[d] - static_cast<double>(hi[d]));
+    }
+    reinterpret_cast<float4*>(recp)[pos] =
+        make_float4(hi[0], hi[1], hi[2], __int_as_float(static_cast<int>(i)));
+    recl[pos] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    reinterpret_cast<float4*>(recm)[pos] =
+        make_float4(static_cast<float>(u[0]), static_cast<float>(u[1]), static_cast<float>(u[2]),
+                    __uint_as_float(node));
   } else {
     Rec64 r;
-    r.u[0] = u0;
-    r.u[1] = u1;
-    r.u[2] = u2;
+    r.u[0] = xr[0];
+    r.u[1] = xr[1];
+    r.u[2] = xr[2];
     r.idx = static_cast<long long>(i);
-    reinterpret_cast<Rec64*>(rec)[pos] = r;
+    reinterpret_cast<Rec64*>(recp)[pos] = r;
+    Rec64 m;
+    m.u[0] = u[0];
+    m.u[1] = u[1];
+    m.u[2] = u[2];
+    m.idx = static_cast<long long>(node);
+    reinterpret_cast<Rec64*>(recm)[pos] = m;
   }
-  skey[pos] = key;
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -211,10 +229,10 @@ void launch_scatter(const p3m_ctx* c, const double* x, int64_t n) {
   if (n == 0) return;
   if (c->fp32)
     k_scatter<true><<<grid_for(n, kBinThreads), kBinThreads, 0, c->stream>>>(
-        c->g, x, n, c->keys, c->ranks, c->starts, c->rec, c->skey);
+        c->g, x, n, c->keys, c->ranks, c->starts, c->recp, c->recl, c->recm);
   else
     k_scatter<false><<<grid_for(n, kBinThreads), kBinThreads, 0, c->stream>>>(
-        c->g, x, n, c->keys, c->ranks, c->starts, c->rec, c->skey);
+        c->g, x, n, c->keys, c->ranks, c->starts, c->recp, nullptr, c->recm);
 }
 
 }  // namespace p3m
