@@ -123,26 +123,39 @@ void free_all(p3m_ctx* c) {
   if (c->have_c2r) cufftDestroy(c->plan_c2r);
   if (c->have_c2r3) cufftDestroy(c->plan_c2r3);
   if (c->s_pp) cudaStreamDestroy(c->s_pp);
+  if (c->work) cudaStreamDestroy(c->work);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
   for (auto& e : c->tev)
     if (e) cudaEventDestroy(e);
 }
 
+// Every call orders its work after the caller's stream (enter) and makes the caller's stream
+// wait for it (finish); the work itself runs on the context's own streams.
+void enter(p3m_ctx* c) {
+  cudaEventRecord(c->ev_in, c->stream);
+  cudaStreamWaitEvent(c->work, c->ev_in, 0);
+}
+
 // Returns a device error latched by earlier calls (and clears it), from the pinned mirror that
-// every call refreshes asynchronously at its end.
+// every call refreshes asynchronously at its end. Also orders the call after the caller's stream.
 p3m_status take_deferred(p3m_ctx* c) {
+  enter(c);
   const int e = *reinterpret_cast<volatile int*>(c->err_host);
   if (!e) return P3M_OK;
   *c->err_host = 0;
-  cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+  cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->work);
   if (e & kErrTimeout) return fail(c, P3M_ETIMEOUT, "a bounded device wait ran out");
   if (e & kErrNaN) return fail(c, P3M_EINVAL, "a particle position is NaN");
   return fail(c, P3M_ERANGE, "a particle lies outside the mesh's valid range or below the cathode");
 }
 
 p3m_status finish(p3m_ctx* c) {
-  cudaMemcpyAsync(c->err_host, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(c->err_host, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->work);
+  cudaEventRecord(c->ev_out, c->work);
+  cudaStreamWaitEvent(c->stream, c->ev_out, 0);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   return P3M_OK;
@@ -199,7 +212,7 @@ p3m_status mesh_solve(p3m_ctx* c, bool want_phi, bool want_diff, bool want_energ
 
 p3m_status forces_impl(p3m_ctx* c, const double* x, int64_t n, double* f, double* energy,
                        int parts) {
-  cudaStream_t st = c->stream;
+  cudaStream_t st = c->work;
   cudaMemsetAsync(c->energy_acc, 0, 2 * sizeof(double), st);
   cudaMemsetAsync(c->pair_acc, 0, 2 * sizeof(unsigned long long), st);
   cudaEventRecord(c->tev[0], st);
@@ -236,7 +249,7 @@ p3m_status forces_impl(p3m_ctx* c, const double* x, int64_t n, double* f, double
 // out = (dF/dx)^T w
 p3m_status vjp_impl(p3m_ctx* c, const double* x, int64_t n, const double* w, double* out) {
   sort_particles(c, x, n, out);
-  launch_pp_vjp(c, n, w, c->stream);  // acc = short-range part
+  launch_pp_vjp(c, n, w, c->work);  // acc = short-range part
   launch_zero_block(c);
   launch_deposit(c, n);
   p3m_status s = mesh_solve(c, false, true, false);
@@ -259,10 +272,10 @@ p3m_status push_impl(p3m_ctx* c, double* x, double* p, int64_t n, double dt, int
     if (s != P3M_OK) return s;
   }
   for (int32_t k = 0; k < nsteps; ++k) {
-    launch_kick_drift(x, p, f, n, 0.5 * dt, dt / c->g.mass, c->stream);
+    launch_kick_drift(x, p, f, n, 0.5 * dt, dt / c->g.mass, c->work);
     p3m_status s = forces_impl(c, x, n, f, nullptr, 3);
     if (s != P3M_OK) return s;
-    launch_kick_drift(x, p, f, n, 0.5 * dt, 0.0, c->stream);
+    launch_kick_drift(x, p, f, n, 0.5 * dt, 0.0, c->work);
   }
   return P3M_OK;
 }
@@ -395,9 +408,15 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     A(alloc(&c->tmp3b, 3 * n_max));
   }
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&c->err_host), sizeof(int), 0);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_pp, cudaStreamNonBlocking);
+  int prio_low = 0, prio_high = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  if (e == cudaSuccess)
+    e = cudaStreamCreateWithPriority(&c->work, cudaStreamNonBlocking, prio_high);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_pp, cudaStreamNonBlocking, prio_low);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
   for (auto& ev : c->tev)
     if (e == cudaSuccess) e = cudaEventCreate(&ev);
   if (e != cudaSuccess) {
@@ -407,8 +426,8 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     return e == cudaErrorMemoryAllocation ? P3M_ENOMEM : P3M_ECUDA;
   }
   *c->err_host = 0;
-  cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
-  cudaMemsetAsync(c->qpad, 0, es * c->n_real, c->stream);
+  cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->work);
+  cudaMemsetAsync(c->qpad, 0, es * c->n_real, c->work);
   if (c->fp32) {
     std::vector<float2> fac(g.M[0] / 2 + 1 + g.M[1] + g.M[2]);
     size_t o = 0;
@@ -422,7 +441,7 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     put(g.M[1], g.M[1]);
     put(g.M[2], g.M[2]);
     cudaMemcpyAsync(c->dfac, fac.data(), sizeof(float2) * fac.size(), cudaMemcpyHostToDevice,
-                    c->stream);
+                    c->work);
   }
   // FFT plans
   cufftResult r = cufftPlan3d(&c->plan_r2c, g.M[2], g.M[1], g.M[0], c->fp32 ? CUFFT_R2C : CUFFT_D2Z);
@@ -441,9 +460,9 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     delete c;
     return r == CUFFT_ALLOC_FAILED ? P3M_ENOMEM : P3M_ECUFFT;
   }
-  cufftSetStream(c->plan_r2c, c->stream);
-  cufftSetStream(c->plan_c2r, c->stream);
-  if (c->have_c2r3) cufftSetStream(c->plan_c2r3, c->stream);
+  cufftSetStream(c->plan_r2c, c->work);
+  cufftSetStream(c->plan_c2r, c->work);
+  if (c->have_c2r3) cufftSetStream(c->plan_c2r3, c->work);
   e = build_green(c);
   if (e != cudaSuccess) {
     free_all(c);
@@ -457,8 +476,9 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
 
 p3m_status p3m_destroy(p3m_ctx* c) {
   if (!c) return P3M_OK;
-  cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->work);
   cudaStreamSynchronize(c->s_pp);
+  cudaStreamSynchronize(c->stream);
   free_all(c);
   delete c;
   return P3M_OK;
@@ -467,9 +487,6 @@ p3m_status p3m_destroy(p3m_ctx* c) {
 p3m_status p3m_set_stream(p3m_ctx* c, void* stream) {
   if (!c) return P3M_EINVAL;
   c->stream = static_cast<cudaStream_t>(stream);
-  cufftSetStream(c->plan_r2c, c->stream);
-  cufftSetStream(c->plan_c2r, c->stream);
-  if (c->have_c2r3) cufftSetStream(c->plan_c2r3, c->stream);
   return P3M_OK;
 }
 
@@ -492,7 +509,7 @@ p3m_status p3m_solve(p3m_ctx* c) {
   p3m_status s = take_deferred(c);
   if (s != P3M_OK) return s;
   if (!c->deposited) return fail(c, P3M_ESTATE, "p3m_solve needs a deposit first");
-  cudaMemsetAsync(c->energy_acc, 0, 2 * sizeof(double), c->stream);
+  cudaMemsetAsync(c->energy_acc, 0, 2 * sizeof(double), c->work);
   s = mesh_solve(c, true, c->fp32, true);
   if (s != P3M_OK) return s;
   return finish(c);
@@ -502,6 +519,7 @@ p3m_status p3m_get_mesh(p3m_ctx* c, int32_t which, double* out) {
   if (!c || !out || (which != 0 && which != 1)) return P3M_EINVAL;
   if (which == 0 && !c->deposited) return fail(c, P3M_ESTATE, "no deposit");
   if (which == 1 && !c->phi_valid) return fail(c, P3M_ESTATE, "no potential (call p3m_solve)");
+  enter(c);
   launch_get_mesh(c, which, out);
   return finish(c);
 }
@@ -528,8 +546,9 @@ p3m_status p3m_forces(p3m_ctx* c, const double* x, int64_t n, double* f, double*
 p3m_status p3m_pair_count(p3m_ctx* c, int64_t* pairs, int64_t* image_pairs) {
   if (!c || !pairs) return P3M_EINVAL;
   unsigned long long v[2] = {0, 0};
-  cudaError_t e = cudaMemcpyAsync(v, c->pair_acc, sizeof(v), cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  enter(c);
+  cudaError_t e = cudaMemcpyAsync(v, c->pair_acc, sizeof(v), cudaMemcpyDeviceToHost, c->work);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
   if (e != cudaSuccess) return cuda_fail(c, e, "p3m_pair_count");
   *pairs = static_cast<int64_t>(v[0]);
   if (image_pairs) *image_pairs = static_cast<int64_t>(v[1]);
@@ -573,7 +592,7 @@ p3m_status p3m_backward(p3m_ctx* c, const double* x0, const double* p0, int64_t 
   p3m_status s = take_deferred(c);
   if (s != P3M_OK) return s;
   if ((s = check_n(c, n)) != P3M_OK) return s;
-  cudaStream_t st = c->stream;
+  cudaStream_t st = c->work;
   const size_t n3 = 3 * static_cast<size_t>(n);
   const size_t bytes = n3 * sizeof(double);
   const size_t slot = 6 * static_cast<size_t>(c->n_max);
@@ -634,14 +653,15 @@ p3m_status p3m_emittance(p3m_ctx* c, const double* x, const double* p, int64_t n
   if (!x || !p || !eps3 || n < 2) return fail(c, P3M_EINVAL, "bad argument");
   p3m_status s = take_deferred(c);
   if (s != P3M_OK) return s;
-  launch_emittance(x, p, n, c->g.mass * kSpeedOfLight, eps3, gx, gp, c->red, c->stream);
+  launch_emittance(x, p, n, c->g.mass * kSpeedOfLight, eps3, gx, gp, c->red, c->work);
   return finish(c);
 }
 
 p3m_status p3m_sync(p3m_ctx* c) {
   if (!c) return P3M_EINVAL;
-  cudaError_t e = cudaStreamSynchronize(c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->work);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_pp);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "p3m_sync");
   int v = 0;
   e = cudaMemcpy(&v, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
@@ -652,7 +672,7 @@ p3m_status p3m_sync(p3m_ctx* c) {
 
 p3m_status p3m_get_timings(p3m_ctx* c, double* ms, int32_t cap, int32_t* count) {
   if (!c || !ms || cap < 0) return P3M_EINVAL;
-  cudaError_t e = cudaStreamSynchronize(c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->work);
   if (e != cudaSuccess) return cuda_fail(c, e, "p3m_get_timings");
   float t[6] = {0, 0, 0, 0, 0, 0};
   cudaEventElapsedTime(&t[0], c->tev[0], c->tev[1]);

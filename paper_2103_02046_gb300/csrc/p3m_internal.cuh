@@ -108,8 +108,10 @@ struct p3m_ctx {
   int device = 0;
   bool fp32 = false;
   cudaStream_t stream = nullptr;  // caller's stream (not owned)
-  cudaStream_t s_pp = nullptr;    // owned side stream for the short range
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t work = nullptr;    // owned, high priority: sort, mesh chain, combination
+  cudaStream_t s_pp = nullptr;    // owned, low priority: the short range (ALU-bound), so that
+                                  // mesh-chain blocks are scheduled first when SMs free up
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr;
   cudaEvent_t tev[8] = {};
 
   // binning / counting sort

@@ -184,7 +184,7 @@ void launch_energy_out(const p3m_ctx* c, double* energy) {
   // long range: (1/2) q sum_m W[m] phi[m] (W = assignment weights, phi in volts)
   const double pp_scale = 0.5 * c->g.ke * c->g.q * c->g.q / c->g.rc;
   const double pm_scale = 0.5 * c->g.q;
-  k_energy_out<<<1, 32, 0, c->stream>>>(c->energy_acc, pp_scale, pm_scale, energy);
+  k_energy_out<<<1, 32, 0, c->work>>>(c->energy_acc, pp_scale, pm_scale, energy);
 }
 
 }  // namespace p3m

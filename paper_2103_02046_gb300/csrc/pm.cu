@@ -604,26 +604,26 @@ cudaError_t build_green(p3m_ctx* c) {
   if (cufftPlan3d(&plan, g.M[2], g.M[1], g.M[0], CUFFT_D2Z) != CUFFT_SUCCESS)
     return fail(cudaErrorUnknown);
   have_plan = true;
-  cufftSetStream(plan, c->stream);
-  k_sample_kernel<<<blocks_for(nreal), kThreads, 0, c->stream>>>(g, samp, 0);
+  cufftSetStream(plan, c->work);
+  k_sample_kernel<<<blocks_for(nreal), kThreads, 0, c->work>>>(g, samp, 0);
   if (cufftExecD2Z(plan, samp, reinterpret_cast<cufftDoubleComplex*>(sf)) != CUFFT_SUCCESS)
     return fail(cudaErrorUnknown);
   if (g.pm_bc) {
-    k_sample_kernel<<<blocks_for(nreal), kThreads, 0, c->stream>>>(g, samp, 1);
+    k_sample_kernel<<<blocks_for(nreal), kThreads, 0, c->work>>>(g, samp, 1);
     if (cufftExecD2Z(plan, samp, reinterpret_cast<cufftDoubleComplex*>(si)) != CUFFT_SUCCESS)
       return fail(cudaErrorUnknown);
   }
   // scale: k_e q / (Mx My Mz); the mesh holds assignment weights, the inverse FFT is unnormalised
   const double scale = g.ke * g.q / static_cast<double>(nreal);
   if (c->fp32)
-    k_finish_kernels<float><<<blocks_for(ncplx), kThreads, 0, c->stream>>>(
+    k_finish_kernels<float><<<blocks_for(ncplx), kThreads, 0, c->work>>>(
         g, sf, si, static_cast<float*>(c->khat_f), static_cast<float2*>(c->khat_i), scale,
         c->prm.influence);
   else
-    k_finish_kernels<double><<<blocks_for(ncplx), kThreads, 0, c->stream>>>(
+    k_finish_kernels<double><<<blocks_for(ncplx), kThreads, 0, c->work>>>(
         g, sf, si, static_cast<double*>(c->khat_f), static_cast<double2*>(c->khat_i), scale,
         c->prm.influence);
-  err = cudaStreamSynchronize(c->stream);
+  err = cudaStreamSynchronize(c->work);
   if (err == cudaSuccess) err = cudaGetLastError();
   return fail(err);
 }
@@ -631,7 +631,7 @@ cudaError_t build_green(p3m_ctx* c) {
 void launch_zero_block(const p3m_ctx* c) {
   const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
   cudaPitchedPtr pp = make_cudaPitchedPtr(c->qpad, es * c->g.M[0], es * c->g.M[0], c->g.M[1]);
-  cudaMemset3DAsync(pp, 0, make_cudaExtent(es * c->g.n[0], c->g.n[1], c->g.n[2]), c->stream);
+  cudaMemset3DAsync(pp, 0, make_cudaExtent(es * c->g.n[0], c->g.n[1], c->g.n[2]), c->work);
 }
 
 void launch_deposit(const p3m_ctx* c, int64_t n) {
@@ -639,11 +639,11 @@ void launch_deposit(const p3m_ctx* c, int64_t n) {
   const uint32_t* total = c->starts + c->nkeys;
   const unsigned blocks = static_cast<unsigned>((n + kDepPerBlock - 1) / kDepPerBlock);
   if (c->fp32)
-    k_deposit_tiled<float, false><<<blocks, kDepThreads, 0, c->stream>>>(
+    k_deposit_tiled<float, false><<<blocks, kDepThreads, 0, c->work>>>(
         c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp),
         nullptr, static_cast<float*>(c->qpad));
   else
-    k_deposit_tiled<double, false><<<blocks, kDepThreads, 0, c->stream>>>(
+    k_deposit_tiled<double, false><<<blocks, kDepThreads, 0, c->work>>>(
         c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp),
         nullptr, static_cast<double*>(c->qpad));
 }
@@ -653,11 +653,11 @@ void launch_dipole_deposit(const p3m_ctx* c, int64_t n, const double* w) {
   const uint32_t* total = c->starts + c->nkeys;
   const unsigned blocks = static_cast<unsigned>((n + kDepPerBlock - 1) / kDepPerBlock);
   if (c->fp32)
-    k_deposit_tiled<float, true><<<blocks, kDepThreads, 0, c->stream>>>(
+    k_deposit_tiled<float, true><<<blocks, kDepThreads, 0, c->work>>>(
         c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp), w,
         static_cast<float*>(c->qpad));
   else
-    k_deposit_tiled<double, true><<<blocks, kDepThreads, 0, c->stream>>>(
+    k_deposit_tiled<double, true><<<blocks, kDepThreads, 0, c->work>>>(
         c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp), w,
         static_cast<double*>(c->qpad));
 }
@@ -667,13 +667,13 @@ void launch_green_multiply(const p3m_ctx* c, bool want_phi, bool want_diff, bool
   const size_t total = static_cast<size_t>(g.M[0] / 2 + 1) * g.M[1] * (g.M[2] / 2 + 1);
   double* en = want_energy ? c->energy_acc + 1 : nullptr;
   if (c->fp32)
-    k_green_multiply<float><<<blocks_for(total), kThreads, 0, c->stream>>>(
+    k_green_multiply<float><<<blocks_for(total), kThreads, 0, c->work>>>(
         g, static_cast<const float2*>(c->qhat), static_cast<const float*>(c->khat_f),
         static_cast<const float2*>(c->khat_i), c->dfac,
         want_diff ? static_cast<float2*>(c->fhat) : nullptr,
         want_phi ? static_cast<float2*>(c->phihat) : nullptr, en, c->n_cplx);
   else
-    k_green_multiply<double><<<blocks_for(total), kThreads, 0, c->stream>>>(
+    k_green_multiply<double><<<blocks_for(total), kThreads, 0, c->work>>>(
         g, static_cast<const double2*>(c->qhat), static_cast<const double*>(c->khat_f),
         static_cast<const double2*>(c->khat_i), nullptr, nullptr,
         want_phi ? static_cast<double2*>(c->phihat) : nullptr, en, c->n_cplx);
@@ -684,11 +684,11 @@ void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts) {
   const uint32_t* total = c->starts + c->nkeys;
   const double pp_scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc);
   if (c->fp32)
-    k_interp<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
+    k_interp<float><<<blocks_for(n), kThreads, 0, c->work>>>(
         c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp),
         static_cast<const float*>(c->freal), c->n_real, c->fpp, f, parts, pp_scale);
   else
-    k_interp<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
+    k_interp<double><<<blocks_for(n), kThreads, 0, c->work>>>(
         c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp),
         static_cast<const double*>(c->phireal), c->n_real, c->fpp, f, parts, pp_scale);
 }
@@ -697,11 +697,11 @@ void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, d
   if (n == 0) return;
   const uint32_t* total = c->starts + c->nkeys;
   if (c->fp32)
-    k_vjp_gather<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
+    k_vjp_gather<float><<<blocks_for(n), kThreads, 0, c->work>>>(
         c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp),
         static_cast<const float*>(c->freal), c->n_real, w, c->acc, out, pass);
   else
-    k_vjp_gather<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
+    k_vjp_gather<double><<<blocks_for(n), kThreads, 0, c->work>>>(
         c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp),
         static_cast<const double*>(c->phireal), c->n_real, w, c->acc, out, pass);
 }
@@ -711,10 +711,10 @@ void launch_get_mesh(const p3m_ctx* c, int which, double* out) {
   const void* src = which == 0 ? c->qpad : c->phireal;
   const double scale = which == 0 ? c->g.q : 1.0;
   if (c->fp32)
-    k_get_mesh<float><<<blocks_for(total), kThreads, 0, c->stream>>>(
+    k_get_mesh<float><<<blocks_for(total), kThreads, 0, c->work>>>(
         c->g, static_cast<const float*>(src), scale, out);
   else
-    k_get_mesh<double><<<blocks_for(total), kThreads, 0, c->stream>>>(
+    k_get_mesh<double><<<blocks_for(total), kThreads, 0, c->work>>>(
         c->g, static_cast<const double*>(src), scale, out);
 }
 

@@ -209,29 +209,29 @@ inline unsigned grid_for(int64_t n, int threads) {
 }  // namespace
 
 void launch_bin(const p3m_ctx* c, const double* x, int64_t n, double* f_zero) {
-  cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * c->nkeys, c->stream);
+  cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * c->nkeys, c->work);
   if (n == 0) return;
-  k_bin<<<grid_for(n, kBinThreads), kBinThreads, 0, c->stream>>>(c->g, x, n, c->counts, c->keys,
+  k_bin<<<grid_for(n, kBinThreads), kBinThreads, 0, c->work>>>(c->g, x, n, c->counts, c->keys,
                                                                   c->ranks, c->err_dev, f_zero);
 }
 
 void launch_scan(const p3m_ctx* c) {
   const uint64_t n = c->nkeys;
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
-  k_scan_tiles<<<static_cast<unsigned>(tiles), kScanThreads, 0, c->stream>>>(c->counts, c->starts,
+  k_scan_tiles<<<static_cast<unsigned>(tiles), kScanThreads, 0, c->work>>>(c->counts, c->starts,
                                                                              c->bsum, n);
-  k_scan_sums<<<1, kScanThreads, 0, c->stream>>>(c->bsum, tiles, c->starts + n);
-  k_scan_add<<<static_cast<unsigned>((n + 255) / 256), 256, 0, c->stream>>>(c->starts, c->bsum,
+  k_scan_sums<<<1, kScanThreads, 0, c->work>>>(c->bsum, tiles, c->starts + n);
+  k_scan_add<<<static_cast<unsigned>((n + 255) / 256), 256, 0, c->work>>>(c->starts, c->bsum,
                                                                             n);
 }
 
 void launch_scatter(const p3m_ctx* c, const double* x, int64_t n) {
   if (n == 0) return;
   if (c->fp32)
-    k_scatter<true><<<grid_for(n, kBinThreads), kBinThreads, 0, c->stream>>>(
+    k_scatter<true><<<grid_for(n, kBinThreads), kBinThreads, 0, c->work>>>(
         c->g, x, n, c->keys, c->ranks, c->starts, c->recp, c->recl, c->recm);
   else
-    k_scatter<false><<<grid_for(n, kBinThreads), kBinThreads, 0, c->stream>>>(
+    k_scatter<false><<<grid_for(n, kBinThreads), kBinThreads, 0, c->work>>>(
         c->g, x, n, c->keys, c->ranks, c->starts, c->recp, nullptr, c->recm);
 }
 
