@@ -104,6 +104,57 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   return g;
 }
 
+// Polynomial for the FP32 pair kernel: R(x) = erfc(x) e^{x^2} on [0, kappa] by Chebyshev
+// interpolation in t = 2x/kappa - 1, converted to monomials in t; the lowest degree whose erfc
+// error is below 2e-7 absolute is kept (a force error of the same relative size, since
+// erfc(x) <= 1 multiplies 1/rho^2 in the pair force).
+PairPoly fit_pair_poly(double kappa) {
+  PairPoly pp{};
+  const int N = 96;
+  std::vector<double> tn(N), fn(N);
+  for (int j = 0; j < N; ++j) {
+    tn[j] = std::cos(kPi * (j + 0.5) / N);
+    const double x = 0.5 * (tn[j] + 1.0) * kappa;
+    fn[j] = std::erfc(x) * std::exp(x * x);
+  }
+  for (int deg = 6; deg < kMaxPoly; ++deg) {
+    std::vector<double> ch(deg + 1);
+    for (int k = 0; k <= deg; ++k) {
+      double acc = 0.0;
+      for (int j = 0; j < N; ++j) acc += fn[j] * std::cos(k * std::acos(tn[j]));
+      ch[k] = acc * 2.0 / N;
+    }
+    ch[0] *= 0.5;
+    // Chebyshev -> monomial: T_0 = 1, T_1 = t, T_{k+1} = 2 t T_k - T_{k-1}
+    std::vector<double> mono(deg + 1, 0.0), tkm1(deg + 1, 0.0), tk(deg + 1, 0.0), tkp1(deg + 1);
+    tkm1[0] = 1.0;
+    tk[1] = 1.0;
+    mono[0] += ch[0];
+    if (deg >= 1) mono[1] += ch[1];
+    for (int k = 1; k < deg; ++k) {
+      for (int m = 0; m <= deg; ++m) tkp1[m] = (m > 0 ? 2.0 * tk[m - 1] : 0.0) - tkm1[m];
+      for (int m = 0; m <= deg; ++m) mono[m] += ch[k + 1] * tkp1[m];
+      tkm1 = tk;
+      tk = tkp1;
+    }
+    double err = 0.0;
+    for (int q = 0; q <= 2000; ++q) {
+      const double x = kappa * q / 2000.0;
+      const float t = static_cast<float>(2.0 * x / kappa - 1.0);
+      float r = static_cast<float>(mono[deg]);
+      for (int m = deg - 1; m >= 0; --m) r = std::fma(r, t, static_cast<float>(mono[m]));
+      err = std::max(err, std::fabs(static_cast<double>(r) * std::exp(-x * x) - std::erfc(x)));
+    }
+    pp.deg = deg;
+    for (int m = 0; m <= deg; ++m) pp.c[m] = static_cast<float>(mono[m]);
+    pp.max_abs_err = static_cast<float>(err);
+    if (err < 2e-7) break;
+  }
+  pp.kappa2_log2e = static_cast<float>(kappa * kappa * 1.4426950408889634);
+  pp.c2k = static_cast<float>(2.0 * kappa / std::sqrt(kPi));
+  return pp;
+}
+
 template <typename T>
 cudaError_t alloc(T** ptr, size_t count) {
   *ptr = nullptr;
@@ -353,6 +404,7 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   auto* c = new p3m_ctx();
   c->prm = *params;
   c->g = make_geom(params, n_max);
+  c->poly = fit_pair_poly(c->g.kappa_eff);
   c->n_max = n_max;
   c->fp32 = params->precision == P3M_FP32_MIXED;
   c->stream = static_cast<cudaStream_t>(stream);

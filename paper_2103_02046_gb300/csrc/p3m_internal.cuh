@@ -49,6 +49,17 @@ struct Geom {
   double kappa_eff;  // alpha * r_c
 };
 
+// FP32 pair kernel: erfc(x) e^{x^2} on x in [0, kappa_eff] as a polynomial in t = 2 x /
+// kappa_eff - 1 (Horner, highest degree first), fitted at context creation.
+constexpr int kMaxPoly = 16;
+struct PairPoly {
+  int deg;
+  float c[kMaxPoly];
+  float kappa2_log2e;  // kappa_eff^2 log2(e): e^{-kappa^2 rho^2} = 2^{-kappa2_log2e rho^2}
+  float c2k;           // 2 kappa_eff / sqrt(pi)
+  float max_abs_err;   // fit error of erfc over [0, kappa_eff] (reported, not used)
+};
+
 __host__ __device__ inline uint32_t cell_key(const Geom& g, int cx, int cy, int cz) {
   return (static_cast<uint32_t>(cz) * g.nc[1] + cy) * g.nc[0] + cx;
 }
@@ -104,6 +115,7 @@ __device__ __forceinline__ void load_rec(const Rec64* rec, uint32_t i, double u[
 struct p3m_ctx {
   p3m_params prm{};
   p3m::Geom g{};
+  p3m::PairPoly poly{};
   int64_t n_max = 0;
   int device = 0;
   bool fp32 = false;

@@ -19,19 +19,37 @@ __device__ __forceinline__ unsigned long long ordered_key(double v) {
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
-__global__ void k_bbox(const double* __restrict__ x, int64_t n3, unsigned long long* __restrict__ mn,
+__global__ void k_bbox(const double* __restrict__ x, int64_t n, unsigned long long* __restrict__ mn,
                        unsigned long long* __restrict__ mx, int* __restrict__ bad) {
-  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (t >= n3) return;
-  const double v = x[t];
-  const int d = static_cast<int>(t % 3);
-  if (!isfinite(v)) {
-    atomicOr(bad, 1);
-    return;
+  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+  int b = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int d = 0; d < 3; ++d) {
+      const double v = x[3 * i + d];
+      if (!isfinite(v)) {
+        b = 1;
+        continue;
+      }
+      const unsigned long long k = ordered_key(v);
+      lo[d] = min(lo[d], k);
+      hi[d] = max(hi[d], k);
+    }
   }
-  const unsigned long long k = ordered_key(v);
-  atomicMin(mn + d, k);
-  atomicMax(mx + d, k);
+  for (int d = 0; d < 3; ++d) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+  }
+  b = __any_sync(0xffffffffu, b);
+  if ((threadIdx.x & 31) == 0) {
+    for (int d = 0; d < 3; ++d) {
+      atomicMin(mn + d, lo[d]);
+      atomicMax(mx + d, hi[d]);
+    }
+    if (b) atomicOr(bad, 1);
+  }
 }
 
 __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ p,
@@ -153,7 +171,9 @@ void launch_bbox(const double* x, int64_t n, double* red, cudaStream_t s) {
   cudaMemsetAsync(mn, 0xff, 3 * sizeof(unsigned long long), s);
   cudaMemsetAsync(mx, 0x00, 3 * sizeof(unsigned long long), s);
   cudaMemsetAsync(bad, 0, sizeof(int), s);
-  if (n > 0) k_bbox<<<blocks_for(3 * n), kThreads, 0, s>>>(x, 3 * n, mn, mx, bad);
+  if (n > 0)
+    k_bbox<<<static_cast<unsigned>(std::min<int64_t>(blocks_for(n), 1216)), kThreads, 0, s>>>(
+        x, n, mn, mx, bad);
 }
 
 void launch_kick_drift(double* x, double* p, const double* f, int64_t n, double kick, double drift,

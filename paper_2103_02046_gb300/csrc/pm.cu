@@ -297,13 +297,14 @@ __global__ void k_green_multiply(Geom g, const C2<T>* __restrict__ qhat, const T
                                  double* __restrict__ energy, size_t ncplx) {
   const int Hx = g.M[0] / 2 + 1;
   const int Mz = g.M[2];
-  const size_t total = static_cast<size_t>(Hx) * g.M[1] * (Mz / 2 + 1);
-  const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  // grid: x covers the (kx, ky) plane with 32-bit indices, y is kz in [0, Mz/2]
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool inside = t < static_cast<uint32_t>(Hx) * static_cast<uint32_t>(g.M[1]);
   double e = 0.0;
-  if (t < total) {
-    const int kx = static_cast<int>(t % Hx);
-    const int ky = static_cast<int>((t / Hx) % g.M[1]);
-    const int kz = static_cast<int>(t / (static_cast<size_t>(Hx) * g.M[1]));
+  if (inside) {
+    const int kx = static_cast<int>(t % static_cast<uint32_t>(Hx));
+    const int ky = static_cast<int>(t / static_cast<uint32_t>(Hx));
+    const int kz = blockIdx.y;
     const int kz2 = (Mz - kz) % Mz;
     const size_t ia = (static_cast<size_t>(kz) * g.M[1] + ky) * Hx + kx;
     const size_t ib = (static_cast<size_t>(kz2) * g.M[1] + ky) * Hx + kx;
@@ -664,16 +665,16 @@ void launch_dipole_deposit(const p3m_ctx* c, int64_t n, const double* w) {
 
 void launch_green_multiply(const p3m_ctx* c, bool want_phi, bool want_diff, bool want_energy) {
   const Geom& g = c->g;
-  const size_t total = static_cast<size_t>(g.M[0] / 2 + 1) * g.M[1] * (g.M[2] / 2 + 1);
+  const dim3 grid(blocks_for(static_cast<uint64_t>(g.M[0] / 2 + 1) * g.M[1]), g.M[2] / 2 + 1);
   double* en = want_energy ? c->energy_acc + 1 : nullptr;
   if (c->fp32)
-    k_green_multiply<float><<<blocks_for(total), kThreads, 0, c->work>>>(
+    k_green_multiply<float><<<grid, kThreads, 0, c->work>>>(
         g, static_cast<const float2*>(c->qhat), static_cast<const float*>(c->khat_f),
         static_cast<const float2*>(c->khat_i), c->dfac,
         want_diff ? static_cast<float2*>(c->fhat) : nullptr,
         want_phi ? static_cast<float2*>(c->phihat) : nullptr, en, c->n_cplx);
   else
-    k_green_multiply<double><<<blocks_for(total), kThreads, 0, c->work>>>(
+    k_green_multiply<double><<<grid, kThreads, 0, c->work>>>(
         g, static_cast<const double2*>(c->qhat), static_cast<const double*>(c->khat_f),
         static_cast<const double2*>(c->khat_i), nullptr, nullptr,
         want_phi ? static_cast<double2*>(c->phihat) : nullptr, en, c->n_cplx);

@@ -41,16 +41,6 @@ struct Acc2 {
   __device__ __forceinline__ float value() const { return hi + lo; }
 };
 
-__device__ __forceinline__ void pair_terms(float r2, float kappa, float c2k, float& fco,
-                                           float& pot) {
-  const float rinv = rsqrtf(r2);
-  const float x = kappa * (r2 * rinv);
-  const float ec = erfcf(x);
-  const float ex = __expf(-x * x);
-  pot = ec * rinv;
-  fco = (pot + c2k * ex) * (rinv * rinv);
-}
-
 __device__ __forceinline__ void pair_terms(double r2, double kappa, double c2k, double& fco,
                                            double& pot) {
   const double r = sqrt(r2);
@@ -63,17 +53,6 @@ __device__ __forceinline__ void pair_terms(double r2, double kappa, double c2k, 
 
 template <typename T>
 struct SumT;
-template <>
-struct SumT<float> {
-  Acc2 v[4];
-  __device__ void zero() {
-    for (int k = 0; k < 4; ++k) v[k].hi = v[k].lo = 0.f;
-  }
-  __device__ void fold(const float r[4]) {
-    for (int k = 0; k < 4; ++k) v[k].add(r[k]);
-  }
-  __device__ float get(int k) const { return v[k].value(); }
-};
 template <>
 struct SumT<double> {
   double v[4];
@@ -262,6 +241,197 @@ __global__ void __launch_bounds__(kThreads)
   warp_add_u64(ni, pairs + 1);
 }
 
+// ------------------------------------------------------------------------------------------
+// FP32 short range with in-warp compaction. Each lane owns one sorted particle i and walks its
+// candidate rows with a warp-uniform loop (one candidate per lane per step). Candidates that
+// pass the cutoff test are pushed, with their separation, onto a per-warp stack in shared
+// memory; whenever 32 are waiting, all 32 lanes evaluate one pair each (no divergence in the
+// pair function) and add the result to the owner's slot with shared-memory atomics. The owner
+// folds its slot into a two-float (TwoSum) accumulator every kFoldEvery batches.
+// The pair function uses one ex2 for both e^{-kappa^2 rho^2} terms and the fitted polynomial
+// R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}.
+// ------------------------------------------------------------------------------------------
+constexpr int kWarps = kThreads / 32;
+constexpr int kStack = 64;
+constexpr int kFoldEvery = 8;
+
+template <int kDeg>
+__device__ __forceinline__ void pair_poly(const PairPoly& P, float r2, float& fco, float& pot) {
+  const float rinv = rsqrtf(r2);
+  const float rho = r2 * rinv;
+  const float t = fmaf(2.f, rho, -1.f);
+  float R = P.c[kDeg];
+#pragma unroll
+  for (int m = kDeg - 1; m >= 0; --m) R = fmaf(R, t, P.c[m]);
+  const float ex = exp2f(-P.kappa2_log2e * r2);
+  pot = R * ex * rinv;
+  fco = fmaf(P.c2k, ex, pot) * (rinv * rinv);
+}
+
+__device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restrict__ starts,
+                                          float px, float py, float pz, int cy, int cz, int r,
+                                          uint32_t& j0, uint32_t& j1) {
+  j0 = j1 = 0;
+  const int ry = cy + (r % 3) - 1, rz = cz + (r / 3) - 1;
+  if (ry < 0 || ry >= g.nc[1] || rz < 0 || rz >= g.nc[2]) return;
+  const float slack = kFilterSlack;
+  const float cwy = static_cast<float>(g.cw[1]), cwz = static_cast<float>(g.cw[2]);
+  const float yl = ry * cwy, yh = yl + cwy, zl = rz * cwz, zh = zl + cwz;
+  const float dy = py < yl ? yl - py : (py > yh ? py - yh : 0.f);
+  const float dz = pz < zl ? zl - pz : (pz > zh ? pz - zh : 0.f);
+  const float d2 = dy * dy + dz * dz;
+  if (d2 >= 1.f + slack) return;
+  const float w = sqrtf(fmaxf(1.f - d2, 0.f)) + slack;
+  const float iwx = static_cast<float>(g.inv_cw[0]);
+  const int c0 = max(static_cast<int>(floorf((px - w) * iwx)), 0);
+  const int c1 = min(static_cast<int>(floorf((px + w) * iwx)), g.nc[0] - 1);
+  if (c0 > c1) return;
+  const uint32_t base = (static_cast<uint32_t>(rz) * g.nc[1] + ry) * g.nc[0];
+  j0 = starts[base + c0];
+  j1 = starts[base + c1 + 1];
+}
+
+template <int kDeg>
+__global__ void __launch_bounds__(kThreads)
+    k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
+             const float4* __restrict__ hi, const float4* __restrict__ lo,
+             const uint32_t* __restrict__ starts, float4* __restrict__ fpp,
+             double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
+  __shared__ float4 stack_s[kWarps][kStack];
+  __shared__ float slot_s[kWarps][4][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* stk = stack_s[warp];
+  float(*slot)[33] = slot_s[warp];
+  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  const uint32_t N = *total;
+  const bool alive = i < N;
+  float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), li = pi;
+  if (alive) {
+    pi = hi[i];
+    li = lo[i];
+  }
+  for (int k = 0; k < 4; ++k) slot[k][lane] = 0.f;
+  Acc2 sum[4];
+  for (int k = 0; k < 4; ++k) sum[k].hi = sum[k].lo = 0.f;
+  const int cy = min(max(static_cast<int>(floorf(pi.y * static_cast<float>(g.inv_cw[1]))), 0),
+                     g.nc[1] - 1);
+  const int cz = min(max(static_cast<int>(floorf(pi.z * static_cast<float>(g.inv_cw[2]))), 0),
+                     g.nc[2] - 1);
+  int row = 0;
+  uint32_t j = 0, jend = 0;
+  if (alive) {
+    while (row < 9 && j >= jend) row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, row++, j, jend);
+  }
+  unsigned long long np = 0;
+  int depth = 0, batches = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  __syncwarp();
+  for (;;) {
+    const bool active = j < jend;
+    if (__ballot_sync(0xffffffffu, active) == 0u) break;
+    bool hit = false;
+    float rx = 0.f, ry = 0.f, rz = 0.f;
+    if (active) {
+      if (j != i) {
+        const float4 hj = hi[j];
+        rx = pi.x - hj.x;
+        ry = pi.y - hj.y;
+        rz = pi.z - hj.z;
+        float r2 = rx * rx + ry * ry + rz * rz;
+        if (r2 < 1.f + kFilterSlack) {
+          const float4 lj = lo[j];
+          rx += li.x - lj.x;
+          ry += li.y - lj.y;
+          rz += li.z - lj.z;
+          r2 = rx * rx + ry * ry + rz * rz;
+          hit = r2 < 1.f && r2 > 0.f;
+        }
+      }
+      if (++j >= jend)
+        while (row < 9 && j >= jend) row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, row++, j, jend);
+    }
+    const unsigned hb = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+      stk[depth + __popc(hb & lt)] = make_float4(rx, ry, rz, __int_as_float(lane));
+      ++np;
+    }
+    depth += __popc(hb);
+    if (depth >= 32) {
+      __syncwarp();
+      const float4 e = stk[depth - 32 + lane];
+      const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
+      float fco, pot;
+      pair_poly<kDeg>(P, r2, fco, pot);
+      const int o = __float_as_int(e.w);
+      atomicAdd(&slot[0][o], fco * e.x);
+      atomicAdd(&slot[1][o], fco * e.y);
+      atomicAdd(&slot[2][o], fco * e.z);
+      atomicAdd(&slot[3][o], pot);
+      depth -= 32;
+      __syncwarp();
+      if (++batches == kFoldEvery) {
+        batches = 0;
+        for (int k = 0; k < 4; ++k) {
+          sum[k].add(slot[k][lane]);
+          slot[k][lane] = 0.f;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+  if (lane < depth) {
+    const float4 e = stk[lane];
+    const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
+    float fco, pot;
+    pair_poly<kDeg>(P, r2, fco, pot);
+    const int o = __float_as_int(e.w);
+    atomicAdd(&slot[0][o], fco * e.x);
+    atomicAdd(&slot[1][o], fco * e.y);
+    atomicAdd(&slot[2][o], fco * e.z);
+    atomicAdd(&slot[3][o], pot);
+  }
+  __syncwarp();
+  for (int k = 0; k < 4; ++k) sum[k].add(slot[k][lane]);
+  unsigned long long ni = 0;
+  if (alive && g.pp_bc) {
+    // images within r_c of particles less than r_c above the cathode (rare): plain loop
+    const double zi = static_cast<double>(pi.z) + static_cast<double>(li.z);
+    if (zi - 0.5 * g.img_c < 1.0) {
+      const float mz = static_cast<float>(g.img_c - zi);
+      const float ch = static_cast<float>(g.img_c);
+      const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
+      for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t j0, uint32_t j1) {
+        float rowv[4] = {0.f, 0.f, 0.f, 0.f};
+        for (uint32_t jj = j0; jj < j1; ++jj) {
+          const float4 hj = hi[jj], lj = lo[jj];
+          const float ax = (pi.x - hj.x) + (li.x - lj.x);
+          const float ay = (pi.y - hj.y) + (li.y - lj.y);
+          const float s = pi.z + hj.z;
+          const float bp = s - pi.z;
+          const float e = (pi.z - (s - bp)) + (hj.z - bp);
+          const float az = ((s - ch) + e) + ((li.z + lj.z) - cl);
+          const float r2 = ax * ax + ay * ay + az * az;
+          if (r2 < 1.f && r2 > 0.f) {
+            float fco, pot;
+            pair_poly<kDeg>(P, r2, fco, pot);
+            rowv[0] -= fco * ax;
+            rowv[1] -= fco * ay;
+            rowv[2] -= fco * az;
+            rowv[3] -= pot;
+            ++ni;
+          }
+        }
+        for (int k = 0; k < 4; ++k) sum[k].add(rowv[k]);
+      });
+    }
+  }
+  if (alive) fpp[i] = make_float4(sum[0].value(), sum[1].value(), sum[2].value(), sum[3].value());
+  if (energy) block_reduce_add(alive ? static_cast<double>(sum[3].value()) : 0.0, energy);
+  warp_add_u64(np, pairs);
+  warp_add_u64(ni, pairs + 1);
+}
+
 // Vector-Jacobian product of the short-range force map, into acc (sorted order):
 //   free pairs:  acc_i += H(d_ij) (w_i - w_j)
 //   image pairs: acc_i -= H(d_ij) (w_i - S w_j)   (S = diag(1, 1, -1), image charge -q)
@@ -387,11 +557,25 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
   if (n == 0) return;
   const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   const uint32_t* total = c->starts + c->nkeys;
-  if (c->fp32)
-    k_pp<float, PosF><<<blocks, kThreads, 0, s>>>(
-        c->g, total, PosF{static_cast<const float4*>(c->recp), c->recl}, c->starts, c->fpp,
-        c->energy_acc, c->pair_acc);
-  else
+  if (c->fp32) {
+    auto run = [&](auto kern) {
+      kern<<<blocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
+                                       c->recl, c->starts, static_cast<float4*>(c->fpp),
+                                       c->energy_acc, c->pair_acc);
+    };
+    switch (c->poly.deg) {
+      case 6: run(k_pp_f32<6>); break;
+      case 7: run(k_pp_f32<7>); break;
+      case 8: run(k_pp_f32<8>); break;
+      case 9: run(k_pp_f32<9>); break;
+      case 10: run(k_pp_f32<10>); break;
+      case 11: run(k_pp_f32<11>); break;
+      case 12: run(k_pp_f32<12>); break;
+      case 13: run(k_pp_f32<13>); break;
+      case 14: run(k_pp_f32<14>); break;
+      default: run(k_pp_f32<15>); break;
+    }
+  } else
     k_pp<double, PosD><<<blocks, kThreads, 0, s>>>(
         c->g, total, PosD{static_cast<const Rec64*>(c->recp)}, c->starts, c->fpp, c->energy_acc,
         c->pair_acc);
