@@ -98,6 +98,11 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   g.pp_bc = p->pp_bc;
   g.zc = p->z_cathode;
   g.img_c = 2.0 * (p->z_cathode - p->lo[2]) / g.rc;
+  g.inv_rc = 1.0 / g.rc;
+  for (int d = 0; d < 3; ++d) {
+    g.inv_h[d] = 1.0 / g.h[d];
+    g.fscale[d] = -p->q / g.h[d];
+  }
   g.q = p->q;
   g.mass = p->mass;
   g.ke = 1.0 / (4.0 * kPi * kEps0);
@@ -283,7 +288,7 @@ p3m_status forces_impl(p3m_ctx* c, const double* x, int64_t n, double* f, double
     launch_deposit(c, n);
     c->deposited = true;
     cudaEventRecord(c->tev[3], st);
-    p3m_status s = mesh_solve(c, false, true, true);
+    p3m_status s = mesh_solve(c, false, true, energy != nullptr);
     if (s != P3M_OK) return s;
   } else {
     cudaEventRecord(c->tev[3], st);

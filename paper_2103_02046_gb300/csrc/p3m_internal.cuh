@@ -45,6 +45,9 @@ struct Geom {
   double a[3];       // h_d / r_c
   double cw[3];      // cell edges in cutoff units (y, z: >= 1; x: 1 / nsub)
   double inv_cw[3];
+  double inv_h[3];   // 1 / h_d
+  double inv_rc;     // 1 / r_c
+  double fscale[3];  // -q / h_d: long-range force per volt of mesh-unit gradient
   double img_c;      // 2 (z_c - lo_z) / r_c: the image of z (cutoff units) is img_c - z
   double kappa_eff;  // alpha * r_c
 };

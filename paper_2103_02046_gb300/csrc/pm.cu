@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kDepThreads)
     T wv[3] = {T(0), T(0), T(0)};
     if (kDipole) {
       const long long idx = orig_index(recp, i);
-      for (int d = 0; d < 3; ++d) wv[d] = static_cast<T>(w[3 * idx + d] / g.h[d]);
+      for (int d = 0; d < 3; ++d) wv[d] = static_cast<T>(w[3 * idx + d] * g.inv_h[d]);
     }
     for (int c = 0; c < S; ++c)
       for (int b = 0; b < S; ++b)
@@ -321,9 +321,12 @@ __global__ void k_green_multiply(Geom g, const C2<T>* __restrict__ qhat, const T
       bb.x -= tb.x;
       bb.y -= tb.y;
     }
-    const double wx = (kx == 0 || 2 * kx == g.M[0]) ? 1.0 : 2.0;
-    e = wx * (static_cast<double>(a.x) * ba.x + static_cast<double>(a.y) * ba.y);
-    if (kz2 != kz) e += wx * (static_cast<double>(b.x) * bb.x + static_cast<double>(b.y) * bb.y);
+    if (energy) {
+      const T wx = (kx == 0 || 2 * kx == g.M[0]) ? T(1) : T(2);
+      T ee = wx * (a.x * ba.x + a.y * ba.y);
+      if (kz2 != kz) ee += wx * (b.x * bb.x + b.y * bb.y);
+      e = static_cast<double>(ee);
+    }
     if (phihat) {
       phihat[ia] = ba;
       if (kz2 != kz) phihat[ib] = bb;
@@ -443,7 +446,7 @@ __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
       grad_from_diff(g, field, nreal, ax, G);
     else
       grad_from_phi(g, field, ax, G);
-    for (int d = 0; d < 3; ++d) F[d] = -g.q / g.h[d] * static_cast<double>(G[d]);
+    for (int d = 0; d < 3; ++d) F[d] = g.fscale[d] * static_cast<double>(G[d]);
   }
   if (parts & 1) {
     if constexpr (sizeof(T) == 4) {
@@ -554,7 +557,7 @@ __global__ void k_vjp_gather(Geom g, const uint32_t* __restrict__ total,
     const double wv[3] = {w[3 * idx], w[3 * idx + 1], w[3 * idx + 2]};
     for (int d = 0; d < 3; ++d) {
       double hw = 0.0;
-      for (int e = 0; e < 3; ++e) hw += static_cast<double>(H[d][e]) / (g.h[d] * g.h[e]) * wv[e];
+      for (int e = 0; e < 3; ++e) hw += static_cast<double>(H[d][e]) * (g.inv_h[d] * g.inv_h[e]) * wv[e];
       acc[3 * i + d] += -g.q * hw;
     }
   } else {
@@ -564,7 +567,7 @@ __global__ void k_vjp_gather(Geom g, const uint32_t* __restrict__ total,
     else
       grad_from_phi(g, field, ax, G);
     for (int d = 0; d < 3; ++d)
-      out[3 * idx + d] = acc[3 * i + d] - g.q * static_cast<double>(G[d]) / g.h[d];
+      out[3 * idx + d] = acc[3 * i + d] + g.fscale[d] * static_cast<double>(G[d]);
   }
 }
 

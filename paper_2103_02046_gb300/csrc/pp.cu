@@ -16,8 +16,8 @@
 //
 // FP32: candidates are tested with the hi parts of the cutoff-unit positions; in-cutoff pairs
 // recompute the separation as (hi_i - hi_j) + (lo_i - lo_j), exact to FP32 relative rounding at
-// any distance. Row sums are accumulated in FP32 and folded into a two-float (TwoSum)
-// accumulator per row, so the per-particle sum is compensated at a few additions per row.
+// any distance. Partial sums are folded into a two-float (TwoSum) accumulator every few pairs,
+// so the per-particle sum is compensated at a small fraction of an addition per pair.
 #include <cmath>
 
 #include "p3m_internal.cuh"
@@ -242,17 +242,19 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ------------------------------------------------------------------------------------------
-// FP32 short range with in-warp compaction. Each lane owns one sorted particle i and walks its
-// candidate rows with a warp-uniform loop (one candidate per lane per step). Candidates that
-// pass the cutoff test are pushed, with their separation, onto a per-warp stack in shared
-// memory; whenever 32 are waiting, all 32 lanes evaluate one pair each (no divergence in the
-// pair function) and add the result to the owner's slot with shared-memory atomics. The owner
-// folds its slot into a two-float (TwoSum) accumulator every kFoldEvery batches.
+// FP32 short range, "scan until hit, then evaluate together". Each lane owns one sorted
+// particle i. A round has two phases:
+//   scan:     every lane walks its own candidate rows (one contiguous, pruned index range per
+//             row) with the cheap hi-part test until it holds kHits in-cutoff separations (made
+//             exact with the lo parts) or runs out of rows;
+//   evaluate: all lanes evaluate their held pairs in lock-step.
+// The divergent part is the ~10-instruction candidate test; the ~25-instruction pair function
+// runs with nearly all lanes active. Each lane accumulates its own force in registers, folded
+// into a two-float (TwoSum) accumulator every kFoldEvery rounds.
 // The pair function uses one ex2 for both e^{-kappa^2 rho^2} terms and the fitted polynomial
 // R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}.
 // ------------------------------------------------------------------------------------------
-constexpr int kWarps = kThreads / 32;
-constexpr int kStack = 64;
+constexpr int kHits = 2;
 constexpr int kFoldEvery = 8;
 
 template <int kDeg>
@@ -297,11 +299,6 @@ __global__ void __launch_bounds__(kThreads)
              const float4* __restrict__ hi, const float4* __restrict__ lo,
              const uint32_t* __restrict__ starts, float4* __restrict__ fpp,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
-  __shared__ float4 stack_s[kWarps][kStack];
-  __shared__ float slot_s[kWarps][4][33];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* stk = stack_s[warp];
-  float(*slot)[33] = slot_s[warp];
   const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
   const uint32_t N = *total;
   const bool alive = i < N;
@@ -310,89 +307,73 @@ __global__ void __launch_bounds__(kThreads)
     pi = hi[i];
     li = lo[i];
   }
-  for (int k = 0; k < 4; ++k) slot[k][lane] = 0.f;
   Acc2 sum[4];
   for (int k = 0; k < 4; ++k) sum[k].hi = sum[k].lo = 0.f;
+  float part[4] = {0.f, 0.f, 0.f, 0.f};
   const int cy = min(max(static_cast<int>(floorf(pi.y * static_cast<float>(g.inv_cw[1]))), 0),
                      g.nc[1] - 1);
   const int cz = min(max(static_cast<int>(floorf(pi.z * static_cast<float>(g.inv_cw[2]))), 0),
                      g.nc[2] - 1);
-  int row = 0;
+  int row = alive ? 0 : 9;
   uint32_t j = 0, jend = 0;
-  if (alive) {
-    while (row < 9 && j >= jend) row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, row++, j, jend);
-  }
   unsigned long long np = 0;
-  int depth = 0, batches = 0;
-  const unsigned lt = (1u << lane) - 1u;
-  __syncwarp();
+  int rounds = 0;
   for (;;) {
-    const bool active = j < jend;
-    if (__ballot_sync(0xffffffffu, active) == 0u) break;
-    bool hit = false;
-    float rx = 0.f, ry = 0.f, rz = 0.f;
-    if (active) {
-      if (j != i) {
-        const float4 hj = hi[j];
-        rx = pi.x - hj.x;
-        ry = pi.y - hj.y;
-        rz = pi.z - hj.z;
-        float r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 < 1.f + kFilterSlack) {
-          const float4 lj = lo[j];
-          rx += li.x - lj.x;
-          ry += li.y - lj.y;
-          rz += li.z - lj.z;
-          r2 = rx * rx + ry * ry + rz * rz;
-          hit = r2 < 1.f && r2 > 0.f;
+    // scan
+    float hx[kHits], hy[kHits], hz[kHits];
+    int nh = 0;
+    while (nh < kHits) {
+      if (j >= jend) {
+        if (row >= 9) break;
+        row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, row++, j, jend);
+        continue;
+      }
+      const uint32_t jj = j++;
+      const float4 hj = hi[jj];
+      float rx = pi.x - hj.x, ry = pi.y - hj.y, rz = pi.z - hj.z;
+      float r2 = rx * rx + ry * ry + rz * rz;
+      if (r2 < 1.f + kFilterSlack && jj != i) {
+        const float4 lj = lo[jj];
+        rx += li.x - lj.x;
+        ry += li.y - lj.y;
+        rz += li.z - lj.z;
+        r2 = rx * rx + ry * ry + rz * rz;
+        if (r2 < 1.f && r2 > 0.f) {
+#pragma unroll
+          for (int k = 0; k < kHits; ++k)
+            if (k == nh) {
+              hx[k] = rx;
+              hy[k] = ry;
+              hz[k] = rz;
+            }
+          ++nh;
         }
       }
-      if (++j >= jend)
-        while (row < 9 && j >= jend) row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, row++, j, jend);
     }
-    const unsigned hb = __ballot_sync(0xffffffffu, hit);
-    if (hit) {
-      stk[depth + __popc(hb & lt)] = make_float4(rx, ry, rz, __int_as_float(lane));
-      ++np;
+    if (__ballot_sync(0xffffffffu, nh > 0) == 0u) break;
+    // evaluate
+#pragma unroll
+    for (int k = 0; k < kHits; ++k) {
+      if (k < nh) {
+        const float r2 = hx[k] * hx[k] + hy[k] * hy[k] + hz[k] * hz[k];
+        float fco, pot;
+        pair_poly<kDeg>(P, r2, fco, pot);
+        part[0] = fmaf(fco, hx[k], part[0]);
+        part[1] = fmaf(fco, hy[k], part[1]);
+        part[2] = fmaf(fco, hz[k], part[2]);
+        part[3] += pot;
+      }
     }
-    depth += __popc(hb);
-    if (depth >= 32) {
-      __syncwarp();
-      const float4 e = stk[depth - 32 + lane];
-      const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
-      float fco, pot;
-      pair_poly<kDeg>(P, r2, fco, pot);
-      const int o = __float_as_int(e.w);
-      atomicAdd(&slot[0][o], fco * e.x);
-      atomicAdd(&slot[1][o], fco * e.y);
-      atomicAdd(&slot[2][o], fco * e.z);
-      atomicAdd(&slot[3][o], pot);
-      depth -= 32;
-      __syncwarp();
-      if (++batches == kFoldEvery) {
-        batches = 0;
-        for (int k = 0; k < 4; ++k) {
-          sum[k].add(slot[k][lane]);
-          slot[k][lane] = 0.f;
-        }
-        __syncwarp();
+    np += nh;
+    if (++rounds == kFoldEvery) {
+      rounds = 0;
+      for (int k = 0; k < 4; ++k) {
+        sum[k].add(part[k]);
+        part[k] = 0.f;
       }
     }
   }
-  __syncwarp();
-  if (lane < depth) {
-    const float4 e = stk[lane];
-    const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
-    float fco, pot;
-    pair_poly<kDeg>(P, r2, fco, pot);
-    const int o = __float_as_int(e.w);
-    atomicAdd(&slot[0][o], fco * e.x);
-    atomicAdd(&slot[1][o], fco * e.y);
-    atomicAdd(&slot[2][o], fco * e.z);
-    atomicAdd(&slot[3][o], pot);
-  }
-  __syncwarp();
-  for (int k = 0; k < 4; ++k) sum[k].add(slot[k][lane]);
+  for (int k = 0; k < 4; ++k) sum[k].add(part[k]);
   unsigned long long ni = 0;
   if (alive && g.pp_bc) {
     // images within r_c of particles less than r_c above the cathode (rare): plain loop

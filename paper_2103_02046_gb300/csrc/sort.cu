@@ -16,13 +16,14 @@ constexpr int kScanItems = 4;  // per thread
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // Validity of one particle and its cell. Valid: the assignment support lies inside the mesh
-// (TSC: floor(s + 1/2) in [1, n - 2]; CIC: floor(s) in [0, n - 2]) with s = (x - lo) / h and,
+// (TSC: floor(s + 1/2) in [1, n - 2]; CIC: floor(s) in [0, n - 2]) with s = (x - lo) / h
+// (computed with the reciprocal: FP64 division is slow on this part) and,
 // with the cathode in the long-range solve, z > z_cathode. Returns 0 if valid, else an error bit.
 __device__ __forceinline__ int particle_cell(const Geom& g, const double* __restrict__ xi,
                                              int cell[3]) {
   int err = 0;
   for (int d = 0; d < 3; ++d) {
-    const double s = (xi[d] - g.lo[d]) / g.h[d];
+    const double s = (xi[d] - g.lo[d]) * g.inv_h[d];
     if (!(s == s)) return kErrNaN;
     const double c = (g.order == 2) ? floor(s + 0.5) : floor(s);
     const double cmin = (g.order == 2) ? 1.0 : 0.0;
@@ -31,7 +32,7 @@ __device__ __forceinline__ int particle_cell(const Geom& g, const double* __rest
   if (g.pm_bc && !(xi[2] > g.zc)) err = kErrRange;
   if (err) return err;
   for (int d = 0; d < 3; ++d) {
-    const double xr = (xi[d] - g.lo[d]) / g.rc;
+    const double xr = (xi[d] - g.lo[d]) * g.inv_rc;
     const int c = static_cast<int>(floor(xr * g.inv_cw[d]));
     cell[d] = min(max(c, 0), g.nc[d] - 1);
   }
@@ -167,8 +168,9 @@ __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
   int c[3];
   for (int d = 0; d < 3; ++d) {
     const double v = x[3 * i + d];
-    xr[d] = (v - g.lo[d]) / g.rc;
-    const double s = (v - g.lo[d]) / g.h[d];
+    const double dv = v - g.lo[d];
+    xr[d] = dv * g.inv_rc;
+    const double s = dv * g.inv_h[d];
     const double cn = (g.order == 2) ? floor(s + 0.5) : floor(s);
     u[d] = s - cn;
     c[d] = static_cast<int>(cn);
