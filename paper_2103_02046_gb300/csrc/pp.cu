@@ -242,20 +242,21 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ------------------------------------------------------------------------------------------
-// FP32 short range, "scan until hit, then evaluate together". Each lane owns one sorted
-// particle i. A round has two phases:
-//   scan:     every lane walks its own candidate rows (one contiguous, pruned index range per
-//             row) with the cheap hi-part test until it holds kHits in-cutoff separations (made
-//             exact with the lo parts) or runs out of rows;
-//   evaluate: all lanes evaluate their held pairs in lock-step.
-// The divergent part is the ~10-instruction candidate test; the ~25-instruction pair function
-// runs with nearly all lanes active. Each lane accumulates its own force in registers, folded
-// into a two-float (TwoSum) accumulator every kFoldEvery rounds.
+// FP32 short range, warp tiles. A warp owns 32 consecutive sorted particles (one per lane;
+// they lie in a stretch of about two cutoffs of one x-row). For every neighbour row of the
+// group's bounding box it streams the row's pruned candidate run in chunks of 32: the chunk is
+// loaded coalesced into shared memory, then each candidate j is broadcast to all lanes and
+// tested against every lane's particle. Pairs inside the cutoff are pushed onto a per-warp
+// stack (separation made exact with the lo parts); whenever 32 are waiting, all lanes evaluate
+// one pair each and add it to the owner's shared-memory slot. Every control decision is
+// warp-uniform, so no lane waits on another lane's loop.
+// The owner folds its slot into a two-float (TwoSum) accumulator every kFoldEvery batches.
 // The pair function uses one ex2 for both e^{-kappa^2 rho^2} terms and the fitted polynomial
 // R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}.
 // ------------------------------------------------------------------------------------------
-constexpr int kHits = 2;
-constexpr int kFoldEvery = 8;
+constexpr int kWarps = kThreads / 32;
+constexpr int kStack = 64;
+constexpr int kFoldEvery = 4;
 
 template <int kDeg>
 __device__ __forceinline__ void pair_poly(const PairPoly& P, float r2, float& fco, float& pot) {
@@ -270,110 +271,134 @@ __device__ __forceinline__ void pair_poly(const PairPoly& P, float r2, float& fc
   fco = fmaf(P.c2k, ex, pot) * (rinv * rinv);
 }
 
-__device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restrict__ starts,
-                                          float px, float py, float pz, int cy, int cz, int r,
-                                          uint32_t& j0, uint32_t& j1) {
-  j0 = j1 = 0;
-  const int ry = cy + (r % 3) - 1, rz = cz + (r / 3) - 1;
-  if (ry < 0 || ry >= g.nc[1] || rz < 0 || rz >= g.nc[2]) return;
-  const float slack = kFilterSlack;
-  const float cwy = static_cast<float>(g.cw[1]), cwz = static_cast<float>(g.cw[2]);
-  const float yl = ry * cwy, yh = yl + cwy, zl = rz * cwz, zh = zl + cwz;
-  const float dy = py < yl ? yl - py : (py > yh ? py - yh : 0.f);
-  const float dz = pz < zl ? zl - pz : (pz > zh ? pz - zh : 0.f);
-  const float d2 = dy * dy + dz * dz;
-  if (d2 >= 1.f + slack) return;
-  const float w = sqrtf(fmaxf(1.f - d2, 0.f)) + slack;
-  const float iwx = static_cast<float>(g.inv_cw[0]);
-  const int c0 = max(static_cast<int>(floorf((px - w) * iwx)), 0);
-  const int c1 = min(static_cast<int>(floorf((px + w) * iwx)), g.nc[0] - 1);
-  if (c0 > c1) return;
-  const uint32_t base = (static_cast<uint32_t>(rz) * g.nc[1] + ry) * g.nc[0];
-  j0 = starts[base + c0];
-  j1 = starts[base + c1 + 1];
+__device__ __forceinline__ float warp_min(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
 template <int kDeg>
-__global__ void __launch_bounds__(kThreads)
+__device__ __forceinline__ void eval_entry(const PairPoly& P, float4 e, float (*slot)[33]) {
+  const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
+  float fco, pot;
+  pair_poly<kDeg>(P, r2, fco, pot);
+  const int o = __float_as_int(e.w);
+  atomicAdd(&slot[0][o], fco * e.x);
+  atomicAdd(&slot[1][o], fco * e.y);
+  atomicAdd(&slot[2][o], fco * e.z);
+  atomicAdd(&slot[3][o], pot);
+}
+
+template <int kDeg>
+__global__ void __launch_bounds__(kThreads, 8)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
              const float4* __restrict__ hi, const float4* __restrict__ lo,
              const uint32_t* __restrict__ starts, float4* __restrict__ fpp,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
-  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  __shared__ float4 jh_s[kWarps][32], jl_s[kWarps][32];
+  __shared__ float4 stack_s[kWarps][kStack];
+  __shared__ float slot_s[kWarps][4][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* jh = jh_s[warp];
+  float4* jl = jl_s[warp];
+  float4* stk = stack_s[warp];
+  float(*slot)[33] = slot_s[warp];
   const uint32_t N = *total;
+  const uint32_t i = (blockIdx.x * kWarps + warp) * 32u + lane;
   const bool alive = i < N;
+  const bool warp_alive = __any_sync(0xffffffffu, alive);
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), li = pi;
   if (alive) {
     pi = hi[i];
     li = lo[i];
   }
+  for (int k = 0; k < 4; ++k) slot[k][lane] = 0.f;
   Acc2 sum[4];
   for (int k = 0; k < 4; ++k) sum[k].hi = sum[k].lo = 0.f;
-  float part[4] = {0.f, 0.f, 0.f, 0.f};
-  const int cy = min(max(static_cast<int>(floorf(pi.y * static_cast<float>(g.inv_cw[1]))), 0),
-                     g.nc[1] - 1);
-  const int cz = min(max(static_cast<int>(floorf(pi.z * static_cast<float>(g.inv_cw[2]))), 0),
-                     g.nc[2] - 1);
-  int row = alive ? 0 : 9;
-  uint32_t j = 0, jend = 0;
   unsigned long long np = 0;
-  int rounds = 0;
-  for (;;) {
-    // scan
-    float hx[kHits], hy[kHits], hz[kHits];
-    int nh = 0;
-    while (nh < kHits) {
-      if (j >= jend) {
-        if (row >= 9) break;
-        row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, row++, j, jend);
-        continue;
-      }
-      const uint32_t jj = j++;
-      const float4 hj = hi[jj];
-      float rx = pi.x - hj.x, ry = pi.y - hj.y, rz = pi.z - hj.z;
-      float r2 = rx * rx + ry * ry + rz * rz;
-      if (r2 < 1.f + kFilterSlack && jj != i) {
-        const float4 lj = lo[jj];
-        rx += li.x - lj.x;
-        ry += li.y - lj.y;
-        rz += li.z - lj.z;
-        r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 < 1.f && r2 > 0.f) {
-#pragma unroll
-          for (int k = 0; k < kHits; ++k)
-            if (k == nh) {
-              hx[k] = rx;
-              hy[k] = ry;
-              hz[k] = rz;
+  const unsigned lt = (1u << lane) - 1u;
+  int depth = 0, batches = 0;
+  if (warp_alive) {
+    const float big = 3.0e38f;
+    const float xmin = warp_min(alive ? pi.x : big), xmax = warp_max(alive ? pi.x : -big);
+    const float ymin = warp_min(alive ? pi.y : big), ymax = warp_max(alive ? pi.y : -big);
+    const float zmin = warp_min(alive ? pi.z : big), zmax = warp_max(alive ? pi.z : -big);
+    const float slack = kFilterSlack;
+    const float cwy = static_cast<float>(g.cw[1]), cwz = static_cast<float>(g.cw[2]);
+    const float iwx = static_cast<float>(g.inv_cw[0]), iwy = static_cast<float>(g.inv_cw[1]),
+                iwz = static_cast<float>(g.inv_cw[2]);
+    const int y0 = max(static_cast<int>(floorf((ymin - 1.f - slack) * iwy)), 0);
+    const int y1 = min(static_cast<int>(floorf((ymax + 1.f + slack) * iwy)), g.nc[1] - 1);
+    const int z0 = max(static_cast<int>(floorf((zmin - 1.f - slack) * iwz)), 0);
+    const int z1 = min(static_cast<int>(floorf((zmax + 1.f + slack) * iwz)), g.nc[2] - 1);
+    __syncwarp();
+    for (int rz = z0; rz <= z1; ++rz) {
+      const float zl = rz * cwz, zh = zl + cwz;
+      const float dz = zmax < zl ? zl - zmax : (zmin > zh ? zmin - zh : 0.f);
+      for (int ry = y0; ry <= y1; ++ry) {
+        const float yl = ry * cwy, yh = yl + cwy;
+        const float dy = ymax < yl ? yl - ymax : (ymin > yh ? ymin - yh : 0.f);
+        const float d2 = dy * dy + dz * dz;
+        if (d2 >= 1.f + slack) continue;
+        const float w = sqrtf(fmaxf(1.f - d2, 0.f)) + slack;
+        const int c0 = max(static_cast<int>(floorf((xmin - w) * iwx)), 0);
+        const int c1 = min(static_cast<int>(floorf((xmax + w) * iwx)), g.nc[0] - 1);
+        if (c0 > c1) continue;
+        const uint32_t rbase = (static_cast<uint32_t>(rz) * g.nc[1] + ry) * g.nc[0];
+        const uint32_t J0 = starts[rbase + c0], J1 = starts[rbase + c1 + 1];
+        for (uint32_t base = J0; base < J1; base += 32) {
+          const uint32_t jl_idx = base + lane;
+          if (jl_idx < J1) {
+            jh[lane] = hi[jl_idx];
+            jl[lane] = lo[jl_idx];
+          }
+          __syncwarp();
+          const int nj = static_cast<int>(min(32u, J1 - base));
+          for (int k = 0; k < nj; ++k) {
+            const float4 hj = jh[k];
+            float rx = pi.x - hj.x, ry2 = pi.y - hj.y, rz2 = pi.z - hj.z;
+            float r2 = rx * rx + ry2 * ry2 + rz2 * rz2;
+            const bool cand = alive && r2 < 1.f + slack && (base + k) != i;
+            if (__any_sync(0xffffffffu, cand)) {
+              const float4 lj = jl[k];
+              rx += li.x - lj.x;
+              ry2 += li.y - lj.y;
+              rz2 += li.z - lj.z;
+              r2 = rx * rx + ry2 * ry2 + rz2 * rz2;
+              const bool hit = cand && r2 < 1.f && r2 > 0.f;
+              const unsigned hm = __ballot_sync(0xffffffffu, hit);
+              if (hit) {
+                stk[depth + __popc(hm & lt)] = make_float4(rx, ry2, rz2, __int_as_float(lane));
+                ++np;
+              }
+              depth += __popc(hm);
+              if (depth >= 32) {
+                __syncwarp();
+                eval_entry<kDeg>(P, stk[depth - 32 + lane], slot);
+                depth -= 32;
+                __syncwarp();
+                if (++batches == kFoldEvery) {
+                  batches = 0;
+                  for (int q = 0; q < 4; ++q) {
+                    sum[q].add(slot[q][lane]);
+                    slot[q][lane] = 0.f;
+                  }
+                  __syncwarp();
+                }
+              }
             }
-          ++nh;
+          }
+          __syncwarp();
         }
       }
     }
-    if (__ballot_sync(0xffffffffu, nh > 0) == 0u) break;
-    // evaluate
-#pragma unroll
-    for (int k = 0; k < kHits; ++k) {
-      if (k < nh) {
-        const float r2 = hx[k] * hx[k] + hy[k] * hy[k] + hz[k] * hz[k];
-        float fco, pot;
-        pair_poly<kDeg>(P, r2, fco, pot);
-        part[0] = fmaf(fco, hx[k], part[0]);
-        part[1] = fmaf(fco, hy[k], part[1]);
-        part[2] = fmaf(fco, hz[k], part[2]);
-        part[3] += pot;
-      }
-    }
-    np += nh;
-    if (++rounds == kFoldEvery) {
-      rounds = 0;
-      for (int k = 0; k < 4; ++k) {
-        sum[k].add(part[k]);
-        part[k] = 0.f;
-      }
-    }
+    if (lane < depth) eval_entry<kDeg>(P, stk[lane], slot);
+    __syncwarp();
+    for (int q = 0; q < 4; ++q) sum[q].add(slot[q][lane]);
   }
-  for (int k = 0; k < 4; ++k) sum[k].add(part[k]);
   unsigned long long ni = 0;
   if (alive && g.pp_bc) {
     // images within r_c of particles less than r_c above the cathode (rare): plain loop
@@ -539,8 +564,9 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   const uint32_t* total = c->starts + c->nkeys;
   if (c->fp32) {
+    const unsigned wblocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
     auto run = [&](auto kern) {
-      kern<<<blocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
+      kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
                                        c->recl, c->starts, static_cast<float4*>(c->fpp),
                                        c->energy_acc, c->pair_acc);
     };

@@ -15,15 +15,26 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;  // per thread
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+// Mesh coordinate s = (x - lo) / h. The product with the reciprocal is used (FP64 division is
+// slow on this part) unless it lies within 1e-9 of a point where the assignment changes its
+// node (integers for CIC, half-integers for TSC); there the IEEE quotient is taken, so the node
+// decision is exactly the one the definition makes.
+__device__ __forceinline__ double mesh_coord(const Geom& g, double v, int d) {
+  const double dv = v - g.lo[d];
+  const double s = dv * g.inv_h[d];
+  const double knot = (g.order == 2) ? floor(s + 0.5) - 0.5 : floor(s);
+  const double dist = fmin(fabs(s - knot), fabs(s - knot - 1.0));
+  return (dist < 1e-9 * fmax(1.0, fabs(s))) ? dv / g.h[d] : s;
+}
+
 // Validity of one particle and its cell. Valid: the assignment support lies inside the mesh
-// (TSC: floor(s + 1/2) in [1, n - 2]; CIC: floor(s) in [0, n - 2]) with s = (x - lo) / h
-// (computed with the reciprocal: FP64 division is slow on this part) and,
-// with the cathode in the long-range solve, z > z_cathode. Returns 0 if valid, else an error bit.
+// (TSC: floor(s + 1/2) in [1, n - 2]; CIC: floor(s) in [0, n - 2]) and, with the cathode in the
+// long-range solve, z > z_cathode. Returns 0 if valid, else an error bit.
 __device__ __forceinline__ int particle_cell(const Geom& g, const double* __restrict__ xi,
                                              int cell[3]) {
   int err = 0;
   for (int d = 0; d < 3; ++d) {
-    const double s = (xi[d] - g.lo[d]) * g.inv_h[d];
+    const double s = mesh_coord(g, xi[d], d);
     if (!(s == s)) return kErrNaN;
     const double c = (g.order == 2) ? floor(s + 0.5) : floor(s);
     const double cmin = (g.order == 2) ? 1.0 : 0.0;
@@ -168,9 +179,8 @@ __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
   int c[3];
   for (int d = 0; d < 3; ++d) {
     const double v = x[3 * i + d];
-    const double dv = v - g.lo[d];
-    xr[d] = dv * g.inv_rc;
-    const double s = dv * g.inv_h[d];
+    xr[d] = (v - g.lo[d]) * g.inv_rc;
+    const double s = mesh_coord(g, v, d);
     const double cn = (g.order == 2) ? floor(s + 0.5) : floor(s);
     u[d] = s - cn;
     c[d] = static_cast<int>(cn);
