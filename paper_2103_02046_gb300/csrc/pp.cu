@@ -242,14 +242,15 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ------------------------------------------------------------------------------------------
-// FP32 short range, warp tiles. A warp owns 32 consecutive sorted particles (one per lane;
-// they lie in a stretch of about two cutoffs of one x-row). For every neighbour row of the
-// group's bounding box it streams the row's pruned candidate run in chunks of 32: the chunk is
-// loaded coalesced into shared memory, then each candidate j is broadcast to all lanes and
-// tested against every lane's particle. Pairs inside the cutoff are pushed onto a per-warp
+// FP32 short range, rows in lockstep. Each lane owns one sorted particle i; a warp holds 32
+// consecutive particles of one stretch of an x-row. The warp walks the 9 neighbour rows
+// together: for row r every lane computes its own pruned candidate run [j0, j1) (so pruning
+// stays per particle), then the warp steps t = 0 .. max_len - 1 and each lane tests j0 + t.
+// Lanes of one warp have runs of nearly the same length and start, so few lanes idle and the
+// loads of one step touch a few cache lines. Pairs inside the cutoff are pushed onto a per-warp
 // stack (separation made exact with the lo parts); whenever 32 are waiting, all lanes evaluate
-// one pair each and add it to the owner's shared-memory slot. Every control decision is
-// warp-uniform, so no lane waits on another lane's loop.
+// one pair each and add it to the owner's shared-memory slot, so the pair function never runs
+// with idle lanes. Every branch around the stack is warp-uniform.
 // The owner folds its slot into a two-float (TwoSum) accumulator every kFoldEvery batches.
 // The pair function uses one ex2 for both e^{-kappa^2 rho^2} terms and the fitted polynomial
 // R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}.
@@ -271,15 +272,6 @@ __device__ __forceinline__ void pair_poly(const PairPoly& P, float r2, float& fc
   fco = fmaf(P.c2k, ex, pot) * (rinv * rinv);
 }
 
-__device__ __forceinline__ float warp_min(float v) {
-  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ float warp_max(float v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
 template <int kDeg>
 __device__ __forceinline__ void eval_entry(const PairPoly& P, float4 e, float (*slot)[33]) {
   const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
@@ -292,24 +284,43 @@ __device__ __forceinline__ void eval_entry(const PairPoly& P, float4 e, float (*
   atomicAdd(&slot[3][o], pot);
 }
 
+__device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restrict__ starts,
+                                          float px, float py, float pz, int cy, int cz, int r,
+                                          uint32_t& j0, uint32_t& j1) {
+  j0 = j1 = 0;
+  const int ry = cy + (r % 3) - 1, rz = cz + (r / 3) - 1;
+  if (ry < 0 || ry >= g.nc[1] || rz < 0 || rz >= g.nc[2]) return;
+  const float slack = kFilterSlack;
+  const float cwy = static_cast<float>(g.cw[1]), cwz = static_cast<float>(g.cw[2]);
+  const float yl = ry * cwy, yh = yl + cwy, zl = rz * cwz, zh = zl + cwz;
+  const float dy = py < yl ? yl - py : (py > yh ? py - yh : 0.f);
+  const float dz = pz < zl ? zl - pz : (pz > zh ? pz - zh : 0.f);
+  const float d2 = dy * dy + dz * dz;
+  if (d2 >= 1.f + slack) return;
+  const float w = sqrtf(fmaxf(1.f - d2, 0.f)) + slack;
+  const float iwx = static_cast<float>(g.inv_cw[0]);
+  const int c0 = max(static_cast<int>(floorf((px - w) * iwx)), 0);
+  const int c1 = min(static_cast<int>(floorf((px + w) * iwx)), g.nc[0] - 1);
+  if (c0 > c1) return;
+  const uint32_t base = (static_cast<uint32_t>(rz) * g.nc[1] + ry) * g.nc[0];
+  j0 = starts[base + c0];
+  j1 = starts[base + c1 + 1];
+}
+
 template <int kDeg>
 __global__ void __launch_bounds__(kThreads, 8)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
              const float4* __restrict__ hi, const float4* __restrict__ lo,
              const uint32_t* __restrict__ starts, float4* __restrict__ fpp,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
-  __shared__ float4 jh_s[kWarps][32], jl_s[kWarps][32];
   __shared__ float4 stack_s[kWarps][kStack];
   __shared__ float slot_s[kWarps][4][33];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* jh = jh_s[warp];
-  float4* jl = jl_s[warp];
   float4* stk = stack_s[warp];
   float(*slot)[33] = slot_s[warp];
   const uint32_t N = *total;
-  const uint32_t i = (blockIdx.x * kWarps + warp) * 32u + lane;
+  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
   const bool alive = i < N;
-  const bool warp_alive = __any_sync(0xffffffffu, alive);
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), li = pi;
   if (alive) {
     pi = hi[i];
@@ -321,84 +332,62 @@ __global__ void __launch_bounds__(kThreads, 8)
   unsigned long long np = 0;
   const unsigned lt = (1u << lane) - 1u;
   int depth = 0, batches = 0;
-  if (warp_alive) {
-    const float big = 3.0e38f;
-    const float xmin = warp_min(alive ? pi.x : big), xmax = warp_max(alive ? pi.x : -big);
-    const float ymin = warp_min(alive ? pi.y : big), ymax = warp_max(alive ? pi.y : -big);
-    const float zmin = warp_min(alive ? pi.z : big), zmax = warp_max(alive ? pi.z : -big);
-    const float slack = kFilterSlack;
-    const float cwy = static_cast<float>(g.cw[1]), cwz = static_cast<float>(g.cw[2]);
-    const float iwx = static_cast<float>(g.inv_cw[0]), iwy = static_cast<float>(g.inv_cw[1]),
-                iwz = static_cast<float>(g.inv_cw[2]);
-    const int y0 = max(static_cast<int>(floorf((ymin - 1.f - slack) * iwy)), 0);
-    const int y1 = min(static_cast<int>(floorf((ymax + 1.f + slack) * iwy)), g.nc[1] - 1);
-    const int z0 = max(static_cast<int>(floorf((zmin - 1.f - slack) * iwz)), 0);
-    const int z1 = min(static_cast<int>(floorf((zmax + 1.f + slack) * iwz)), g.nc[2] - 1);
-    __syncwarp();
-    for (int rz = z0; rz <= z1; ++rz) {
-      const float zl = rz * cwz, zh = zl + cwz;
-      const float dz = zmax < zl ? zl - zmax : (zmin > zh ? zmin - zh : 0.f);
-      for (int ry = y0; ry <= y1; ++ry) {
-        const float yl = ry * cwy, yh = yl + cwy;
-        const float dy = ymax < yl ? yl - ymax : (ymin > yh ? ymin - yh : 0.f);
-        const float d2 = dy * dy + dz * dz;
-        if (d2 >= 1.f + slack) continue;
-        const float w = sqrtf(fmaxf(1.f - d2, 0.f)) + slack;
-        const int c0 = max(static_cast<int>(floorf((xmin - w) * iwx)), 0);
-        const int c1 = min(static_cast<int>(floorf((xmax + w) * iwx)), g.nc[0] - 1);
-        if (c0 > c1) continue;
-        const uint32_t rbase = (static_cast<uint32_t>(rz) * g.nc[1] + ry) * g.nc[0];
-        const uint32_t J0 = starts[rbase + c0], J1 = starts[rbase + c1 + 1];
-        for (uint32_t base = J0; base < J1; base += 32) {
-          const uint32_t jl_idx = base + lane;
-          if (jl_idx < J1) {
-            jh[lane] = hi[jl_idx];
-            jl[lane] = lo[jl_idx];
-          }
-          __syncwarp();
-          const int nj = static_cast<int>(min(32u, J1 - base));
-          for (int k = 0; k < nj; ++k) {
-            const float4 hj = jh[k];
-            float rx = pi.x - hj.x, ry2 = pi.y - hj.y, rz2 = pi.z - hj.z;
-            float r2 = rx * rx + ry2 * ry2 + rz2 * rz2;
-            const bool cand = alive && r2 < 1.f + slack && (base + k) != i;
-            if (__any_sync(0xffffffffu, cand)) {
-              const float4 lj = jl[k];
-              rx += li.x - lj.x;
-              ry2 += li.y - lj.y;
-              rz2 += li.z - lj.z;
-              r2 = rx * rx + ry2 * ry2 + rz2 * rz2;
-              const bool hit = cand && r2 < 1.f && r2 > 0.f;
-              const unsigned hm = __ballot_sync(0xffffffffu, hit);
-              if (hit) {
-                stk[depth + __popc(hm & lt)] = make_float4(rx, ry2, rz2, __int_as_float(lane));
-                ++np;
-              }
-              depth += __popc(hm);
-              if (depth >= 32) {
-                __syncwarp();
-                eval_entry<kDeg>(P, stk[depth - 32 + lane], slot);
-                depth -= 32;
-                __syncwarp();
-                if (++batches == kFoldEvery) {
-                  batches = 0;
-                  for (int q = 0; q < 4; ++q) {
-                    sum[q].add(slot[q][lane]);
-                    slot[q][lane] = 0.f;
-                  }
-                  __syncwarp();
-                }
-              }
-            }
+  const int cy = min(max(static_cast<int>(floorf(pi.y * static_cast<float>(g.inv_cw[1]))), 0),
+                     g.nc[1] - 1);
+  const int cz = min(max(static_cast<int>(floorf(pi.z * static_cast<float>(g.inv_cw[2]))), 0),
+                     g.nc[2] - 1);
+  __syncwarp();
+  for (int r = 0; r < 9; ++r) {
+    uint32_t j0 = 0, j1 = 0;
+    if (alive) row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
+    const int len = static_cast<int>(j1 - j0);
+    int maxlen = len;
+    for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
+    for (int t = 0; t < maxlen; ++t) {
+      const uint32_t j = j0 + t;
+      bool hit = false;
+      float rx = 0.f, ry = 0.f, rz = 0.f;
+      if (t < len) {
+        const float4 hj = hi[j];
+        rx = pi.x - hj.x;
+        ry = pi.y - hj.y;
+        rz = pi.z - hj.z;
+        float r2 = rx * rx + ry * ry + rz * rz;
+        if (r2 < 1.f + kFilterSlack && j != i) {
+          const float4 lj = lo[j];
+          rx += li.x - lj.x;
+          ry += li.y - lj.y;
+          rz += li.z - lj.z;
+          r2 = rx * rx + ry * ry + rz * rz;
+          hit = r2 < 1.f && r2 > 0.f;
+        }
+      }
+      const unsigned hm = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        stk[depth + __popc(hm & lt)] = make_float4(rx, ry, rz, __int_as_float(lane));
+        ++np;
+      }
+      depth += __popc(hm);
+      if (depth >= 32) {
+        __syncwarp();
+        eval_entry<kDeg>(P, stk[depth - 32 + lane], slot);
+        depth -= 32;
+        __syncwarp();
+        if (++batches == kFoldEvery) {
+          batches = 0;
+          for (int q = 0; q < 4; ++q) {
+            sum[q].add(slot[q][lane]);
+            slot[q][lane] = 0.f;
           }
           __syncwarp();
         }
       }
     }
-    if (lane < depth) eval_entry<kDeg>(P, stk[lane], slot);
-    __syncwarp();
-    for (int q = 0; q < 4; ++q) sum[q].add(slot[q][lane]);
   }
+  __syncwarp();
+  if (lane < depth) eval_entry<kDeg>(P, stk[lane], slot);
+  __syncwarp();
+  for (int q = 0; q < 4; ++q) sum[q].add(slot[q][lane]);
   unsigned long long ni = 0;
   if (alive && g.pp_bc) {
     // images within r_c of particles less than r_c above the cathode (rare): plain loop
@@ -407,9 +396,9 @@ __global__ void __launch_bounds__(kThreads, 8)
       const float mz = static_cast<float>(g.img_c - zi);
       const float ch = static_cast<float>(g.img_c);
       const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
-      for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t j0, uint32_t j1) {
+      for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t ja, uint32_t jb) {
         float rowv[4] = {0.f, 0.f, 0.f, 0.f};
-        for (uint32_t jj = j0; jj < j1; ++jj) {
+        for (uint32_t jj = ja; jj < jb; ++jj) {
           const float4 hj = hi[jj], lj = lo[jj];
           const float ax = (pi.x - hj.x) + (li.x - lj.x);
           const float ay = (pi.y - hj.y) + (li.y - lj.y);
