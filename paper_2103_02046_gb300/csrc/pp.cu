@@ -313,11 +313,6 @@ __global__ void __launch_bounds__(kThreads, 8)
              const float4* __restrict__ hi, const float4* __restrict__ lo,
              const uint32_t* __restrict__ starts, float4* __restrict__ fpp,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
-  __shared__ float4 stack_s[kWarps][kStack];
-  __shared__ float slot_s[kWarps][4][33];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* stk = stack_s[warp];
-  float(*slot)[33] = slot_s[warp];
   const uint32_t N = *total;
   const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
   const bool alive = i < N;
@@ -326,68 +321,43 @@ __global__ void __launch_bounds__(kThreads, 8)
     pi = hi[i];
     li = lo[i];
   }
-  for (int k = 0; k < 4; ++k) slot[k][lane] = 0.f;
   Acc2 sum[4];
   for (int k = 0; k < 4; ++k) sum[k].hi = sum[k].lo = 0.f;
   unsigned long long np = 0;
-  const unsigned lt = (1u << lane) - 1u;
-  int depth = 0, batches = 0;
   const int cy = min(max(static_cast<int>(floorf(pi.y * static_cast<float>(g.inv_cw[1]))), 0),
                      g.nc[1] - 1);
   const int cz = min(max(static_cast<int>(floorf(pi.z * static_cast<float>(g.inv_cw[2]))), 0),
                      g.nc[2] - 1);
-  __syncwarp();
   for (int r = 0; r < 9; ++r) {
     uint32_t j0 = 0, j1 = 0;
     if (alive) row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
     const int len = static_cast<int>(j1 - j0);
     int maxlen = len;
     for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
+    float part[4] = {0.f, 0.f, 0.f, 0.f};
     for (int t = 0; t < maxlen; ++t) {
-      const uint32_t j = j0 + t;
-      bool hit = false;
-      float rx = 0.f, ry = 0.f, rz = 0.f;
-      if (t < len) {
-        const float4 hj = hi[j];
-        rx = pi.x - hj.x;
-        ry = pi.y - hj.y;
-        rz = pi.z - hj.z;
-        float r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 < 1.f + kFilterSlack && j != i) {
-          const float4 lj = lo[j];
-          rx += li.x - lj.x;
-          ry += li.y - lj.y;
-          rz += li.z - lj.z;
-          r2 = rx * rx + ry * ry + rz * rz;
-          hit = r2 < 1.f && r2 > 0.f;
-        }
-      }
-      const unsigned hm = __ballot_sync(0xffffffffu, hit);
-      if (hit) {
-        stk[depth + __popc(hm & lt)] = make_float4(rx, ry, rz, __int_as_float(lane));
-        ++np;
-      }
-      depth += __popc(hm);
-      if (depth >= 32) {
-        __syncwarp();
-        eval_entry<kDeg>(P, stk[depth - 32 + lane], slot);
-        depth -= 32;
-        __syncwarp();
-        if (++batches == kFoldEvery) {
-          batches = 0;
-          for (int q = 0; q < 4; ++q) {
-            sum[q].add(slot[q][lane]);
-            slot[q][lane] = 0.f;
-          }
-          __syncwarp();
-        }
+      const bool in = t < len;
+      const uint32_t j = in ? j0 + t : i;  // an idle lane re-reads itself: separation 0, no pair
+      const float4 hj = hi[j], lj = lo[j];
+      const float rx = (pi.x - hj.x) + (li.x - lj.x);
+      const float ry = (pi.y - hj.y) + (li.y - lj.y);
+      const float rz = (pi.z - hj.z) + (li.z - lj.z);
+      const float r2 = rx * rx + ry * ry + rz * rz;
+      const bool hit = r2 < 1.f && r2 > 0.f;  // the self pair has r2 == 0 exactly
+      if (__any_sync(0xffffffffu, hit)) {
+        float fco, pot;
+        pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
+        fco = hit ? fco : 0.f;
+        pot = hit ? pot : 0.f;
+        part[0] = fmaf(fco, rx, part[0]);
+        part[1] = fmaf(fco, ry, part[1]);
+        part[2] = fmaf(fco, rz, part[2]);
+        part[3] += pot;
+        np += hit;
       }
     }
+    for (int k = 0; k < 4; ++k) sum[k].add(part[k]);
   }
-  __syncwarp();
-  if (lane < depth) eval_entry<kDeg>(P, stk[lane], slot);
-  __syncwarp();
-  for (int q = 0; q < 4; ++q) sum[q].add(slot[q][lane]);
   unsigned long long ni = 0;
   if (alive && g.pp_bc) {
     // images within r_c of particles less than r_c above the cathode (rare): plain loop
