@@ -245,20 +245,16 @@ __global__ void __launch_bounds__(kThreads)
 // FP32 short range, rows in lockstep. Each lane owns one sorted particle i; a warp holds 32
 // consecutive particles of one stretch of an x-row. The warp walks the 9 neighbour rows
 // together: for row r every lane computes its own pruned candidate run [j0, j1) (so pruning
-// stays per particle), then the warp steps t = 0 .. max_len - 1 and each lane tests j0 + t.
+// stays per particle), then the warp steps t = 0 .. max_len - 1 and each lane tests j0 + t
+// (a lane past its run re-reads itself, which has separation 0 and is never a pair). Control
+// flow is warp-uniform: the pair function runs, predicated, whenever any lane holds a pair.
 // Lanes of one warp have runs of nearly the same length and start, so few lanes idle and the
-// loads of one step touch a few cache lines. Pairs inside the cutoff are pushed onto a per-warp
-// stack (separation made exact with the lo parts); whenever 32 are waiting, all lanes evaluate
-// one pair each and add it to the owner's shared-memory slot, so the pair function never runs
-// with idle lanes. Every branch around the stack is warp-uniform.
-// The owner folds its slot into a two-float (TwoSum) accumulator every kFoldEvery batches.
+// loads of one step touch a few cache lines. Separations are exact to FP32 relative rounding
+// ((hi_i - hi_j) + (lo_i - lo_j)). Each row's FP32 partial sum is folded into a two-float
+// (TwoSum) accumulator.
 // The pair function uses one ex2 for both e^{-kappa^2 rho^2} terms and the fitted polynomial
 // R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}.
 // ------------------------------------------------------------------------------------------
-constexpr int kWarps = kThreads / 32;
-constexpr int kStack = 64;
-constexpr int kFoldEvery = 4;
-
 template <int kDeg>
 __device__ __forceinline__ void pair_poly(const PairPoly& P, float r2, float& fco, float& pot) {
   const float rinv = rsqrtf(r2);
@@ -270,18 +266,6 @@ __device__ __forceinline__ void pair_poly(const PairPoly& P, float r2, float& fc
   const float ex = exp2f(-P.kappa2_log2e * r2);
   pot = R * ex * rinv;
   fco = fmaf(P.c2k, ex, pot) * (rinv * rinv);
-}
-
-template <int kDeg>
-__device__ __forceinline__ void eval_entry(const PairPoly& P, float4 e, float (*slot)[33]) {
-  const float r2 = e.x * e.x + e.y * e.y + e.z * e.z;
-  float fco, pot;
-  pair_poly<kDeg>(P, r2, fco, pot);
-  const int o = __float_as_int(e.w);
-  atomicAdd(&slot[0][o], fco * e.x);
-  atomicAdd(&slot[1][o], fco * e.y);
-  atomicAdd(&slot[2][o], fco * e.z);
-  atomicAdd(&slot[3][o], pot);
 }
 
 __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restrict__ starts,
