@@ -156,6 +156,29 @@ p3m_status p3m_backward(p3m_ctx* ctx, const double* x0, const double* p0, int64_
 p3m_status p3m_emittance(p3m_ctx* ctx, const double* x, const double* p, int64_t n, double* eps3,
                          double* gx, double* gp);
 
+/* Largest n accepted by p3m_emittance_noalloc. */
+#define P3M_NOALLOC_MAX_N 16777216
+
+/* The same normalised rms emittance (and optional gradient) as p3m_emittance, for callers that
+ * cannot allocate device memory: code that runs inside a host application owning every byte of
+ * the device through its own allocator or a fixed memory budget, monitoring hooks called from a
+ * simulation loop where an allocation could stall or fail mid-run, and code that must not touch
+ * the CUDA allocator at all. The paper has no counterpart; this is a library service.
+ *   x, p: device [n][3] float64 (caller-owned); mass [kg] > 0; eps3: device float64[3];
+ *   gx, gp: nullable device [n][3] float64 for the gradient of eps_x + eps_y + eps_z;
+ *   stream: cudaStream_t (may be NULL).
+ * It needs no context and allocates nothing: its scratch is a fixed 512 KiB array in device
+ * memory that every GPU loading the library holds until the process exits. Its first call on a
+ * device looks up that array's address (once per device, with the device current); make that
+ * first call before any stream capture. Every call shares the array; each call writes every
+ * slot it later reads, so no state carries over, but calls that overlap on the GPU (other
+ * streams, no ordering between them) race and must not be issued. The sums are combined in a
+ * fixed order, so results are reproducible run to run.
+ * Errors: EINVAL for NULL x/p/eps3, n < 2, mass <= 0 or n > P3M_NOALLOC_MAX_N; ECUDA if the
+ * scratch address cannot be obtained or a launch fails. Asynchronous on `stream`. */
+p3m_status p3m_emittance_noalloc(const double* x, const double* p, int64_t n, double mass,
+                                 double* eps3, double* gx, double* gp, void* stream);
+
 /* Waits for the context's stream and returns any latched device error (then clears it). */
 p3m_status p3m_sync(p3m_ctx* ctx);
 
