@@ -5,7 +5,8 @@
 //   bin + counting sort --(fork)--> short range on a side stream
 //                       \--> zero mesh, deposit, R2C, Green multiply, C2R (long range)
 //   join --> interpolation + combination, written in the caller's particle order.
-// The short range is ALU-bound and the FFTs are HBM-bound, so the two streams overlap.
+// The short range (ALU-bound, the longest stage) runs at high priority; the mesh chain fills
+// the SMs its blocks leave free, mostly in its tail.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -101,6 +102,8 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   g.inv_rc = 1.0 / g.rc;
   for (int d = 0; d < 3; ++d) {
     g.inv_h[d] = 1.0 / g.h[d];
+    g.inv_h_f[d] = static_cast<float>(g.inv_h[d]);
+    g.inv_cell_f[d] = static_cast<float>(g.inv_cw[d] / g.rc);
     g.fscale[d] = -p->q / g.h[d];
   }
   g.q = p->q;
@@ -468,8 +471,8 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   int prio_low = 0, prio_high = 0;
   cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
   if (e == cudaSuccess)
-    e = cudaStreamCreateWithPriority(&c->work, cudaStreamNonBlocking, prio_high);
-  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_pp, cudaStreamNonBlocking, prio_low);
+    e = cudaStreamCreateWithPriority(&c->work, cudaStreamNonBlocking, prio_low);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_pp, cudaStreamNonBlocking, prio_high);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);

@@ -46,6 +46,8 @@ struct Geom {
   double cw[3];      // cell edges in cutoff units (y, z: >= 1; x: 1 / nsub)
   double inv_cw[3];
   double inv_h[3];   // 1 / h_d
+  float inv_h_f[3];  // 1 / h_d, FP32
+  float inv_cell_f[3];  // 1 / (r_c cw_d): metres from lo -> cell index, FP32
   double inv_rc;     // 1 / r_c
   double fscale[3];  // -q / h_d: long-range force per volt of mesh-unit gradient
   double img_c;      // 2 (z_c - lo_z) / r_c: the image of z (cutoff units) is img_c - z
@@ -123,9 +125,9 @@ struct p3m_ctx {
   int device = 0;
   bool fp32 = false;
   cudaStream_t stream = nullptr;  // caller's stream (not owned)
-  cudaStream_t work = nullptr;    // owned, high priority: sort, mesh chain, combination
-  cudaStream_t s_pp = nullptr;    // owned, low priority: the short range (ALU-bound), so that
-                                  // mesh-chain blocks are scheduled first when SMs free up
+  cudaStream_t work = nullptr;    // owned, low priority: sort, mesh chain, combination
+  cudaStream_t s_pp = nullptr;    // owned, high priority: the short range (the longest stage),
+                                  // so the mesh chain only takes SMs its blocks leave free
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr;
   cudaEvent_t tev[8] = {};
 

@@ -28,26 +28,35 @@ __device__ __forceinline__ double mesh_coord(const Geom& g, double v, int d) {
 }
 
 // Validity of one particle and its cell. Valid: the assignment support lies inside the mesh
-// (TSC: floor(s + 1/2) in [1, n - 2]; CIC: floor(s) in [0, n - 2]) and, with the cathode in the
-// long-range solve, z > z_cathode. Returns 0 if valid, else an error bit.
+// (TSC: floor(s + 1/2) in [1, n - 2], i.e. s in [1/2, n - 3/2); CIC: floor(s) in [0, n - 2],
+// i.e. s in [0, n - 1)) and, with the cathode in the long-range solve, z > z_cathode. The test
+// runs in FP32 (the FP64 rate of this part is low) and falls back to the exact FP64 coordinate
+// within 1e-3 of a boundary, so the decision is always the definition's. The cell index only
+// has to be consistent with the stored positions to within the search slack, so FP32 suffices.
+// Returns 0 if valid, else an error bit.
 __device__ __forceinline__ int particle_cell(const Geom& g, const double* __restrict__ xi,
                                              int cell[3]) {
   int err = 0;
   for (int d = 0; d < 3; ++d) {
-    const double s = mesh_coord(g, xi[d], d);
-    if (!(s == s)) return kErrNaN;
-    const double c = (g.order == 2) ? floor(s + 0.5) : floor(s);
-    const double cmin = (g.order == 2) ? 1.0 : 0.0;
-    if (!(c >= cmin && c <= static_cast<double>(g.n[d] - 2))) err = kErrRange;
+    const double dv = xi[d] - g.lo[d];
+    const float f = static_cast<float>(dv);
+    if (!(f == f)) return kErrNaN;
+    const float s = f * g.inv_h_f[d];
+    const float b0 = (g.order == 2) ? 0.5f : 0.0f;
+    const float b1 = static_cast<float>(g.n[d]) - ((g.order == 2) ? 1.5f : 1.0f);
+    bool ok;
+    if (fabsf(s - b0) < 1e-3f || fabsf(s - b1) < 1e-3f) {
+      const double se = mesh_coord(g, xi[d], d);
+      const double c = (g.order == 2) ? floor(se + 0.5) : floor(se);
+      ok = c >= ((g.order == 2) ? 1.0 : 0.0) && c <= static_cast<double>(g.n[d] - 2);
+    } else {
+      ok = s >= b0 && s < b1;
+    }
+    if (!ok) err = kErrRange;
+    cell[d] = min(max(static_cast<int>(floorf(f * g.inv_cell_f[d])), 0), g.nc[d] - 1);
   }
   if (g.pm_bc && !(xi[2] > g.zc)) err = kErrRange;
-  if (err) return err;
-  for (int d = 0; d < 3; ++d) {
-    const double xr = (xi[d] - g.lo[d]) * g.inv_rc;
-    const int c = static_cast<int>(floor(xr * g.inv_cw[d]));
-    cell[d] = min(max(c, 0), g.nc[d] - 1);
-  }
-  return 0;
+  return err;
 }
 
 __global__ void k_bin(Geom g, const double* __restrict__ x, int64_t n,
@@ -179,10 +188,21 @@ __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
   int c[3];
   for (int d = 0; d < 3; ++d) {
     const double v = x[3 * i + d];
-    xr[d] = (v - g.lo[d]) * g.inv_rc;
-    const double s = mesh_coord(g, v, d);
-    const double cn = (g.order == 2) ? floor(s + 0.5) : floor(s);
-    u[d] = s - cn;
+    const double dv = v - g.lo[d];
+    xr[d] = dv * g.inv_rc;
+    // node from an FP32 estimate unless it is within 1e-3 of a knot; then from the exact s
+    const float sf = static_cast<float>(dv) * g.inv_h_f[d];
+    const float cf = (g.order == 2) ? floorf(sf + 0.5f) : floorf(sf);
+    const float kl = (g.order == 2) ? cf - 0.5f : cf;
+    double cn;
+    if (fabsf(sf - kl) < 1e-3f || fabsf(sf - kl - 1.f) < 1e-3f) {
+      const double s = mesh_coord(g, v, d);
+      cn = (g.order == 2) ? floor(s + 0.5) : floor(s);
+      u[d] = s - cn;
+    } else {
+      cn = static_cast<double>(cf);
+      u[d] = fma(-cn, g.h[d], dv) * g.inv_h[d];
+    }
     c[d] = static_cast<int>(cn);
   }
   const uint32_t node = pack_node(c[0], c[1], c[2]);
