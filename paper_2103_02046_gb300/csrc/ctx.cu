@@ -72,8 +72,8 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   g.rc = p->rc_over_h * hmax;
   g.alpha = p->alpha > 0.0 ? p->alpha : p->kappa / g.rc;
   g.kappa_eff = g.alpha * g.rc;
-  // cells: y and z edges a hair above r_c (so a pair closer than r_c is never two cells apart
-  // after rounding); x edges r_c / nsub, nsub = 4 unless that makes too many cells
+  // cells: y and z edges a hair above r_c / 2 (so a pair closer than r_c is never more than two
+  // cells apart after rounding); x edges r_c / nsub, nsub = 4 unless that makes too many cells
   const double edge = 1.0 + 1e-9;
   double ext[3];
   for (int d = 0; d < 3; ++d) {
@@ -84,7 +84,7 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   const double cap = std::max<double>(4.0 * static_cast<double>(n_max), 1 << 20);
   for (;;) {
     g.cw[0] = edge / nsub;
-    g.cw[1] = g.cw[2] = edge;
+    g.cw[1] = g.cw[2] = edge / kRowsPerCutoff;
     double cells = 1.0;
     for (int d = 0; d < 3; ++d) {
       g.inv_cw[d] = 1.0 / g.cw[d];

@@ -1,9 +1,10 @@
 // Internal declarations of the GB300 P3M library (not part of the C ABI).
 //
 // Data layout in HBM (one context, up to n_max particles, mesh n = (nx, ny, nz), n_d <= 1024):
-//   * Cells for the short-range search are rows along x: edge >= r_c in y and z, r_c / nsub in x,
-//     keys x-fastest, so the cells of one (y, z) row within any x-interval hold a contiguous run
-//     of sorted particles. Each neighbour row of a particle is then one pruned index range.
+//   * Cells for the short-range search are rows along x: edge a hair above r_c / 2 in y and z,
+//     r_c / nsub in x, keys x-fastest, so the cells of one (y, z) row within any x-interval hold a
+//     contiguous run of sorted particles. Each of the 5 x 5 neighbour rows of a particle is then
+//     one index range, pruned by the particle's distance to the row.
 //   * Sorted records (counting sort by cell key):
 //       recp  positions in cutoff units from the mesh origin, (x - lo) / r_c:
 //             FP32 float4 {hi_x, hi_y, hi_z, bits(original index)}, FP64 {x, y, z, index};
@@ -28,6 +29,7 @@
 namespace p3m {
 
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
+constexpr int kRowsPerCutoff = 2;  // cell rows are r_c / 2 wide in y and z
 constexpr int kMaxMesh = 1024;
 
 enum ErrBits : int { kErrRange = 1, kErrNaN = 2, kErrTimeout = 4 };

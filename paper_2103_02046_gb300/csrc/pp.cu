@@ -8,11 +8,11 @@
 // Work is in cutoff units (rho = r / r_c, kappa = a r_c): the force is
 // (k_e q^2 / r_c^2) [erfc(kappa rho)/rho + (2 kappa/sqrt(pi)) e^{-kappa^2 rho^2}] rho_vec / rho^2.
 //
-// Search: cells are rows along x (>= r_c wide in y and z, r_c / nsub in x, keys x-fastest). For
-// particle i and each of the 3 x 3 neighbour rows, the distance d from i to the row's (y, z)
-// rectangle bounds |dx| < sqrt(1 - d^2), which selects one contiguous run of sorted particles.
-// Rows with d >= 1 are skipped. This visits about 13 r_c^3 of volume per particle instead of
-// the 27 r_c^3 of a plain 27-cell stencil.
+// Search: cells are rows along x (r_c / 2 wide in y and z, r_c / nsub in x, keys x-fastest).
+// For particle i and each of the 5 x 5 neighbour rows, the distance d from i to the row's (y, z)
+// rectangle bounds |dx| < sqrt(1 - d^2), which selects one contiguous run of sorted particles;
+// rows with d >= 1 are skipped. This visits about 8 r_c^3 of volume per particle (the cutoff
+// sphere is 4.19 r_c^3) instead of the 27 r_c^3 of a plain 27-cell stencil.
 //
 // FP32: candidates are tested with the hi parts of the cutoff-unit positions; in-cutoff pairs
 // recompute the separation as (hi_i - hi_j) + (lo_i - lo_j), exact to FP32 relative rounding at
@@ -27,7 +27,8 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr float kFilterSlack = 1e-4f;   // hi-only separations err by < 1e-5 r_c
-constexpr int kPend = 3;                 // pending pairs per lane in the FP32 short range
+constexpr int kRowReach = kRowsPerCutoff;          // neighbour rows on each side (y and z)
+constexpr int kRowSpan = 2 * kRowReach + 1;
 
 // two-float accumulator (hi + lo) with Knuth's TwoSum
 struct Acc2 {
@@ -244,12 +245,11 @@ __global__ void __launch_bounds__(kThreads)
 
 // ------------------------------------------------------------------------------------------
 // FP32 short range, rows in lockstep. Each lane owns one sorted particle i; a warp holds 32
-// consecutive particles of one stretch of an x-row. The warp walks the 9 neighbour rows
+// consecutive particles of one stretch of an x-row. The warp walks the 25 neighbour rows
 // together: for row r every lane computes its own pruned candidate run [j0, j1) (so pruning
 // stays per particle), then the warp steps t = 0 .. max_len - 1 and each lane tests j0 + t
 // (a lane past its run re-reads itself, which has separation 0 and is never a pair). Control
-// flow is warp-uniform. In-cutoff separations wait in registers (up to kPend per lane); the
-// pair function runs, predicated, whenever some lane's buffer is full, for every lane holding one.
+// flow is warp-uniform: the pair function runs, predicated, whenever any lane holds a pair.
 // Lanes of one warp have runs of nearly the same length and start, so few lanes idle and the
 // loads of one step touch a few cache lines. Separations are exact to FP32 relative rounding
 // ((hi_i - hi_j) + (lo_i - lo_j)). Each row's FP32 partial sum is folded into a two-float
@@ -274,7 +274,7 @@ __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restr
                                           float px, float py, float pz, int cy, int cz, int r,
                                           uint32_t& j0, uint32_t& j1) {
   j0 = j1 = 0;
-  const int ry = cy + (r % 3) - 1, rz = cz + (r / 3) - 1;
+  const int ry = cy + (r % kRowSpan) - kRowReach, rz = cz + (r / kRowSpan) - kRowReach;
   if (ry < 0 || ry >= g.nc[1] || rz < 0 || rz >= g.nc[2]) return;
   const float slack = kFilterSlack;
   const float cwy = static_cast<float>(g.cw[1]), cwz = static_cast<float>(g.cw[2]);
@@ -314,32 +314,13 @@ __global__ void __launch_bounds__(kThreads, 8)
                      g.nc[1] - 1);
   const int cz = min(max(static_cast<int>(floorf(pi.z * static_cast<float>(g.inv_cw[2]))), 0),
                      g.nc[2] - 1);
-  // up to kPend in-cutoff separations wait per lane; the warp evaluates one per lane (those
-  // holding one) as soon as any lane's buffer is full, so the pair function runs with about half
-  // of the lanes busy instead of the ~1/5 that hit at any single step
-  float4 q0 = make_float4(0.f, 0.f, 0.f, 0.5f), q1 = q0, q2 = q0;
-  int cnt = 0;
-  float part[4] = {0.f, 0.f, 0.f, 0.f};
-  auto evaluate = [&]() {
-    const bool has = cnt > 0;
-    float fco, pot;
-    pair_poly<kDeg>(P, has ? q0.w : 0.5f, fco, pot);
-    fco = has ? fco : 0.f;
-    pot = has ? pot : 0.f;
-    part[0] = fmaf(fco, q0.x, part[0]);
-    part[1] = fmaf(fco, q0.y, part[1]);
-    part[2] = fmaf(fco, q0.z, part[2]);
-    part[3] += pot;
-    q0 = q1;
-    q1 = q2;
-    cnt = has ? cnt - 1 : 0;
-  };
-  for (int r = 0; r < 9; ++r) {
+  for (int r = 0; r < kRowSpan * kRowSpan; ++r) {
     uint32_t j0 = 0, j1 = 0;
     if (alive) row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
     const int len = static_cast<int>(j1 - j0);
     int maxlen = len;
     for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
+    float part[4] = {0.f, 0.f, 0.f, 0.f};
     for (int t = 0; t < maxlen; ++t) {
       const bool in = t < len;
       const uint32_t j = in ? j0 + t : i;  // an idle lane re-reads itself: separation 0, no pair
@@ -348,26 +329,21 @@ __global__ void __launch_bounds__(kThreads, 8)
       const float ry = (pi.y - hj.y) + (li.y - lj.y);
       const float rz = (pi.z - hj.z) + (li.z - lj.z);
       const float r2 = rx * rx + ry * ry + rz * rz;
-      if (r2 < 1.f && r2 > 0.f) {  // the self pair has r2 == 0 exactly
-        const float4 v = make_float4(rx, ry, rz, r2);
-        if (cnt == 0)
-          q0 = v;
-        else if (cnt == 1)
-          q1 = v;
-        else
-          q2 = v;
-        ++cnt;
-        ++np;
+      const bool hit = r2 < 1.f && r2 > 0.f;  // the self pair has r2 == 0 exactly
+      if (__any_sync(0xffffffffu, hit)) {
+        float fco, pot;
+        pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
+        fco = hit ? fco : 0.f;
+        pot = hit ? pot : 0.f;
+        part[0] = fmaf(fco, rx, part[0]);
+        part[1] = fmaf(fco, ry, part[1]);
+        part[2] = fmaf(fco, rz, part[2]);
+        part[3] += pot;
+        np += hit;
       }
-      if (__any_sync(0xffffffffu, cnt == kPend)) evaluate();
     }
-    for (int k = 0; k < 4; ++k) {
-      sum[k].add(part[k]);
-      part[k] = 0.f;
-    }
+    for (int k = 0; k < 4; ++k) sum[k].add(part[k]);
   }
-  while (__any_sync(0xffffffffu, cnt > 0)) evaluate();
-  for (int k = 0; k < 4; ++k) sum[k].add(part[k]);
   unsigned long long ni = 0;
   if (alive && g.pp_bc) {
     // images within r_c of particles less than r_c above the cathode (rare): plain loop
