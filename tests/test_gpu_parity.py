@@ -249,3 +249,24 @@ def test_autograd_emittance_gradient():
     assert float(J) == pytest.approx(O.emittance(xT_o, pT_o, P).sum(), rel=1e-12)
     assert rel(xg.grad, ogx) <= 1e-10
     assert rel(pg.grad, ogp) <= 1e-10
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [1, 0])
+def test_full_size_sphere_sampled(precision):
+    """The benchmark workload at full size (16,777,216-particle uniform sphere, 256^3 mesh,
+    r_c = 2h, open boundaries) in the benchmark's launch configuration, checked against the oracle
+    on 2048 sampled particles (full deposit and solve, short range and interpolation per sample)."""
+    spec = dict(B.WORKLOADS["sphere16m"])
+    x = B.positions(spec)
+    P = O.auto_mesh(x, 256, rc_over_h=2.0)
+    idx = B.subsample(len(x), 2048, seed=12345)
+    ref = O.forces(x, P, sample=idx)
+    ctx = p3m().Context(gpu_params(P, precision), len(x))
+    f = ctx.forces(cuda(x))
+    ctx.sync()
+    fs = f[torch.from_numpy(idx).cuda()]
+    assert rel(fs, ref.F) <= TOL[precision]
+    pairs, _ = ctx.pair_count()
+    assert pairs > 1.0e9
+    ctx.close()
