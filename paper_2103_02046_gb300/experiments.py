@@ -1,0 +1,170 @@
+"""Workload runs that report the paper's physics quantities on the GPU path.
+
+  python -m paper_2103_02046_gb300.experiments boundary   # cathode BC in the short range vs mesh error
+  python -m paper_2103_02046_gb300.experiments energy     # leapfrog energy drift and momentum
+  python -m paper_2103_02046_gb300.experiments gradient   # adjoint gradient vs finite differences
+
+Each prints one JSON line. Everything runs through the C ABI (``p3m``); no oracle is used.
+
+* boundary (Sec. 3.1.1, the paper's claim that neglecting the cathode in the short range costs an
+  error tied to the mesh discretisation error): 4,194,304 particles, 95% Gaussian core
+  (sigma = 1 mm) + 5% uniform halo shell at 4-6 sigma, lifted so the lowest particle sits one mesh
+  spacing above the grounded cathode; r_c = 3h; long range with the cathode. Reports
+  ||F(pp_bc=1) - F(pp_bc=0)|| / ||F|| against the refinement error ||F_h - F_{h/2}|| / ||F||
+  at n = 128 and n = 256, and the locality of the short-range boundary effect.
+* energy: 1,048,576-particle Gaussian bunch (sigma = 1, 1, 3 mm), thermal momenta 1e-4 m_e c rms,
+  64^3 mesh, r_c = 2h, dt = 1e-12 s, 100 kick-drift-kick steps: relative energy drift and the
+  total momentum.
+* gradient: the same bunch, 200 steps with checkpoints every 20: gradient of the final rms
+  emittance J = eps_x + eps_y + eps_z with respect to (x0, p0) by the reverse pass, checked by
+  central finite differences along random directions (relative step 1e-6 of the coordinates in
+  FP64, 1e-4 in FP32, where the evaluation order of the force sums makes J reproducible only to
+  about 1e-10 relative).
+"""
+from __future__ import annotations
+
+import json
+import math
+import sys
+import time
+
+import numpy as np
+import torch
+
+from . import bunches as B
+from . import p3m as m
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _rel(a, b):
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+def boundary(precision: int = m.FP32_MIXED, n_particles: int = 4_194_304):
+    spec = dict(B.WORKLOADS["halo4m"])
+    x0 = B.positions(spec, n_particles)
+    # lift by one spacing of the coarse mesh (h does not depend on the translation)
+    h128 = m.auto_mesh(_cuda(x0), m.Params(n=(128,) * 3)).h[2]
+    xg = _cuda(B.lift_to_plane(x0, 0.0, h128))
+    z = xg[:, 2]
+    out = {"experiment": "boundary", "n": n_particles, "precision": precision, "levels": []}
+    F_bc = {}
+    for n in (128, 256):
+        base = m.auto_mesh(xg, m.Params(n=(n,) * 3, rc_over_h=3.0, pm_bc=1, z_cathode=0.0,
+                                        precision=precision))
+        rc = base.rc_over_h * max(base.h)
+        res, img = {}, 0
+        for pp_bc in (0, 1):
+            ctx = m.Context(m.Params(**{**base.__dict__, "pp_bc": pp_bc}), n_particles)
+            res[pp_bc] = ctx.forces(xg)
+            ctx.sync()
+            if pp_bc:
+                img = ctx.pair_count()[1]
+            ctx.close()
+        dF = res[1] - res[0]
+        changed = torch.linalg.norm(dF, dim=1) > 0
+        out["levels"].append({
+            "mesh": n, "h": list(base.h), "rc": rc,
+            "bc_rel_l2": _rel(res[0], res[1]),
+            "image_pairs": img,
+            "particles_within_rc_of_cathode": int((z < rc).sum()),
+            "particles_changed": int(changed.sum()),
+            "max_height_changed_over_rc": float(z[changed].max() / rc) if changed.any() else 0.0,
+        })
+        F_bc[n] = res[1]
+        del res, dF
+    out["refinement_rel_l2_128_vs_256"] = _rel(F_bc[128], F_bc[256])
+    out["ratio_bc_over_refinement_at_128"] = (out["levels"][0]["bc_rel_l2"]
+                                              / out["refinement_rel_l2_128_vs_256"])
+    return out
+
+
+def _grad_bunch(n):
+    spec = dict(B.WORKLOADS["gauss1m"])
+    x = B.positions(spec, n)
+    p = B.momenta(spec, n)
+    return x, p
+
+
+def energy(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps: int = 100):
+    x, p = _grad_bunch(n_particles)
+    xg, pg = _cuda(x), _cuda(p)
+    # a mesh with room for the bunch to move: the bounding box of the initial bunch, widened
+    prm = m.auto_mesh(_cuda(x * 1.05), m.Params(n=(64,) * 3, rc_over_h=2.0, precision=precision))
+    ctx = m.Context(prm, n_particles)
+    mass = prm.mass
+    k_e = 8.9875517923e9
+    self_e = n_particles * k_e * prm.q ** 2 * (prm.kappa / (prm.rc_over_h * max(prm.h))) / math.sqrt(math.pi)
+
+    def total_energy():
+        f, e = ctx.forces(xg, energy=True)
+        ke = float((pg * pg).sum()) / (2 * mass)
+        return ke + float(e.sum()) - self_e, f
+
+    E0, f = total_energy()
+    P0 = pg.sum(dim=0).clone()
+    t0 = time.time()
+    energies = [E0]
+    for _ in range(steps // 10):
+        f = ctx.push(xg, pg, 1e-12, 10, f)
+        energies.append(total_energy()[0])
+    ctx.sync()
+    elapsed = time.time() - t0
+    P1 = pg.sum(dim=0)
+    scale = float(torch.linalg.norm(pg, dim=1).sum())
+    return {"experiment": "energy", "n": n_particles, "steps": steps, "precision": precision,
+            "E0": E0, "rel_drift_final": (energies[-1] - E0) / abs(E0),
+            "rel_drift_max": max(abs(e - E0) for e in energies) / abs(E0),
+            "momentum_change_rel": float(torch.linalg.norm(P1 - P0)) / scale,
+            "seconds": elapsed}
+
+
+def gradient(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps: int = 200,
+             every: int = 20, directions: int = 2):
+    x, p = _grad_bunch(n_particles)
+    spec_mesh = m.auto_mesh(_cuda(x * 1.05), m.Params(n=(64,) * 3, rc_over_h=2.0,
+                                                       precision=precision,
+                                                       adj_slots=(steps + every - 1) // every,
+                                                       adj_segment=every))
+    ctx = m.Context(spec_mesh, n_particles)
+    dt = 1e-12
+    x0, p0 = _cuda(x), _cuda(p)
+
+    def J(xa, pa):
+        xx, pp = xa.clone(), pa.clone()
+        ctx.push(xx, pp, dt, steps)
+        return float(ctx.emittance(xx, pp).sum()), xx, pp
+
+    t0 = time.time()
+    J0, xT, pT = J(x0, p0)
+    _, gxT, gpT = ctx.emittance(xT, pT, grad=True)
+    gx0, gp0 = ctx.backward(x0, p0, dt, steps, gxT, gpT)
+    ctx.sync()
+    t_grad = time.time() - t0
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    res = []
+    for k in range(directions):
+        vx = torch.randn(x0.shape, generator=gen, device="cuda", dtype=torch.float64) * x0.abs().mean()
+        vp = torch.randn(p0.shape, generator=gen, device="cuda", dtype=torch.float64) * p0.abs().mean()
+        eps = 1e-6 if precision == m.FP64 else 1e-4
+        Jp, _, _ = J(x0 + eps * vx, p0 + eps * vp)
+        Jm, _, _ = J(x0 - eps * vx, p0 - eps * vp)
+        fd = (Jp - Jm) / (2 * eps)
+        ad = float((gx0 * vx).sum() + (gp0 * vp).sum())
+        res.append({"fd": fd, "adjoint": ad, "rel_diff": abs(fd - ad) / abs(fd)})
+    return {"experiment": "gradient", "n": n_particles, "steps": steps, "checkpoint_every": every,
+            "precision": precision, "J": J0, "directions": res, "seconds_gradient": t_grad}
+
+
+def main(argv):
+    which = argv[1] if len(argv) > 1 else "boundary"
+    prec = m.FP64 if "--fp64" in argv else m.FP32_MIXED
+    fn = {"boundary": boundary, "energy": energy, "gradient": gradient}[which]
+    print(json.dumps(fn(precision=prec)), flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv)
