@@ -19,9 +19,9 @@ Each prints one JSON line. Everything runs through the C ABI (``p3m``); no oracl
   expands by millimetres within 1e-10 s, so 200 steps of 1e-12 s would leave any fixed mesh)
   with checkpoints every 20: gradient of the final rms
   emittance J = eps_x + eps_y + eps_z with respect to (x0, p0) by the reverse pass, checked by
-  central finite differences along random directions (relative step 1e-6 of the coordinates in
-  FP64, 1e-4 in FP32, where the evaluation order of the force sums makes J reproducible only to
-  about 1e-10 relative).
+  central finite differences along two directions that change J at first order (dilations of
+  x0 and of p0 about their means), relative step 1e-6 in FP64 and 1e-3 in FP32 (the evaluation
+  order of the FP32 force sums is not fixed, which leaves J reproducible to about 1e-7).
 """
 from __future__ import annotations
 
@@ -151,17 +151,19 @@ def gradient(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps:
     gx0, gp0 = ctx.backward(x0, p0, dt, steps, gxT, gpT)
     ctx.sync()
     t_grad = time.time() - t0
-    gen = torch.Generator(device="cuda").manual_seed(7)
+    # directions that change the emittance at first order: dilations of the positions and of the
+    # momenta about their means (a random direction's first-order change nearly cancels over
+    # a million particles and drowns in the rounding of the FP32 force sums)
+    dirs = [("dilate_x", x0 - x0.mean(dim=0), torch.zeros_like(p0)),
+            ("dilate_p", torch.zeros_like(x0), p0 - p0.mean(dim=0))]
     res = []
-    for k in range(directions):
-        vx = torch.randn(x0.shape, generator=gen, device="cuda", dtype=torch.float64) * x0.abs().mean()
-        vp = torch.randn(p0.shape, generator=gen, device="cuda", dtype=torch.float64) * p0.abs().mean()
-        eps = 1e-6 if precision == m.FP64 else 1e-4
+    for name, vx, vp in dirs[:directions]:
+        eps = 1e-6 if precision == m.FP64 else 1e-3
         Jp, _, _ = J(x0 + eps * vx, p0 + eps * vp)
         Jm, _, _ = J(x0 - eps * vx, p0 - eps * vp)
         fd = (Jp - Jm) / (2 * eps)
         ad = float((gx0 * vx).sum() + (gp0 * vp).sum())
-        res.append({"fd": fd, "adjoint": ad, "rel_diff": abs(fd - ad) / abs(fd)})
+        res.append({"direction": name, "fd": fd, "adjoint": ad, "rel_diff": abs(fd - ad) / abs(fd)})
     return {"experiment": "gradient", "n": n_particles, "steps": steps, "dt": dt,
             "checkpoint_every": every,
             "precision": precision, "J": J0, "directions": res, "seconds_gradient": t_grad}
