@@ -171,9 +171,11 @@ def gradient(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps:
 
 def main(argv):
     which = argv[1] if len(argv) > 1 else "boundary"
-    prec = m.FP64 if "--fp64" in argv else m.FP32_MIXED
+    kw = {"precision": m.FP64 if "--fp64" in argv else m.FP32_MIXED}
+    if "--n" in argv:
+        kw["n_particles"] = int(argv[argv.index("--n") + 1])
     fn = {"boundary": boundary, "energy": energy, "gradient": gradient}[which]
-    print(json.dumps(fn(precision=prec)), flush=True)
+    print(json.dumps(fn(**kw)), flush=True)
 
 
 if __name__ == "__main__":
