@@ -171,7 +171,7 @@ cudaError_t alloc(T** ptr, size_t count) {
 }
 
 void free_all(p3m_ctx* c) {
-  void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recl, c->recm, c->fpp,
+  void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recm, c->fpp,
                   c->acc, c->qpad, c->qhat, c->khat_f, c->khat_i, c->fhat, c->freal,
                   c->phihat, c->phireal, c->dfac, c->energy_acc, c->pair_acc, c->err_dev,
                   c->ckpt, c->seg, c->lam_x, c->lam_p, c->xw, c->pw, c->tmp3, c->tmp3b,
@@ -436,8 +436,7 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   A(alloc(&c->bsum, tiles));
   A(alloc(&c->keys, n_max));
   A(alloc(&c->ranks, n_max));
-  A(cudaMalloc(&c->recp, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
-  if (c->fp32) A(alloc(&c->recl, n_max));
+  A(cudaMalloc(&c->recp, 32 * static_cast<size_t>(n_max)));
   A(cudaMalloc(&c->recm, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
   A(cudaMalloc(&c->fpp, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
   A(alloc(&c->acc, 3 * n_max));

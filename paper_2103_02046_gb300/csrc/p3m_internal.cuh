@@ -6,11 +6,11 @@
 //     contiguous run of sorted particles. Each of the 5 x 5 neighbour rows of a particle is then
 //     one index range, pruned by the particle's distance to the row.
 //   * Sorted records (counting sort by cell key):
-//       recp  positions in cutoff units from the mesh origin, (x - lo) / r_c:
-//             FP32 float4 {hi_x, hi_y, hi_z, bits(original index)}, FP64 {x, y, z, index};
-//       recl  FP32 only: float4 {lo_x, lo_y, lo_z, 0}, the rounding remainders, so that
-//             (hi_i - hi_j) + (lo_i - lo_j) is the separation to FP32 relative accuracy
-//             however close the pair is (read only for pairs near or inside the cutoff);
+//       recp  positions in cutoff units from the mesh origin, (x - lo) / r_c, 32 B each:
+//             FP32 two float4 {hi_x, hi_y, hi_z, bits(original index)} {lo_x, lo_y, lo_z, 0},
+//             lo the rounding remainders, so that (hi_i - hi_j) + (lo_i - lo_j) is the
+//             separation to FP32 relative accuracy however close the pair is; FP64
+//             {x, y, z, index};
 //       recm  assignment data in mesh units: the node c = floor(s + 1/2) (TSC) or floor(s)
 //             (CIC) packed 10 bits per axis, and the offset u = s - c, s = (x - lo) / h, computed
 //             in FP64 exactly as the definition reads (FP32 float4 or FP64 {u, node}).
@@ -140,8 +140,7 @@ struct p3m_ctx {
   uint32_t* bsum = nullptr;     // scan block sums
   uint32_t* keys = nullptr;     // [n_max] key of each input particle
   uint32_t* ranks = nullptr;    // [n_max] rank within its cell
-  void* recp = nullptr;         // [n_max] sorted positions, cutoff units (float4 hi / Rec64)
-  float4* recl = nullptr;       // [n_max] FP32: rounding remainders of recp
+  void* recp = nullptr;         // [n_max] sorted positions, cutoff units (2 float4 / Rec64)
   void* recm = nullptr;         // [n_max] sorted assignment records (float4 / Rec64)
   void* fpp = nullptr;          // [n_max] short-range force + potential, sorted (float4/double4)
   double* acc = nullptr;        // [3 n_max] adjoint accumulator, sorted order

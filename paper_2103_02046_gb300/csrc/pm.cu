@@ -171,7 +171,7 @@ __device__ __forceinline__ void particle_axes(const Geom& g, const typename RecT
 }
 
 __device__ __forceinline__ long long orig_index(const float4* recp, uint32_t i) {
-  return __float_as_int(recp[i].w);
+  return __float_as_int(recp[2 * i].w);  // FP32 records: hi at 2i carries the index
 }
 __device__ __forceinline__ long long orig_index(const Rec64* recp, uint32_t i) {
   return recp[i].idx;

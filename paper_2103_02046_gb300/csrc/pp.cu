@@ -121,8 +121,7 @@ __device__ __forceinline__ void for_rows(const Geom& g, const uint32_t* __restri
 // Position access: FP32 hi (+ lo remainder on demand), FP64 exact.
 // ------------------------------------------------------------------------------------------
 struct PosF {
-  const float4* __restrict__ hi;  // hi parts (w = index bits)
-  const float4* __restrict__ lo;  // rounding remainders
+  const float4* __restrict__ r;  // [2 n]: hi parts at 2j (w = index bits), lo parts at 2j + 1
 };
 struct PosD {
   const Rec64* __restrict__ r;
@@ -143,7 +142,7 @@ __global__ void __launch_bounds__(kThreads)
   if (i < N) {
     T pi[3], li[3] = {T(0), T(0), T(0)};
     if constexpr (sizeof(T) == 4) {
-      const float4 h = pos.hi[i], l = pos.lo[i];
+      const float4 h = pos.r[2 * i], l = pos.r[2 * i + 1];
       pi[0] = h.x; pi[1] = h.y; pi[2] = h.z;
       li[0] = l.x; li[1] = l.y; li[2] = l.z;
     } else {
@@ -158,13 +157,13 @@ __global__ void __launch_bounds__(kThreads)
         if (j == i) continue;
         T rx, ry, rz, r2;
         if constexpr (sizeof(T) == 4) {
-          const float4 hj = pos.hi[j];
+          const float4 hj = pos.r[2 * j];
           rx = pi[0] - hj.x;
           ry = pi[1] - hj.y;
           rz = pi[2] - hj.z;
           r2 = rx * rx + ry * ry + rz * rz;
           if (!(r2 < T(1) + T(kFilterSlack))) continue;
-          const float4 lj = pos.lo[j];
+          const float4 lj = pos.r[2 * j + 1];
           rx += li[0] - lj.x;
           ry += li[1] - lj.y;
           rz += li[2] - lj.z;
@@ -201,7 +200,7 @@ __global__ void __launch_bounds__(kThreads)
           for (uint32_t j = j0; j < j1; ++j) {
             T rx, ry, rz;
             if constexpr (sizeof(T) == 4) {
-              const float4 hj = pos.hi[j], lj = pos.lo[j];
+              const float4 hj = pos.r[2 * j], lj = pos.r[2 * j + 1];
               rx = (pi[0] - hj.x) + (li[0] - lj.x);
               ry = (pi[1] - hj.y) + (li[1] - lj.y);
               // z_i - (img_c - z_j) with an exact two-sum of the hi parts
@@ -248,8 +247,7 @@ __global__ void __launch_bounds__(kThreads)
 // consecutive particles of one stretch of an x-row. The warp walks the 25 neighbour rows
 // together: for row r every lane computes its own pruned candidate run [j0, j1) (so pruning
 // stays per particle), then the warp steps t = 0 .. max_len - 1 and each lane tests j0 + t
-// (a lane past its run re-reads itself, which is never a pair). The low parts of the positions
-// are loaded only by lanes whose high-part separation passes the cutoff test. Control
+// (a lane past its run re-reads itself, which has separation 0 and is never a pair). Control
 // flow is warp-uniform: the pair function runs, predicated, whenever any lane holds a pair.
 // Lanes of one warp have runs of nearly the same length and start, so few lanes idle and the
 // loads of one step touch a few cache lines. Separations are exact to FP32 relative rounding
@@ -297,16 +295,16 @@ __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restr
 template <int kDeg>
 __global__ void __launch_bounds__(kThreads, 8)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
-             const float4* __restrict__ hi, const float4* __restrict__ lo,
-             const uint32_t* __restrict__ starts, float4* __restrict__ fpp,
+             const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
+             float4* __restrict__ fpp,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
   const uint32_t N = *total;
   const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
   const bool alive = i < N;
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), li = pi;
   if (alive) {
-    pi = hi[i];
-    li = lo[i];
+    pi = rec[2 * i];
+    li = rec[2 * i + 1];
   }
   Acc2 sum[4];
   for (int k = 0; k < 4; ++k) sum[k].hi = sum[k].lo = 0.f;
@@ -325,17 +323,12 @@ __global__ void __launch_bounds__(kThreads, 8)
     for (int t = 0; t < maxlen; ++t) {
       const bool in = t < len;
       const uint32_t j = in ? j0 + t : i;  // an idle lane re-reads itself: separation 0, no pair
-      const float4 hj = hi[j];
-      float rx = pi.x - hj.x, ry = pi.y - hj.y, rz = pi.z - hj.z;
-      const float r2h = rx * rx + ry * ry + rz * rz;
-      const bool cand = r2h < 1.f + kFilterSlack && j != i;
-      float4 lj = make_float4(li.x, li.y, li.z, 0.f);
-      if (cand) lj = lo[j];  // remainders only where the pair may be inside the cutoff
-      rx += li.x - lj.x;
-      ry += li.y - lj.y;
-      rz += li.z - lj.z;
+      const float4 hj = rec[2 * j], lj = rec[2 * j + 1];
+      const float rx = (pi.x - hj.x) + (li.x - lj.x);
+      const float ry = (pi.y - hj.y) + (li.y - lj.y);
+      const float rz = (pi.z - hj.z) + (li.z - lj.z);
       const float r2 = rx * rx + ry * ry + rz * rz;
-      const bool hit = cand && r2 < 1.f && r2 > 0.f;
+      const bool hit = r2 < 1.f && r2 > 0.f;  // the self pair has r2 == 0 exactly
       if (__any_sync(0xffffffffu, hit)) {
         float fco, pot;
         pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
@@ -361,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 8)
       for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t ja, uint32_t jb) {
         float rowv[4] = {0.f, 0.f, 0.f, 0.f};
         for (uint32_t jj = ja; jj < jb; ++jj) {
-          const float4 hj = hi[jj], lj = lo[jj];
+          const float4 hj = rec[2 * jj], lj = rec[2 * jj + 1];
           const float ax = (pi.x - hj.x) + (li.x - lj.x);
           const float ay = (pi.y - hj.y) + (li.y - lj.y);
           const float s = pi.z + hj.z;
@@ -418,7 +411,7 @@ __global__ void __launch_bounds__(kThreads)
   T pi[3], li[3] = {T(0), T(0), T(0)};
   long long idx;
   if constexpr (sizeof(T) == 4) {
-    const float4 h = pos.hi[i], l = pos.lo[i];
+    const float4 h = pos.r[2 * i], l = pos.r[2 * i + 1];
     pi[0] = h.x; pi[1] = h.y; pi[2] = h.z;
     li[0] = l.x; li[1] = l.y; li[2] = l.z;
     idx = __float_as_int(h.w);
@@ -432,7 +425,7 @@ __global__ void __launch_bounds__(kThreads)
   double out[3] = {0.0, 0.0, 0.0};
   auto sep = [&](uint32_t j, bool image, T& rx, T& ry, T& rz, long long& jdx) {
     if constexpr (sizeof(T) == 4) {
-      const float4 hj = pos.hi[j], lj = pos.lo[j];
+      const float4 hj = pos.r[2 * j], lj = pos.r[2 * j + 1];
       jdx = __float_as_int(hj.w);
       rx = (pi[0] - hj.x) + (li[0] - lj.x);
       ry = (pi[1] - hj.y) + (li[1] - lj.y);
@@ -518,7 +511,7 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
     const unsigned wblocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
     auto run = [&](auto kern) {
       kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
-                                       c->recl, c->starts, static_cast<float4*>(c->fpp),
+                                       c->starts, static_cast<float4*>(c->fpp),
                                        c->energy_acc, c->pair_acc);
     };
     switch (c->poly.deg) {
@@ -547,7 +540,7 @@ void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s)
   const double scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc * c->g.rc);
   if (c->fp32)
     k_pp_vjp<float, PosF><<<blocks, kThreads, 0, s>>>(
-        c->g, total, PosF{static_cast<const float4*>(c->recp), c->recl}, c->starts, w, c->acc,
+        c->g, total, PosF{static_cast<const float4*>(c->recp)}, c->starts, w, c->acc,
         scale);
   else
     k_pp_vjp<double, PosD><<<blocks, kThreads, 0, s>>>(

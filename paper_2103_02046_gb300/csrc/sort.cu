@@ -178,7 +178,7 @@ template <bool kFP32>
 __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
                           const uint32_t* __restrict__ keys, const uint32_t* __restrict__ ranks,
                           const uint32_t* __restrict__ starts, void* __restrict__ recp,
-                          float4* __restrict__ recl, void* __restrict__ recm) {
+                          void* __restrict__ recm) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n) return;
   const uint32_t key = keys[i];
@@ -212,9 +212,10 @@ __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
       hi[d] = static_cast<float>(xr[d]);
       lo[d] = static_cast<float>(xr[d] - static_cast<double>(hi[d]));
     }
-    reinterpret_cast<float4*>(recp)[pos] =
-        make_float4(hi[0], hi[1], hi[2], __int_as_float(static_cast<int>(i)));
-    recl[pos] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    // hi and lo together fill one 32-byte sector: a full-sector scattered write
+    float4* r = reinterpret_cast<float4*>(recp) + 2 * static_cast<size_t>(pos);
+    r[0] = make_float4(hi[0], hi[1], hi[2], __int_as_float(static_cast<int>(i)));
+    r[1] = make_float4(lo[0], lo[1], lo[2], 0.f);
     reinterpret_cast<float4*>(recm)[pos] =
         make_float4(static_cast<float>(u[0]), static_cast<float>(u[1]), static_cast<float>(u[2]),
                     __uint_as_float(node));
@@ -261,10 +262,10 @@ void launch_scatter(const p3m_ctx* c, const double* x, int64_t n) {
   if (n == 0) return;
   if (c->fp32)
     k_scatter<true><<<grid_for(n, kBinThreads), kBinThreads, 0, c->work>>>(
-        c->g, x, n, c->keys, c->ranks, c->starts, c->recp, c->recl, c->recm);
+        c->g, x, n, c->keys, c->ranks, c->starts, c->recp, c->recm);
   else
     k_scatter<false><<<grid_for(n, kBinThreads), kBinThreads, 0, c->work>>>(
-        c->g, x, n, c->keys, c->ranks, c->starts, c->recp, nullptr, c->recm);
+        c->g, x, n, c->keys, c->ranks, c->starts, c->recp, c->recm);
 }
 
 }  // namespace p3m
