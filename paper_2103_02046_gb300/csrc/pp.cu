@@ -28,7 +28,6 @@ namespace {
 constexpr int kThreads = 128;
 constexpr float kFilterSlack = 1e-4f;   // hi-only separations err by < 1e-5 r_c
 constexpr int kRowReach = kRowsPerCutoff;          // neighbour rows on each side (y and z)
-constexpr int kRing = 4;                           // deferred pairs per lane (power of two)
 constexpr int kRowSpan = 2 * kRowReach + 1;
 
 // two-float accumulator (hi + lo) with Knuth's TwoSum
@@ -249,9 +248,7 @@ __global__ void __launch_bounds__(kThreads)
 // together: for row r every lane computes its own pruned candidate run [j0, j1) (so pruning
 // stays per particle), then the warp steps t = 0 .. max_len - 1 and each lane tests j0 + t
 // (a lane past its run re-reads itself, which has separation 0 and is never a pair). Control
-// flow is warp-uniform. Pairs found wait in a per-lane ring in shared memory (kRing entries);
-// whenever a ring is full, every lane that holds one evaluates its oldest pair, so the pair
-// function runs with most lanes busy.
+// flow is warp-uniform: the pair function runs, predicated, whenever any lane holds a pair.
 // Lanes of one warp have runs of nearly the same length and start, so few lanes idle and the
 // loads of one step touch a few cache lines. Separations are exact to FP32 relative rounding
 // ((hi_i - hi_j) + (lo_i - lo_j)). Each row's FP32 partial sum is folded into a two-float
@@ -316,34 +313,13 @@ __global__ void __launch_bounds__(kThreads, 8)
                      g.nc[1] - 1);
   const int cz = min(max(static_cast<int>(floorf(pi.z * static_cast<float>(g.inv_cw[2]))), 0),
                      g.nc[2] - 1);
-  // In-cutoff separations wait in a per-lane ring of kRing slots in shared memory; whenever some
-  // lane's ring is full, every lane holding one evaluates its oldest entry. The pair function
-  // then runs with most lanes busy instead of the ~1/5 that hit at a single step.
-  __shared__ float4 ring_s[kThreads / 32][kRing][32];
-  float4(*ring)[32] = ring_s[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
-  int head = 0, cnt = 0;
-  float part[4] = {0.f, 0.f, 0.f, 0.f};
-  auto evaluate = [&]() {
-    const bool has = cnt > 0;
-    const float4 e = ring[head & (kRing - 1)][lane];
-    float fco, pot;
-    pair_poly<kDeg>(P, has ? e.w : 0.5f, fco, pot);
-    fco = has ? fco : 0.f;
-    pot = has ? pot : 0.f;
-    part[0] = fmaf(fco, e.x, part[0]);
-    part[1] = fmaf(fco, e.y, part[1]);
-    part[2] = fmaf(fco, e.z, part[2]);
-    part[3] += pot;
-    head += has;
-    cnt -= has;
-  };
   for (int r = 0; r < kRowSpan * kRowSpan; ++r) {
     uint32_t j0 = 0, j1 = 0;
     if (alive) row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
     const int len = static_cast<int>(j1 - j0);
     int maxlen = len;
     for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
+    float part[4] = {0.f, 0.f, 0.f, 0.f};
     for (int t = 0; t < maxlen; ++t) {
       const bool in = t < len;
       const uint32_t j = in ? j0 + t : i;  // an idle lane re-reads itself: separation 0, no pair
@@ -352,20 +328,21 @@ __global__ void __launch_bounds__(kThreads, 8)
       const float ry = (pi.y - hj.y) + (li.y - lj.y);
       const float rz = (pi.z - hj.z) + (li.z - lj.z);
       const float r2 = rx * rx + ry * ry + rz * rz;
-      if (r2 < 1.f && r2 > 0.f) {  // the self pair has r2 == 0 exactly
-        ring[(head + cnt) & (kRing - 1)][lane] = make_float4(rx, ry, rz, r2);
-        ++cnt;
-        ++np;
+      const bool hit = r2 < 1.f && r2 > 0.f;  // the self pair has r2 == 0 exactly
+      if (__any_sync(0xffffffffu, hit)) {
+        float fco, pot;
+        pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
+        fco = hit ? fco : 0.f;
+        pot = hit ? pot : 0.f;
+        part[0] = fmaf(fco, rx, part[0]);
+        part[1] = fmaf(fco, ry, part[1]);
+        part[2] = fmaf(fco, rz, part[2]);
+        part[3] += pot;
+        np += hit;
       }
-      if (__any_sync(0xffffffffu, cnt == kRing)) evaluate();
     }
-    for (int k = 0; k < 4; ++k) {
-      sum[k].add(part[k]);
-      part[k] = 0.f;
-    }
+    for (int k = 0; k < 4; ++k) sum[k].add(part[k]);
   }
-  while (__any_sync(0xffffffffu, cnt > 0)) evaluate();
-  for (int k = 0; k < 4; ++k) sum[k].add(part[k]);
   unsigned long long ni = 0;
   if (alive && g.pp_bc) {
     // images within r_c of particles less than r_c above the cathode (rare): plain loop
