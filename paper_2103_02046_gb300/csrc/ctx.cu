@@ -172,15 +172,15 @@ cudaError_t alloc(T** ptr, size_t count) {
 
 void free_all(p3m_ctx* c) {
   void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recm, c->fpp,
-                  c->acc, c->qpad, c->qhat, c->khat_f, c->khat_i, c->fhat, c->freal,
+                  c->acc, c->qpad, c->qhat, c->qhat2, c->khat_f, c->khat_i, c->fhat, c->freal,
                   c->phihat, c->phireal, c->dfac, c->energy_acc, c->pair_acc, c->err_dev,
                   c->ckpt, c->seg, c->lam_x, c->lam_p, c->xw, c->pw, c->tmp3, c->tmp3b,
                   c->f_work, c->red};
   for (void* b : bufs) cudaFree(b);
   if (c->err_host) cudaFreeHost(c->err_host);
-  if (c->have_r2c) cufftDestroy(c->plan_r2c);
-  if (c->have_c2r) cufftDestroy(c->plan_c2r);
-  if (c->have_c2r3) cufftDestroy(c->plan_c2r3);
+  if (c->have_xy_f) cufftDestroy(c->plan_xy_f);
+  if (c->have_z) cufftDestroy(c->plan_z);
+  if (c->have_xy_i) cufftDestroy(c->plan_xy_i);
   if (c->s_pp) cudaStreamDestroy(c->s_pp);
   if (c->work) cudaStreamDestroy(c->work);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -234,13 +234,39 @@ void sort_particles(p3m_ctx* c, const double* x, int64_t n, double* f_zero) {
 
 p3m_status fft_r2c(p3m_ctx* c) {
   cufftResult r;
-  if (c->fp32)
-    r = cufftExecR2C(c->plan_r2c, static_cast<cufftReal*>(c->qpad),
+  if (c->fp32) {
+    r = cufftExecR2C(c->plan_xy_f, static_cast<cufftReal*>(c->qpad),
                      static_cast<cufftComplex*>(c->qhat));
-  else
-    r = cufftExecD2Z(c->plan_r2c, static_cast<cufftDoubleReal*>(c->qpad),
+    if (r == CUFFT_SUCCESS)
+      r = cufftExecC2C(c->plan_z, static_cast<cufftComplex*>(c->qhat),
+                       static_cast<cufftComplex*>(c->qhat2), CUFFT_FORWARD);
+  } else {
+    r = cufftExecD2Z(c->plan_xy_f, static_cast<cufftDoubleReal*>(c->qpad),
                      static_cast<cufftDoubleComplex*>(c->qhat));
+    if (r == CUFFT_SUCCESS)
+      r = cufftExecZ2Z(c->plan_z, static_cast<cufftDoubleComplex*>(c->qhat),
+                       static_cast<cufftDoubleComplex*>(c->qhat2), CUFFT_FORWARD);
+  }
   return r == CUFFT_SUCCESS ? P3M_OK : fail(c, P3M_ECUFFT, "cuFFT forward transform failed");
+}
+
+// Inverse transform of one spectrum (destroyed) into the planes z < n_z of a real field.
+cufftResult fft_c2r(p3m_ctx* c, void* spec, void* real) {
+  cufftResult r;
+  if (c->fp32) {
+    r = cufftExecC2C(c->plan_z, static_cast<cufftComplex*>(spec),
+                     static_cast<cufftComplex*>(spec), CUFFT_INVERSE);
+    if (r == CUFFT_SUCCESS)
+      r = cufftExecC2R(c->plan_xy_i, static_cast<cufftComplex*>(spec),
+                       static_cast<cufftReal*>(real));
+  } else {
+    r = cufftExecZ2Z(c->plan_z, static_cast<cufftDoubleComplex*>(spec),
+                     static_cast<cufftDoubleComplex*>(spec), CUFFT_INVERSE);
+    if (r == CUFFT_SUCCESS)
+      r = cufftExecZ2D(c->plan_xy_i, static_cast<cufftDoubleComplex*>(spec),
+                       static_cast<cufftDoubleReal*>(real));
+  }
+  return r;
 }
 
 // Solve on the current qpad: FP64 -> potential; FP32 -> difference fields (and the potential
@@ -250,21 +276,18 @@ p3m_status mesh_solve(p3m_ctx* c, bool want_phi, bool want_diff, bool want_energ
   if (s != P3M_OK) return s;
   if (!c->fp32) want_phi = true, want_diff = false;
   launch_green_multiply(c, want_phi, want_diff, want_energy);
-  cufftResult r = CUFFT_SUCCESS;
   if (want_phi) {
-    if (c->fp32)
-      r = cufftExecC2R(c->plan_c2r, static_cast<cufftComplex*>(c->phihat),
-                       static_cast<cufftReal*>(c->phireal));
-    else
-      r = cufftExecZ2D(c->plan_c2r, static_cast<cufftDoubleComplex*>(c->phihat),
-                       static_cast<cufftDoubleReal*>(c->phireal));
-    if (r != CUFFT_SUCCESS) return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
+    if (fft_c2r(c, c->phihat, c->phireal) != CUFFT_SUCCESS)
+      return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
     c->phi_valid = true;
   }
   if (want_diff) {
-    r = cufftExecC2R(c->plan_c2r3, static_cast<cufftComplex*>(c->fhat),
-                     static_cast<cufftReal*>(c->freal));
-    if (r != CUFFT_SUCCESS) return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
+    for (int d = 0; d < 3; ++d) {
+      void* spec = static_cast<float2*>(c->fhat) + d * c->n_cplx;
+      void* real = static_cast<float*>(c->freal) + d * c->n_real;
+      if (fft_c2r(c, spec, real) != CUFFT_SUCCESS)
+        return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
+    }
   }
   return P3M_OK;
 }
@@ -442,6 +465,7 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   A(alloc(&c->acc, 3 * n_max));
   A(cudaMalloc(&c->qpad, es * c->n_real));
   A(cudaMalloc(&c->qhat, 2 * es * c->n_cplx));
+  A(cudaMalloc(&c->qhat2, 2 * es * c->n_cplx));
   A(cudaMalloc(&c->khat_f, es * c->n_cplx));
   if (g.pm_bc) A(cudaMalloc(&c->khat_i, 2 * es * c->n_cplx));
   A(cudaMalloc(&c->phihat, 2 * es * c->n_cplx));
@@ -487,6 +511,7 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   *c->err_host = 0;
   cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->work);
   cudaMemsetAsync(c->qpad, 0, es * c->n_real, c->work);
+  cudaMemsetAsync(c->qhat, 0, 2 * es * c->n_cplx, c->work);  // planes z >= n_z stay zero
   if (c->fp32) {
     std::vector<float2> fac(g.M[0] / 2 + 1 + g.M[1] + g.M[2]);
     size_t o = 0;
@@ -502,26 +527,36 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     cudaMemcpyAsync(c->dfac, fac.data(), sizeof(float2) * fac.size(), cudaMemcpyHostToDevice,
                     c->work);
   }
-  // FFT plans
-  cufftResult r = cufftPlan3d(&c->plan_r2c, g.M[2], g.M[1], g.M[0], c->fp32 ? CUFFT_R2C : CUFFT_D2Z);
-  c->have_r2c = r == CUFFT_SUCCESS;
-  if (r == CUFFT_SUCCESS) {
-    r = cufftPlan3d(&c->plan_c2r, g.M[2], g.M[1], g.M[0], c->fp32 ? CUFFT_C2R : CUFFT_Z2D);
-    c->have_c2r = r == CUFFT_SUCCESS;
+  // FFT plans (see p3m_internal.cuh: pruned to the planes that carry charge or are read back)
+  {
+    const int Hx = g.M[0] / 2 + 1;
+    int xy[2] = {g.M[1], g.M[0]};
+    int in_r[2] = {g.M[1], g.M[0]}, in_c[2] = {g.M[1], Hx};
+    int zlen[1] = {g.M[2]};
+    const long long col = static_cast<long long>(g.M[1]) * Hx;
+    cufftResult r = cufftPlanMany(&c->plan_xy_f, 2, xy, in_r, 1, g.M[1] * g.M[0], in_c, 1,
+                                  g.M[1] * Hx, c->fp32 ? CUFFT_R2C : CUFFT_D2Z, g.n[2]);
+    c->have_xy_f = r == CUFFT_SUCCESS;
+    if (r == CUFFT_SUCCESS) {
+      r = cufftPlanMany(&c->plan_z, 1, zlen, zlen, static_cast<int>(col), 1, zlen,
+                        static_cast<int>(col), 1, c->fp32 ? CUFFT_C2C : CUFFT_Z2Z,
+                        static_cast<int>(col));
+      c->have_z = r == CUFFT_SUCCESS;
+    }
+    if (r == CUFFT_SUCCESS) {
+      r = cufftPlanMany(&c->plan_xy_i, 2, xy, in_c, 1, g.M[1] * Hx, in_r, 1, g.M[1] * g.M[0],
+                        c->fp32 ? CUFFT_C2R : CUFFT_Z2D, g.n[2]);
+      c->have_xy_i = r == CUFFT_SUCCESS;
+    }
+    if (r != CUFFT_SUCCESS) {
+      free_all(c);
+      delete c;
+      return r == CUFFT_ALLOC_FAILED ? P3M_ENOMEM : P3M_ECUFFT;
+    }
+    cufftSetStream(c->plan_xy_f, c->work);
+    cufftSetStream(c->plan_z, c->work);
+    cufftSetStream(c->plan_xy_i, c->work);
   }
-  if (r == CUFFT_SUCCESS && c->fp32) {
-    int dims[3] = {g.M[2], g.M[1], g.M[0]};
-    r = cufftPlanMany(&c->plan_c2r3, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 3);
-    c->have_c2r3 = r == CUFFT_SUCCESS;
-  }
-  if (r != CUFFT_SUCCESS) {
-    free_all(c);
-    delete c;
-    return r == CUFFT_ALLOC_FAILED ? P3M_ENOMEM : P3M_ECUFFT;
-  }
-  cufftSetStream(c->plan_r2c, c->work);
-  cufftSetStream(c->plan_c2r, c->work);
-  if (c->have_c2r3) cufftSetStream(c->plan_c2r3, c->work);
   e = build_green(c);
   if (e != cudaSuccess) {
     free_all(c);

@@ -149,7 +149,7 @@ struct p3m_ctx {
   size_t n_real = 0;            // Mx My Mz
   size_t n_cplx = 0;            // Mz My (Mx/2 + 1)
   void* qpad = nullptr;         // real, doubled mesh, zero outside the n^3 block
-  void* qhat = nullptr;         // spectrum of qpad
+  void* qhat = nullptr;         // x-y transformed planes z < n_z (planes above stay zero)
   void* khat_f = nullptr;       // real spectrum of the free kernel (scaled)
   void* khat_i = nullptr;       // complex spectrum of the image kernel (scaled, phase folded)
   void* fhat = nullptr;         // FP32: 3 difference spectra; FP64: unused
@@ -157,8 +157,14 @@ struct p3m_ctx {
   void* phihat = nullptr;       // potential spectrum
   void* phireal = nullptr;      // potential on the doubled mesh
   float2* dfac = nullptr;       // FP32: difference factors e^{2 pi i k/M} - 1 per axis (Mx/2+1 + My + Mz)
-  cufftHandle plan_r2c = 0, plan_c2r = 0, plan_c2r3 = 0;
-  bool have_r2c = false, have_c2r = false, have_c2r3 = false;
+  // Pruned transforms of the doubled mesh: the charge is non-zero, and the fields are needed,
+  // only in the n^3 block, so the x-y plane transforms run on the first n_z planes only and
+  // the z transforms are strided 1D batches over all (kx, ky) columns.
+  void* qhat2 = nullptr;        // full spectrum of qpad (z transformed, out of place)
+  cufftHandle plan_xy_f = 0;    // 2D R2C (or D2Z) on planes z < n_z: qpad -> qhat
+  cufftHandle plan_z = 0;       // 1D C2C (or Z2Z) along z, stride My (Mx/2 + 1), all columns
+  cufftHandle plan_xy_i = 0;    // 2D C2R (or Z2D) on planes z < n_z: spectrum -> real field
+  bool have_xy_f = false, have_z = false, have_xy_i = false;
 
   // diagnostics
   double* energy_acc = nullptr;              // device [2]

@@ -195,8 +195,15 @@ __global__ void __launch_bounds__(kDepThreads)
                     const typename RecT<T>::type* __restrict__ recm,
                     const typename RecT<T>::type* __restrict__ recp,
                     const double* __restrict__ w, T* __restrict__ qpad) {
-  constexpr int kTile = kTileBytes / sizeof(T);
-  __shared__ T tile[kTile];
+  // FP32 charge deposit: the tile accumulates in unsigned 32-bit fixed point (2^-23 per unit of
+  // weight; a tile node receives at most one weight <= 27/64 from each of 1024 particles, so the
+  // sum stays below 2^32),
+  // because integer shared-memory atomics are native while float ones are compare-and-swap
+  // loops. Sums inside a tile are then exact and independent of the order of the particles.
+  constexpr bool kFixed = (sizeof(T) == 4) && !kDipole;
+  using Slot = typename std::conditional<kFixed, unsigned int, T>::type;
+  constexpr int kTile = kTileBytes / sizeof(Slot);
+  __shared__ Slot tile[kTile];
   __shared__ int bmin[3], bmax[3];
   const uint32_t N = *total;
   const uint32_t b0 = blockIdx.x * kDepPerBlock;
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(kDepThreads)
   const int ex = bmax[0] - bmin[0] + 1, ey = bmax[1] - bmin[1] + 1, ez = bmax[2] - bmin[2] + 1;
   const bool use_tile = static_cast<long long>(ex) * ey * ez <= kTile;
   if (use_tile)
-    for (int t = threadIdx.x; t < ex * ey * ez; t += kDepThreads) tile[t] = T(0);
+    for (int t = threadIdx.x; t < ex * ey * ez; t += kDepThreads) tile[t] = Slot(0);
   __syncthreads();
   for (int k = 0; k < kDepItems; ++k) {
     const uint32_t i = b0 + k * kDepThreads + threadIdx.x;
@@ -258,16 +265,24 @@ __global__ void __launch_bounds__(kDepThreads)
           else
             v = A[0].w[a] * A[1].w[b] * A[2].w[c];
           const int gx = A[0].c + a, gy = A[1].c + b, gz = A[2].c + c;
-          if (use_tile)
-            atomicAdd(&tile[((gz - bmin[2]) * ey + (gy - bmin[1])) * ex + (gx - bmin[0])], v);
-          else
+          if (use_tile) {
+            Slot* slot = &tile[((gz - bmin[2]) * ey + (gy - bmin[1])) * ex + (gx - bmin[0])];
+            if constexpr (kFixed)
+              atomicAdd(slot, __float2uint_rn(static_cast<float>(v) * 8388608.0f));
+            else
+              atomicAdd(slot, v);
+          } else
             atomicAdd(qpad + real_index(g, gx, gy, gz), v);
         }
   }
   if (!use_tile) return;
   __syncthreads();
   for (int t = threadIdx.x; t < ex * ey * ez; t += kDepThreads) {
-    const T v = tile[t];
+    T v;
+    if constexpr (kFixed)
+      v = static_cast<T>(static_cast<float>(tile[t]) * (1.0f / 8388608.0f));
+    else
+      v = tile[t];
     if (v != T(0)) {
       const int gx = bmin[0] + t % ex, gy = bmin[1] + (t / ex) % ey, gz = bmin[2] + t / (ex * ey);
       atomicAdd(qpad + real_index(g, gx, gy, gz), v);
@@ -672,13 +687,13 @@ void launch_green_multiply(const p3m_ctx* c, bool want_phi, bool want_diff, bool
   double* en = want_energy ? c->energy_acc + 1 : nullptr;
   if (c->fp32)
     k_green_multiply<float><<<grid, kThreads, 0, c->work>>>(
-        g, static_cast<const float2*>(c->qhat), static_cast<const float*>(c->khat_f),
+        g, static_cast<const float2*>(c->qhat2), static_cast<const float*>(c->khat_f),
         static_cast<const float2*>(c->khat_i), c->dfac,
         want_diff ? static_cast<float2*>(c->fhat) : nullptr,
         want_phi ? static_cast<float2*>(c->phihat) : nullptr, en, c->n_cplx);
   else
     k_green_multiply<double><<<grid, kThreads, 0, c->work>>>(
-        g, static_cast<const double2*>(c->qhat), static_cast<const double*>(c->khat_f),
+        g, static_cast<const double2*>(c->qhat2), static_cast<const double*>(c->khat_f),
         static_cast<const double2*>(c->khat_i), nullptr, nullptr,
         want_phi ? static_cast<double2*>(c->phihat) : nullptr, en, c->n_cplx);
 }
