@@ -293,7 +293,7 @@ __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restr
 }
 
 template <int kDeg>
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, 10)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
              const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
              float4* __restrict__ fpp,
