@@ -160,6 +160,22 @@ def cpu_baseline(x: np.ndarray, mesh: int, rc: float, budget_s: float = 25.0):
 
 
 # ------------------------------------------------------------------------------------------
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """Largest of the ranks' timed-region durations (ms); every rank gets the same value."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t)
+
+
+def job_rate(evals_per_rank: int, world: int, t_max_ms: float) -> float:
+    """Whole-job evaluations per second: all ranks' evaluations over the slowest rank's time."""
+    return evals_per_rank * world / (t_max_ms / 1e3)
+
+
+# ------------------------------------------------------------------------------------------
 def run_ours(a, rank, world, local_rank):
     import torch
     from paper_2103_02046_gb300 import p3m as m
@@ -202,12 +218,8 @@ def run_ours(a, rank, world, local_rank):
         barrier()
     ms = ev0.elapsed_time(ev1)
     ctx.sync()
-    t_max = ms
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt)
-    evals_per_s = K * world / (t_max / 1e3)
+    t_max = max_over_ranks(ms, world, dev)
+    evals_per_s = job_rate(K, world, t_max)
     pp_avg_ms = float(np.mean(pp_ms))
     pp_pairs_per_s = pairs / (pp_avg_ms / 1e3)
     clocks = clk.summary()
@@ -249,12 +261,8 @@ def run_ours(a, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    t_e2e = e2e_ms
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(tt)
-    e2e_value = K * world / (t_e2e / 1e3)
+    t_e2e = max_over_ranks(e2e_ms, world, dev)
+    e2e_value = job_rate(K, world, t_e2e)
 
     sm_mhz_max = 2070.0
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz_max * 1e6 / 1e12

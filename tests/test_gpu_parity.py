@@ -270,3 +270,95 @@ def test_full_size_sphere_sampled(precision):
     pairs, _ = ctx.pair_count()
     assert pairs > 1.0e9
     ctx.close()
+
+
+# ------------------------------------------------------------------------------------------
+# the other workloads at their own sizes
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [0, 1])
+def test_workload_gauss4k_cathode_eval_and_10_steps(precision):
+    """4096-particle Gaussian (sigma 1 mm, seed 0, cold, q = 1e-15 C), 16^3 mesh, TSC, r_c = 2h,
+    grounded cathode one spacing below the lowest particle: one evaluation and 10 steps of
+    1e-12 s against the oracle."""
+    spec = dict(B.WORKLOADS["gauss4k"])
+    x0 = B.positions(spec)
+    h = O.auto_mesh(x0, 16).h[2]
+    x = B.lift_to_plane(x0, 0.0, h)
+    P = O.auto_mesh(x * np.array([1.0, 1.0, 1.0]), 16, rc_over_h=2.0, pm_bc=1, z_cathode=0.0)
+    kern = O.green_kernels(P)
+    ref = O.forces(x, P, kernels=kern)
+    ctx = p3m().Context(gpu_params(P, precision), len(x))
+    xg = cuda(x)
+    f = ctx.forces(xg)
+    ctx.sync()
+    assert rel(f, ref.F) <= TOL[precision]
+    p = np.zeros_like(x)
+    xT, pT, _ = O.push(x, p, 1e-12, 10, P, force=lambda y: O.forces(y, P, kernels=kern).F)
+    pg = cuda(p)
+    ctx.push(xg, pg, 1e-12, 10)
+    ctx.sync()
+    assert rel(xg - cuda(x), xT - x) <= 10 * TOL[precision]
+    assert rel(pg, pT) <= 10 * TOL[precision]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [1, 0])
+def test_workload_gauss1m_sampled(precision):
+    """1,048,576-particle Gaussian (sigma 1, 1, 3 mm, thermal), 64^3 mesh, r_c = 2h (about 3e10
+    in-cutoff pairs per evaluation): one evaluation on 1024 sampled particles."""
+    spec = dict(B.WORKLOADS["gauss1m"])
+    x = B.positions(spec)
+    P = O.auto_mesh(x, 64, rc_over_h=2.0)
+    idx = B.subsample(len(x), 1024, seed=12345)
+    ref = O.forces(x, P, sample=idx)
+    ctx = p3m().Context(gpu_params(P, precision), len(x))
+    f = ctx.forces(cuda(x))
+    ctx.sync()
+    assert rel(f[torch.from_numpy(idx).cuda()], ref.F) <= TOL[precision]
+    ctx.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("pp_bc", [0, 1])
+def test_workload_halo4m_cathode_sampled(precision, pp_bc):
+    """4,194,304 particles (95% Gaussian core sigma 1 mm + 5% shell at 4-6 sigma) lifted one
+    spacing above the cathode, 128^3 mesh, r_c = 3h, cathode in the long range and (pp_bc = 1)
+    in the short range: one evaluation on 1024 sampled particles plus every particle within
+    r_c of the cathode."""
+    spec = dict(B.WORKLOADS["halo4m"])
+    x0 = B.positions(spec)
+    h = O.auto_mesh(x0, 128).h[2]
+    x = B.lift_to_plane(x0, 0.0, h)
+    P = O.auto_mesh(x, 128, rc_over_h=3.0, pm_bc=1, pp_bc=pp_bc, z_cathode=0.0)
+    near = np.nonzero(x[:, 2] < P.rc)[0]
+    idx = np.union1d(B.subsample(len(x), 1024, seed=12345), near)
+    ref = O.forces(x, P, sample=idx)
+    ctx = p3m().Context(gpu_params(P, precision), len(x))
+    f = ctx.forces(cuda(x))
+    ctx.sync()
+    assert rel(f[torch.from_numpy(idx).cuda()], ref.F) <= TOL[precision]
+    if pp_bc:
+        assert ref.image_pairs > 0
+    ctx.close()
+
+
+@pytest.mark.slow
+def test_workload_gradient_4096_200_steps():
+    """Reverse pass over 200 steps with checkpoints every 20 (4096-particle Gaussian, sigma 1, 1,
+    3 mm, thermal, 64^3 mesh, r_c = 2h, dt = 2.5e-13 s) against the oracle's gradient of the final
+    rms emittance, FP64."""
+    spec = dict(B.WORKLOADS["gauss1m_grad"])
+    x0 = B.positions(spec, 4096)
+    p0 = B.momenta(spec, 4096)
+    P = O.auto_mesh(x0 * 1.05, 64, rc_over_h=2.0)
+    kern = O.green_kernels(P)
+    dt, T = 2.5e-13, 200
+    xT, pT, _ = O.push(x0, p0, dt, T, P, force=lambda y: O.forces(y, P, kernels=kern).F)
+    gxT, gpT = O.emittance_grad(xT, pT, P)
+    ogx, ogp = O.backward(x0, p0, dt, T, gxT, gpT, P, kern)
+    ctx = p3m().Context(gpu_params(P, 0, adj_slots=10, adj_segment=20), len(x0))
+    gx0, gp0 = ctx.backward(cuda(x0), cuda(p0), dt, T, cuda(gxT), cuda(gpT))
+    ctx.sync()
+    assert rel(gx0, ogx) <= 1e-9
+    assert rel(gp0, ogp) <= 1e-9
