@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 10)
   }
   Acc2 sum[4];
   for (int k = 0; k < 4; ++k) sum[k].hi = sum[k].lo = 0.f;
-  unsigned long long np = 0;
+  unsigned int np = 0;
   const int cy = min(max(static_cast<int>(floorf(pi.y * static_cast<float>(g.inv_cw[1]))), 0),
                      g.nc[1] - 1);
   const int cz = min(max(static_cast<int>(floorf(pi.z * static_cast<float>(g.inv_cw[2]))), 0),
@@ -320,26 +320,38 @@ __global__ void __launch_bounds__(kThreads, 10)
     int maxlen = len;
     for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
     float part[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int t = 0; t < maxlen; ++t) {
-      const bool in = t < len;
-      const uint32_t j = in ? j0 + t : i;  // an idle lane re-reads itself: separation 0, no pair
-      const float4 hj = rec[2 * j], lj = rec[2 * j + 1];
-      const float rx = (pi.x - hj.x) + (li.x - lj.x);
-      const float ry = (pi.y - hj.y) + (li.y - lj.y);
-      const float rz = (pi.z - hj.z) + (li.z - lj.z);
+    const float4* base = rec + 2 * static_cast<size_t>(j0);
+    const float4* self = rec + 2 * static_cast<size_t>(i);
+    auto test = [&](const float4* pj, float& rx, float& ry, float& rz) {
+      const float4 hj = pj[0], lj = pj[1];
+      rx = (pi.x - hj.x) + (li.x - lj.x);
+      ry = (pi.y - hj.y) + (li.y - lj.y);
+      rz = (pi.z - hj.z) + (li.z - lj.z);
       const float r2 = rx * rx + ry * ry + rz * rz;
-      const bool hit = r2 < 1.f && r2 > 0.f;  // the self pair has r2 == 0 exactly
-      if (__any_sync(0xffffffffu, hit)) {
-        float fco, pot;
-        pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
-        fco = hit ? fco : 0.f;
-        pot = hit ? pot : 0.f;
-        part[0] = fmaf(fco, rx, part[0]);
-        part[1] = fmaf(fco, ry, part[1]);
-        part[2] = fmaf(fco, rz, part[2]);
-        part[3] += pot;
-        np += hit;
-      }
+      return r2;
+    };
+    auto accumulate = [&](bool hit, float r2, float rx, float ry, float rz) {
+      float fco, pot;
+      pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
+      fco = hit ? fco : 0.f;
+      pot = hit ? pot : 0.f;
+      part[0] = fmaf(fco, rx, part[0]);
+      part[1] = fmaf(fco, ry, part[1]);
+      part[2] = fmaf(fco, rz, part[2]);
+      part[3] += pot;
+      np += hit;
+    };
+    // two candidates per step; a lane past its run re-reads itself (separation 0, no pair)
+    for (int t = 0; t < maxlen; t += 2) {
+      const float4* pa = t < len ? base + 2 * t : self;
+      const float4* pb = t + 1 < len ? base + 2 * (t + 1) : self;
+      float ax, ay, az, bx, by, bz;
+      const float ra = test(pa, ax, ay, az);
+      const float rb = test(pb, bx, by, bz);
+      const bool ha = ra < 1.f && ra > 0.f;  // the self pair has r2 == 0 exactly
+      const bool hb = rb < 1.f && rb > 0.f;
+      if (__any_sync(0xffffffffu, ha)) accumulate(ha, ra, ax, ay, az);
+      if (__any_sync(0xffffffffu, hb)) accumulate(hb, rb, bx, by, bz);
     }
     for (int k = 0; k < 4; ++k) sum[k].add(part[k]);
   }
