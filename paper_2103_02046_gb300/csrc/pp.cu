@@ -53,20 +53,6 @@ __device__ __forceinline__ void pair_terms(double r2, double kappa, double c2k, 
   fco = (pot + c2k * ex) / r2;
 }
 
-template <typename T>
-struct SumT;
-template <>
-struct SumT<double> {
-  double v[4];
-  __device__ void zero() {
-    for (int k = 0; k < 4; ++k) v[k] = 0.0;
-  }
-  __device__ void fold(const double r[4]) {
-    for (int k = 0; k < 4; ++k) v[k] += r[k];
-  }
-  __device__ double get(int k) const { return v[k]; }
-};
-
 __device__ __forceinline__ void block_reduce_add(double v, double* dst) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __shared__ double ws[kThreads / 32];
@@ -127,121 +113,6 @@ struct PosD {
   const Rec64* __restrict__ r;
 };
 
-// Short-range forces: one thread per sorted particle.
-template <typename T, typename Pos>
-__global__ void __launch_bounds__(kThreads)
-    k_pp(Geom g, const uint32_t* __restrict__ total, Pos pos, const uint32_t* __restrict__ starts,
-         void* __restrict__ fpp, double* __restrict__ energy,
-         unsigned long long* __restrict__ pairs) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t N = *total;
-  const T kappa = static_cast<T>(g.kappa_eff);
-  const T c2k = static_cast<T>(2.0 * g.kappa_eff * 0.56418958354775628695);
-  double pot_out = 0.0;
-  unsigned long long np = 0, ni = 0;
-  if (i < N) {
-    T pi[3], li[3] = {T(0), T(0), T(0)};
-    if constexpr (sizeof(T) == 4) {
-      const float4 h = pos.r[2 * i], l = pos.r[2 * i + 1];
-      pi[0] = h.x; pi[1] = h.y; pi[2] = h.z;
-      li[0] = l.x; li[1] = l.y; li[2] = l.z;
-    } else {
-      const Rec64 r = pos.r[i];
-      pi[0] = r.u[0]; pi[1] = r.u[1]; pi[2] = r.u[2];
-    }
-    SumT<T> sum;
-    sum.zero();
-    for_rows<T>(g, starts, pi[0], pi[1], pi[2], [&](uint32_t j0, uint32_t j1) {
-      T row[4] = {T(0), T(0), T(0), T(0)};
-      for (uint32_t j = j0; j < j1; ++j) {
-        if (j == i) continue;
-        T rx, ry, rz, r2;
-        if constexpr (sizeof(T) == 4) {
-          const float4 hj = pos.r[2 * j];
-          rx = pi[0] - hj.x;
-          ry = pi[1] - hj.y;
-          rz = pi[2] - hj.z;
-          r2 = rx * rx + ry * ry + rz * rz;
-          if (!(r2 < T(1) + T(kFilterSlack))) continue;
-          const float4 lj = pos.r[2 * j + 1];
-          rx += li[0] - lj.x;
-          ry += li[1] - lj.y;
-          rz += li[2] - lj.z;
-          r2 = rx * rx + ry * ry + rz * rz;
-        } else {
-          const Rec64 rj = pos.r[j];
-          rx = pi[0] - rj.u[0];
-          ry = pi[1] - rj.u[1];
-          rz = pi[2] - rj.u[2];
-          r2 = rx * rx + ry * ry + rz * rz;
-        }
-        if (r2 < T(1) && r2 > T(0)) {
-          T fco, pot;
-          pair_terms(r2, kappa, c2k, fco, pot);
-          row[0] += fco * rx;
-          row[1] += fco * ry;
-          row[2] += fco * rz;
-          row[3] += pot;
-          ++np;
-        }
-      }
-      sum.fold(row);
-    });
-    if (g.pp_bc) {
-      // images of the sources within r_c: the image of z_j is img_c - z_j; only particles less
-      // than r_c above the cathode can meet one
-      const double zi = static_cast<double>(pi[2]) + static_cast<double>(li[2]);
-      if (zi - 0.5 * g.img_c < 1.0) {
-        const T mz = static_cast<T>(g.img_c - zi);  // mirrored query point
-        const float ch = static_cast<float>(g.img_c);
-        const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
-        for_rows<T>(g, starts, pi[0], pi[1], mz, [&](uint32_t j0, uint32_t j1) {
-          T row[4] = {T(0), T(0), T(0), T(0)};
-          for (uint32_t j = j0; j < j1; ++j) {
-            T rx, ry, rz;
-            if constexpr (sizeof(T) == 4) {
-              const float4 hj = pos.r[2 * j], lj = pos.r[2 * j + 1];
-              rx = (pi[0] - hj.x) + (li[0] - lj.x);
-              ry = (pi[1] - hj.y) + (li[1] - lj.y);
-              // z_i - (img_c - z_j) with an exact two-sum of the hi parts
-              const float s = pi[2] + hj.z;
-              const float bp = s - pi[2];
-              const float e = (pi[2] - (s - bp)) + (hj.z - bp);
-              rz = ((s - ch) + e) + ((li[2] + lj.z) - cl);
-            } else {
-              const Rec64 rj = pos.r[j];
-              rx = pi[0] - rj.u[0];
-              ry = pi[1] - rj.u[1];
-              rz = pi[2] + rj.u[2] - static_cast<T>(g.img_c);
-            }
-            const T r2 = rx * rx + ry * ry + rz * rz;
-            if (r2 < T(1) && r2 > T(0)) {
-              T fco, pot;
-              pair_terms(r2, kappa, c2k, fco, pot);
-              row[0] -= fco * rx;
-              row[1] -= fco * ry;
-              row[2] -= fco * rz;
-              row[3] -= pot;
-              ++ni;
-            }
-          }
-          sum.fold(row);
-        });
-      }
-    }
-    if constexpr (sizeof(T) == 4) {
-      reinterpret_cast<float4*>(fpp)[i] =
-          make_float4(sum.get(0), sum.get(1), sum.get(2), sum.get(3));
-    } else {
-      reinterpret_cast<D4*>(fpp)[i] = D4{sum.get(0), sum.get(1), sum.get(2), sum.get(3)};
-    }
-    pot_out = static_cast<double>(sum.get(3));
-  }
-  if (energy) block_reduce_add(pot_out, energy);
-  warp_add_u64(np, pairs);
-  warp_add_u64(ni, pairs + 1);
-}
-
 // ------------------------------------------------------------------------------------------
 // FP32 short range, rows in lockstep. Each lane owns one sorted particle i; a warp holds 32
 // consecutive particles of one stretch of an x-row. The warp walks the 25 neighbour rows
@@ -301,11 +172,10 @@ __global__ void __launch_bounds__(kThreads, 10)
   const uint32_t N = *total;
   const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
   const bool alive = i < N;
-  float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), li = pi;
-  if (alive) {
-    pi = rec[2 * i];
-    li = rec[2 * i + 1];
-  }
+  // lanes past the last particle walk nothing; they compare record 0 with itself (in bounds,
+  // separation exactly 0, never a pair) so that every lane can take part in the lockstep loop
+  const uint32_t ie = alive ? i : 0u;
+  const float4 pi = rec[2 * ie], li = rec[2 * ie + 1];
   Acc2 sum[4];
   for (int k = 0; k < 4; ++k) sum[k].hi = sum[k].lo = 0.f;
   unsigned int np = 0;
@@ -321,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 10)
     for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
     float part[4] = {0.f, 0.f, 0.f, 0.f};
     const float4* base = rec + 2 * static_cast<size_t>(j0);
-    const float4* self = rec + 2 * static_cast<size_t>(i);
+    const float4* self = rec + 2 * static_cast<size_t>(ie);
     auto test = [&](const float4* pj, float& rx, float& ry, float& rz) {
       const float4 hj = pj[0], lj = pj[1];
       rx = (pi.x - hj.x) + (li.x - lj.x);
@@ -390,6 +260,116 @@ __global__ void __launch_bounds__(kThreads, 10)
   }
   if (alive) fpp[i] = make_float4(sum[0].value(), sum[1].value(), sum[2].value(), sum[3].value());
   if (energy) block_reduce_add(alive ? static_cast<double>(sum[3].value()) : 0.0, energy);
+  warp_add_u64(np, pairs);
+  warp_add_u64(ni, pairs + 1);
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 short range: the same lockstep walk over the 5 x 5 neighbour rows. The FP64 pair function
+// (erfc, exp, division) costs far more than finding a pair on this part, so pairs found wait in
+// a per-lane ring in shared memory and are evaluated, a batch of one per lane, whenever some
+// lane's ring is full: the pair function then runs with most lanes busy.
+// ------------------------------------------------------------------------------------------
+constexpr int kRing64 = 4;
+
+__device__ __forceinline__ void row_range64(const Geom& g, const uint32_t* __restrict__ starts,
+                                            double px, double py, double pz, int cy, int cz,
+                                            int r, uint32_t& j0, uint32_t& j1) {
+  j0 = j1 = 0;
+  const int ry = cy + (r % kRowSpan) - kRowReach, rz = cz + (r / kRowSpan) - kRowReach;
+  if (ry < 0 || ry >= g.nc[1] || rz < 0 || rz >= g.nc[2]) return;
+  const double slack = kFilterSlack;
+  const double yl = ry * g.cw[1], yh = yl + g.cw[1], zl = rz * g.cw[2], zh = zl + g.cw[2];
+  const double dy = py < yl ? yl - py : (py > yh ? py - yh : 0.0);
+  const double dz = pz < zl ? zl - pz : (pz > zh ? pz - zh : 0.0);
+  const double d2 = dy * dy + dz * dz;
+  if (d2 >= 1.0 + slack) return;
+  const double w = sqrt(fmax(1.0 - d2, 0.0)) + slack;
+  const int c0 = max(static_cast<int>(floor((px - w) * g.inv_cw[0])), 0);
+  const int c1 = min(static_cast<int>(floor((px + w) * g.inv_cw[0])), g.nc[0] - 1);
+  if (c0 > c1) return;
+  const uint32_t base = (static_cast<uint32_t>(rz) * g.nc[1] + ry) * g.nc[0];
+  j0 = starts[base + c0];
+  j1 = starts[base + c1 + 1];
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_pp_f64(Geom g, const uint32_t* __restrict__ total, const Rec64* __restrict__ rec,
+             const uint32_t* __restrict__ starts, D4* __restrict__ fpp,
+             double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
+  __shared__ D4 ring_s[kThreads / 32][kRing64][32];
+  D4(*ring)[32] = ring_s[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const uint32_t N = *total;
+  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  const bool alive = i < N;
+  const double kappa = g.kappa_eff;
+  const double c2k = 2.0 * g.kappa_eff * 0.56418958354775628695;
+  const uint32_t ie = alive ? i : 0u;  // see k_pp_f32: idle lanes compare record 0 with itself
+  const Rec64 me = rec[ie];
+  const double px = me.u[0], py = me.u[1], pz = me.u[2];
+  const int cy = min(max(static_cast<int>(floor(py * g.inv_cw[1])), 0), g.nc[1] - 1);
+  const int cz = min(max(static_cast<int>(floor(pz * g.inv_cw[2])), 0), g.nc[2] - 1);
+  double sum[4] = {0.0, 0.0, 0.0, 0.0};
+  unsigned int np = 0;
+  int head = 0, cnt = 0;
+  auto evaluate = [&]() {
+    const bool has = cnt > 0;
+    D4 e = ring[head & (kRing64 - 1)][lane];
+    if (!has) e = D4{0.0, 0.0, 0.0, 0.5};
+    double fco, pot;
+    pair_terms(e.w, kappa, c2k, fco, pot);
+    if (has) {
+      sum[0] += fco * e.x;
+      sum[1] += fco * e.y;
+      sum[2] += fco * e.z;
+      sum[3] += pot;
+    }
+    head += has;
+    cnt -= has;
+  };
+  for (int r = 0; r < kRowSpan * kRowSpan; ++r) {
+    uint32_t j0 = 0, j1 = 0;
+    if (alive) row_range64(g, starts, px, py, pz, cy, cz, r, j0, j1);
+    const int len = static_cast<int>(j1 - j0);
+    int maxlen = len;
+    for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
+    for (int t = 0; t < maxlen; ++t) {
+      const uint32_t j = t < len ? j0 + t : ie;  // an idle lane re-reads itself: no pair
+      const Rec64 rj = rec[j];
+      const double rx = px - rj.u[0], ry = py - rj.u[1], rz = pz - rj.u[2];
+      const double r2 = rx * rx + ry * ry + rz * rz;
+      if (alive && r2 < 1.0 && r2 > 0.0) {
+        ring[(head + cnt) & (kRing64 - 1)][lane] = D4{rx, ry, rz, r2};
+        ++cnt;
+        ++np;
+      }
+      if (__any_sync(0xffffffffu, cnt == kRing64)) evaluate();
+    }
+  }
+  while (__any_sync(0xffffffffu, cnt > 0)) evaluate();
+  unsigned long long ni = 0;
+  if (alive && g.pp_bc && pz - 0.5 * g.img_c < 1.0) {
+    // images within r_c of particles less than r_c above the cathode (rare): plain loop
+    for_rows<double>(g, starts, px, py, g.img_c - pz, [&](uint32_t ja, uint32_t jb) {
+      for (uint32_t jj = ja; jj < jb; ++jj) {
+        const Rec64 rj = rec[jj];
+        const double ax = px - rj.u[0], ay = py - rj.u[1], az = pz + rj.u[2] - g.img_c;
+        const double r2 = ax * ax + ay * ay + az * az;
+        if (r2 < 1.0 && r2 > 0.0) {
+          double fco, pot;
+          pair_terms(r2, kappa, c2k, fco, pot);
+          sum[0] -= fco * ax;
+          sum[1] -= fco * ay;
+          sum[2] -= fco * az;
+          sum[3] -= pot;
+          ++ni;
+        }
+      }
+    });
+  }
+  if (alive) fpp[i] = D4{sum[0], sum[1], sum[2], sum[3]};
+  if (energy) block_reduce_add(alive ? sum[3] : 0.0, energy);
   warp_add_u64(np, pairs);
   warp_add_u64(ni, pairs + 1);
 }
@@ -538,10 +518,10 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
       case 14: run(k_pp_f32<14>); break;
       default: run(k_pp_f32<15>); break;
     }
-  } else
-    k_pp<double, PosD><<<blocks, kThreads, 0, s>>>(
-        c->g, total, PosD{static_cast<const Rec64*>(c->recp)}, c->starts, c->fpp, c->energy_acc,
-        c->pair_acc);
+  } else {
+    k_pp_f64<<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const Rec64*>(c->recp), c->starts,
+                                         static_cast<D4*>(c->fpp), c->energy_acc, c->pair_acc);
+  }
 }
 
 void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s) {
