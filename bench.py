@@ -36,6 +36,12 @@ from paper_2103_02046_gb300 import bunches as B  # noqa: E402
 METRIC = "P3M force evals/s and PP pair-interactions/s at N=16M, FP32 vs FP64 at stated error"
 FLOPS_PER_PAIR = 37.0  # algorithmic FP32 flops per in-cutoff pair (FFMA = 2, incl. 3 MUFU)
 KERNELS_PER_EVAL = 9   # bin, 3 scan passes, scatter, short range, deposit, Green multiply, interp
+# DRAM bytes (read + write) of one k_pp_f32<12> launch per particle, from an ncu capture of the
+# 2,097,152-particle sphere on a 128^3 mesh (93.08 MB per launch, profiles/k_pp_f32_sphere2m_128.md).
+# The kernel reads each 32-B record about once from DRAM (neighbour runs hit L2; 77 MB read for
+# 67 MB of records) and writes 16 B per particle, part of which is still in L2 when it ends, so
+# its traffic scales with the particle count at fixed density.
+PP_DRAM_BYTES_PER_PARTICLE = 93.076224e6 / 2097152
 
 
 def parse():
@@ -292,7 +298,10 @@ def run_ours(a, rank, world, local_rank):
         "error": {"fp32_vs_fp64_gpu_rel_l2": err32},
         "roofline": {"bound": "alu", "kernel": "short range (k_pp<float>)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": None,
+                     "traffic": PP_DRAM_BYTES_PER_PARTICLE * N,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                                       "k_pp_f32 on the 2,097,152-particle sphere (128^3), "
+                                       "scaled by particle count",
                      "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                                     f"{sm_mhz_max:.0f} MHz (max SM clock)",
                      "flops_per_pair": FLOPS_PER_PAIR},

@@ -195,11 +195,12 @@ __global__ void __launch_bounds__(kDepThreads)
                     const typename RecT<T>::type* __restrict__ recm,
                     const typename RecT<T>::type* __restrict__ recp,
                     const double* __restrict__ w, T* __restrict__ qpad) {
-  // FP32 charge deposit: the tile accumulates in unsigned 32-bit fixed point (2^-23 per unit of
-  // weight; a tile node receives at most one weight <= 27/64 from each of 1024 particles, so the
-  // sum stays below 2^32),
-  // because integer shared-memory atomics are native while float ones are compare-and-swap
-  // loops. Sums inside a tile are then exact and independent of the order of the particles.
+  // FP32 charge deposit: the tile accumulates in unsigned 32-bit fixed point, because integer
+  // shared-memory atomics are native while float ones are compare-and-swap loops. A tile node
+  // receives at most one weight from each of the block's 1024 particles: at most 27/64 with TSC
+  // (2^23 per unit of weight keeps the sum below 1024 * 27/64 * 2^23 < 2^32) and at most 1 with
+  // CIC (2^21 per unit: below 2^31). Sums inside a tile are then exact and independent of the
+  // order of the particles.
   constexpr bool kFixed = (sizeof(T) == 4) && !kDipole;
   using Slot = typename std::conditional<kFixed, unsigned int, T>::type;
   constexpr int kTile = kTileBytes / sizeof(Slot);
@@ -209,6 +210,8 @@ __global__ void __launch_bounds__(kDepThreads)
   const uint32_t b0 = blockIdx.x * kDepPerBlock;
   if (b0 >= N) return;
   const int S = g.order == 2 ? 3 : 2;
+  const float fix_scale = g.order == 2 ? 8388608.0f : 2097152.0f;
+  const float fix_inv = 1.0f / fix_scale;
   if (threadIdx.x < 3) {
     bmin[threadIdx.x] = 1 << 30;
     bmax[threadIdx.x] = -1;
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(kDepThreads)
           if (use_tile) {
             Slot* slot = &tile[((gz - bmin[2]) * ey + (gy - bmin[1])) * ex + (gx - bmin[0])];
             if constexpr (kFixed)
-              atomicAdd(slot, __float2uint_rn(static_cast<float>(v) * 8388608.0f));
+              atomicAdd(slot, __float2uint_rn(static_cast<float>(v) * fix_scale));
             else
               atomicAdd(slot, v);
           } else
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(kDepThreads)
   for (int t = threadIdx.x; t < ex * ey * ez; t += kDepThreads) {
     T v;
     if constexpr (kFixed)
-      v = static_cast<T>(static_cast<float>(tile[t]) * (1.0f / 8388608.0f));
+      v = static_cast<T>(static_cast<float>(tile[t]) * fix_inv);
     else
       v = tile[t];
     if (v != T(0)) {

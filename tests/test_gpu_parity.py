@@ -104,6 +104,27 @@ def test_mesh_charge_and_potential(precision):
     assert float(Qg.sum()) == pytest.approx(len(x) * P.q, rel=1e-12 if precision == 0 else 1e-6)
 
 
+@pytest.mark.parametrize("order", [1, 2])
+def test_deposit_dense_clump(order):
+    # 3072 coincident particles on one mesh node: a deposit block (1024 particles) puts its
+    # largest possible weight (1 for CIC, 27/64 for TSC) on one node, the edge of the FP32
+    # fixed-point tile's range
+    base = bunch_4k(False)
+    P = O.auto_mesh(base, 16, assign_order=order)
+    node = np.array([P.lo[d] + 8 * P.h[d] for d in range(3)])
+    x = np.concatenate([base, np.repeat(node[None, :], 3072, axis=0)])
+    Q, _ = O.deposit(x, P)
+    for precision in (0, 1):
+        ctx = p3m().Context(gpu_params(P, precision), len(x))
+        ctx.deposit(cuda(x))
+        Qg = ctx.get_mesh(0)
+        ctx.sync()
+        ctx.close()
+        assert rel(Qg, Q) <= (1e-14 if precision == 0 else 1e-6)
+        assert float(Qg.max()) == pytest.approx(float(Q.max()),
+                                                rel=1e-13 if precision == 0 else 1e-6)
+
+
 def test_auto_mesh_matches_oracle():
     m = p3m()
     x = B.gaussian(5000, (1e-3, 2e-3, 3e-3), 21)
