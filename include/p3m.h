@@ -57,7 +57,7 @@ typedef struct p3m_params {
   int32_t n[3];          /* mesh nodes per axis, x, y, z (each in [8, 1024]) */
   double lo[3];          /* position of node 0 [m]; node g sits at lo + g*h (Sec. 2.4.2) */
   double h[3];           /* mesh spacing per axis [m] */
-  double rc_over_h;      /* short-range cutoff r_c = rc_over_h * max_d h_d */
+  double rc_over_h;      /* short-range cutoff r_c = rc_over_h * max_d h_d; >= 0.25 */
   double kappa;          /* Ewald parameter a = kappa / r_c (eq. (ewald_split)) unless alpha > 0 */
   double alpha;          /* explicit Ewald parameter [1/m]; <= 0 selects kappa / r_c */
   int32_t assign_order;  /* 1 = cloud-in-cell (eq. (interpolation_splines_b0)), 2 = TSC */

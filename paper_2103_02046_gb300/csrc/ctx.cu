@@ -45,7 +45,7 @@ p3m_status validate(const p3m_params* p, std::string* why) {
     if (!finite_pos(p->h[d])) { *why = "mesh spacing h must be finite and > 0"; return P3M_EINVAL; }
     if (!std::isfinite(p->lo[d])) { *why = "mesh origin lo must be finite"; return P3M_EINVAL; }
   }
-  if (!finite_pos(p->rc_over_h)) { *why = "rc_over_h must be > 0"; return P3M_EINVAL; }
+  if (!(p->rc_over_h >= 0.25) || !std::isfinite(p->rc_over_h)) { *why = "rc_over_h must be >= 0.25"; return P3M_EINVAL; }
   if (!(p->alpha > 0.0) && !finite_pos(p->kappa)) { *why = "kappa must be > 0 (or alpha > 0)"; return P3M_EINVAL; }
   if (p->assign_order != 1 && p->assign_order != 2) { *why = "assign_order must be 1 or 2"; return P3M_EINVAL; }
   if ((p->pm_bc != 0 && p->pm_bc != 1) || (p->pp_bc != 0 && p->pp_bc != 1)) { *why = "pm_bc/pp_bc must be 0 or 1"; return P3M_EINVAL; }
@@ -72,19 +72,24 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   g.rc = p->rc_over_h * hmax;
   g.alpha = p->alpha > 0.0 ? p->alpha : p->kappa / g.rc;
   g.kappa_eff = g.alpha * g.rc;
-  // cells: y and z edges a hair above r_c / 2 (so a pair closer than r_c is never more than two
-  // cells apart after rounding); x edges r_c / nsub, nsub = 4 unless that makes too many cells
-  const double edge = 1.0 + 1e-9;
+  // cells: y and z edges r_c (1 + 4 slack) / 2, x edges r_c / nsub (nsub = 4 unless that makes
+  // too many cells). A particle's row is computed in FP32 and may be off by one within rounding
+  // (< slack / 3) of a row boundary; with rows this wide, two particles closer than r_c still
+  // sit at most two rows apart, so the 5 x 5 row block around a particle's row holds all of its
+  // neighbours.
   double ext[3];
+  double ext_max = 0.0;
   for (int d = 0; d < 3; ++d) {
     g.a[d] = g.h[d] / g.rc;
     ext[d] = (g.n[d] - 1) * g.a[d];
+    ext_max = std::max(ext_max, ext[d]);
   }
+  g.slack = std::max(1e-4, 1e-6 * ext_max);
   int nsub = 4;
   const double cap = std::max<double>(4.0 * static_cast<double>(n_max), 1 << 20);
   for (;;) {
-    g.cw[0] = edge / nsub;
-    g.cw[1] = g.cw[2] = edge / kRowsPerCutoff;
+    g.cw[0] = (1.0 + 1e-9) / nsub;
+    g.cw[1] = g.cw[2] = (1.0 + 4.0 * g.slack) / kRowsPerCutoff;
     double cells = 1.0;
     for (int d = 0; d < 3; ++d) {
       g.inv_cw[d] = 1.0 / g.cw[d];

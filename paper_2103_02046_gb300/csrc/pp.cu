@@ -26,7 +26,6 @@ namespace p3m {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr float kFilterSlack = 1e-4f;   // hi-only separations err by < 1e-5 r_c
 constexpr int kRowReach = kRowsPerCutoff;          // neighbour rows on each side (y and z)
 constexpr int kRowSpan = 2 * kRowReach + 1;
 
@@ -72,12 +71,13 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long v, unsigned long
 
 // Calls visit(j0, j1) for every neighbour row of the query point (px, py, pz) (cutoff units)
 // that can hold particles within distance 1, with [j0, j1) the sorted range of its cells whose
-// x-extent meets (px - w, px + w), w = sqrt(1 - d^2) (+ slack), d the point's distance to the
-// row's (y, z) rectangle.
+// x-extent meets (px - w, px + w), w = sqrt(1 - d^2) + slack, d the point's distance to the
+// row's (y, z) rectangle less the slack. The slack (Geom::slack) exceeds every rounding in where
+// the sort placed a particle, so no particle within distance 1 is left out.
 template <typename T, typename V>
 __device__ __forceinline__ void for_rows(const Geom& g, const uint32_t* __restrict__ starts, T px,
                                          T py, T pz, V&& visit) {
-  const T slack = T(kFilterSlack);
+  const T slack = static_cast<T>(g.slack);
   const T cwy = static_cast<T>(g.cw[1]), cwz = static_cast<T>(g.cw[2]);
   const T iwx = static_cast<T>(g.inv_cw[0]), iwy = static_cast<T>(g.inv_cw[1]),
           iwz = static_cast<T>(g.inv_cw[2]);
@@ -87,13 +87,13 @@ __device__ __forceinline__ void for_rows(const Geom& g, const uint32_t* __restri
   const int z1 = min(static_cast<int>(floor((pz + T(1) + slack) * iwz)), g.nc[2] - 1);
   for (int rz = z0; rz <= z1; ++rz) {
     const T zl = static_cast<T>(rz) * cwz, zh = zl + cwz;
-    const T dz = pz < zl ? zl - pz : (pz > zh ? pz - zh : T(0));
+    const T dz = max((pz < zl ? zl - pz : (pz > zh ? pz - zh : T(0))) - slack, T(0));
     for (int ry = y0; ry <= y1; ++ry) {
       const T yl = static_cast<T>(ry) * cwy, yh = yl + cwy;
-      const T dy = py < yl ? yl - py : (py > yh ? py - yh : T(0));
+      const T dy = max((py < yl ? yl - py : (py > yh ? py - yh : T(0))) - slack, T(0));
       const T d2 = dy * dy + dz * dz;
-      if (d2 >= T(1) + slack) continue;
-      const T w = sqrt(max(T(1) - d2, T(0))) + slack;
+      if (d2 >= T(1)) continue;
+      const T w = sqrt(T(1) - d2) + slack;
       const int c0 = max(static_cast<int>(floor((px - w) * iwx)), 0);
       const int c1 = min(static_cast<int>(floor((px + w) * iwx)), g.nc[0] - 1);
       if (c0 > c1) continue;
@@ -114,19 +114,36 @@ struct PosD {
 };
 
 // ------------------------------------------------------------------------------------------
-// FP32 short range, rows in lockstep. Each lane owns one sorted particle i; a warp holds 32
-// consecutive particles of one stretch of an x-row. The warp walks the 25 neighbour rows
-// together: for row r every lane computes its own pruned candidate run [j0, j1) (so pruning
-// stays per particle), then the warp steps t = 0 .. max_len - 1 and each lane tests j0 + t
-// (a lane past its run re-reads itself, which has separation 0 and is never a pair). Control
-// flow is warp-uniform: the pair function runs, predicated, whenever any lane holds a pair.
-// Lanes of one warp have runs of nearly the same length and start, so few lanes idle and the
-// loads of one step touch a few cache lines. Separations are exact to FP32 relative rounding
-// ((hi_i - hi_j) + (lo_i - lo_j)). Each row's FP32 partial sum is folded into a two-float
-// (TwoSum) accumulator.
+// FP32 short range: each unordered pair once (Newton's third law), lanes walking their own
+// candidate lists in lockstep.
+//
+// Pairs: particle i takes the pairs (i, j) with j > i in sorted order. Sorted order is row-major
+// over (z row, y row, x cell), so these are the later part of i's own row and the 12 neighbour
+// rows after it (dz > 0, or dz = 0 and dy > 0) -- 13 of the 25 rows. i's row is the one the sort
+// put it in (stored with the record), so every pair is taken by exactly one of its particles.
+// The force on i accumulates in registers; the reaction -f goes to j by one vector reduction
+// (red.global.add.v4.f32) into the zeroed result array, and i's own sum is added the same way
+// at the end.
+//
+// Walk: each lane first writes its non-empty candidate runs (at most 13) to shared memory, then
+// the warp steps through them together, two candidates per lane per step; a lane moves on to its
+// next run as soon as one ends, so a warp takes as many steps as its longest lane's total
+// rather than the sum over rows of each row's longest run. Lanes with nothing left re-read their
+// own record (separation 0, never a pair). Control flow is warp-uniform: the pair function runs,
+// predicated, whenever any lane holds a pair. Separations are exact to FP32 relative rounding
+// ((hi_i - hi_j) + (lo_i - lo_j)). FP32 partial sums are folded into a two-float (TwoSum)
+// accumulator every 8 steps.
 // The pair function uses one ex2 for both e^{-kappa^2 rho^2} terms and the fitted polynomial
 // R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}.
 // ------------------------------------------------------------------------------------------
+constexpr int kHalfRows = kRowSpan * kRowSpan / 2 + 1;  // own row + the 12 after it
+
+__device__ __forceinline__ void red_add_v4(float4* dst, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(a), "f"(b),
+               "f"(c), "f"(d)
+               : "memory");
+}
+
 template <int kDeg>
 __device__ __forceinline__ void pair_poly(const PairPoly& P, float r2, float& fco, float& pot) {
   const float rinv = rsqrtf(r2);
@@ -140,20 +157,23 @@ __device__ __forceinline__ void pair_poly(const PairPoly& P, float r2, float& fc
   fco = fmaf(P.c2k, ex, pot) * (rinv * rinv);
 }
 
+// Sorted range [j0, j1) of neighbour row r (0..24, y fastest, 12 = the particle's own row
+// (cy, cz)) that can hold particles within distance 1 of (px, py, pz); empty if none can. The
+// rectangle distance and the x half-width carry the search slack, as in for_rows.
 __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restrict__ starts,
                                           float px, float py, float pz, int cy, int cz, int r,
                                           uint32_t& j0, uint32_t& j1) {
   j0 = j1 = 0;
   const int ry = cy + (r % kRowSpan) - kRowReach, rz = cz + (r / kRowSpan) - kRowReach;
   if (ry < 0 || ry >= g.nc[1] || rz < 0 || rz >= g.nc[2]) return;
-  const float slack = kFilterSlack;
+  const float slack = static_cast<float>(g.slack);
   const float cwy = static_cast<float>(g.cw[1]), cwz = static_cast<float>(g.cw[2]);
   const float yl = ry * cwy, yh = yl + cwy, zl = rz * cwz, zh = zl + cwz;
-  const float dy = py < yl ? yl - py : (py > yh ? py - yh : 0.f);
-  const float dz = pz < zl ? zl - pz : (pz > zh ? pz - zh : 0.f);
+  const float dy = fmaxf((py < yl ? yl - py : (py > yh ? py - yh : 0.f)) - slack, 0.f);
+  const float dz = fmaxf((pz < zl ? zl - pz : (pz > zh ? pz - zh : 0.f)) - slack, 0.f);
   const float d2 = dy * dy + dz * dz;
-  if (d2 >= 1.f + slack) return;
-  const float w = sqrtf(fmaxf(1.f - d2, 0.f)) + slack;
+  if (d2 >= 1.f) return;
+  const float w = sqrtf(1.f - d2) + slack;
   const float iwx = static_cast<float>(g.inv_cw[0]);
   const int c0 = max(static_cast<int>(floorf((px - w) * iwx)), 0);
   const int c1 = min(static_cast<int>(floorf((px + w) * iwx)), g.nc[0] - 1);
@@ -169,65 +189,90 @@ __global__ void __launch_bounds__(kThreads, 10)
              const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
              float4* __restrict__ fpp,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
+  __shared__ uint32_t run_j0[kHalfRows][kThreads], run_j1[kHalfRows][kThreads];
+  const int tid = threadIdx.x;
   const uint32_t N = *total;
-  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  const uint32_t i = blockIdx.x * kThreads + tid;
   const bool alive = i < N;
   // lanes past the last particle walk nothing; they compare record 0 with itself (in bounds,
   // separation exactly 0, never a pair) so that every lane can take part in the lockstep loop
   const uint32_t ie = alive ? i : 0u;
   const float4 pi = rec[2 * ie], li = rec[2 * ie + 1];
-  Acc2 sum[4];
-  for (int k = 0; k < 4; ++k) sum[k].hi = sum[k].lo = 0.f;
-  unsigned int np = 0;
-  const int cy = min(max(static_cast<int>(floorf(pi.y * static_cast<float>(g.inv_cw[1]))), 0),
-                     g.nc[1] - 1);
-  const int cz = min(max(static_cast<int>(floorf(pi.z * static_cast<float>(g.inv_cw[2]))), 0),
-                     g.nc[2] - 1);
-  for (int r = 0; r < kRowSpan * kRowSpan; ++r) {
-    uint32_t j0 = 0, j1 = 0;
-    if (alive) row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
-    const int len = static_cast<int>(j1 - j0);
-    int maxlen = len;
-    for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
-    float part[4] = {0.f, 0.f, 0.f, 0.f};
-    const float4* base = rec + 2 * static_cast<size_t>(j0);
-    const float4* self = rec + 2 * static_cast<size_t>(ie);
-    auto test = [&](const float4* pj, float& rx, float& ry, float& rz) {
-      const float4 hj = pj[0], lj = pj[1];
-      rx = (pi.x - hj.x) + (li.x - lj.x);
-      ry = (pi.y - hj.y) + (li.y - lj.y);
-      rz = (pi.z - hj.z) + (li.z - lj.z);
-      const float r2 = rx * rx + ry * ry + rz * rz;
-      return r2;
-    };
-    auto accumulate = [&](bool hit, float r2, float rx, float ry, float rz) {
-      float fco, pot;
-      pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
-      fco = hit ? fco : 0.f;
-      pot = hit ? pot : 0.f;
-      part[0] = fmaf(fco, rx, part[0]);
-      part[1] = fmaf(fco, ry, part[1]);
-      part[2] = fmaf(fco, rz, part[2]);
-      part[3] += pot;
-      np += hit;
-    };
-    // two candidates per step; a lane past its run re-reads itself (separation 0, no pair)
-    for (int t = 0; t < maxlen; t += 2) {
-      const float4* pa = t < len ? base + 2 * t : self;
-      const float4* pb = t + 1 < len ? base + 2 * (t + 1) : self;
-      float ax, ay, az, bx, by, bz;
-      const float ra = test(pa, ax, ay, az);
-      const float rb = test(pb, bx, by, bz);
-      const bool ha = ra < 1.f && ra > 0.f;  // the self pair has r2 == 0 exactly
-      const bool hb = rb < 1.f && rb > 0.f;
-      if (__any_sync(0xffffffffu, ha)) accumulate(ha, ra, ax, ay, az);
-      if (__any_sync(0xffffffffu, hb)) accumulate(hb, rb, bx, by, bz);
+  const float4* self = rec + 2 * static_cast<size_t>(ie);
+  int cnt = 0;
+  if (alive) {
+    const uint32_t row = __float_as_uint(li.w);
+    const int cy = static_cast<int>(row % static_cast<uint32_t>(g.nc[1]));
+    const int cz = static_cast<int>(row / static_cast<uint32_t>(g.nc[1]));
+    for (int r = kRowSpan * kRowSpan / 2; r < kRowSpan * kRowSpan; ++r) {
+      uint32_t j0, j1;
+      row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
+      j0 = max(j0, i + 1);  // own row: only the particles after i (a no-op for later rows)
+      if (j0 < j1) {
+        run_j0[cnt][tid] = j0;
+        run_j1[cnt][tid] = j1;
+        ++cnt;
+      }
     }
-    for (int k = 0; k < 4; ++k) sum[k].add(part[k]);
   }
+  uint32_t ptr = 0, end = 0;
+  if (cnt > 0) {
+    ptr = run_j0[0][tid];
+    end = run_j1[0][tid];
+  }
+  int k = 0;
+  Acc2 sum[4];
+  for (int c = 0; c < 4; ++c) sum[c].hi = sum[c].lo = 0.f;
+  float part[4] = {0.f, 0.f, 0.f, 0.f};
+  unsigned int np = 0;
+  auto test = [&](const float4* pj, float& rx, float& ry, float& rz) {
+    const float4 hj = pj[0], lj = pj[1];
+    rx = (pi.x - hj.x) + (li.x - lj.x);
+    ry = (pi.y - hj.y) + (li.y - lj.y);
+    rz = (pi.z - hj.z) + (li.z - lj.z);
+    return rx * rx + ry * ry + rz * rz;
+  };
+  auto pair = [&](bool hit, float r2, float rx, float ry, float rz, uint32_t j) {
+    float fco, pot;
+    pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
+    fco = hit ? fco : 0.f;
+    pot = hit ? pot : 0.f;
+    part[0] = fmaf(fco, rx, part[0]);
+    part[1] = fmaf(fco, ry, part[1]);
+    part[2] = fmaf(fco, rz, part[2]);
+    part[3] += pot;
+    np += hit;
+    if (hit) red_add_v4(fpp + j, -fco * rx, -fco * ry, -fco * rz, pot);
+  };
+  int step = 0;
+  while (__any_sync(0xffffffffu, ptr < end)) {
+    const float4* pa = ptr < end ? rec + 2 * static_cast<size_t>(ptr) : self;
+    const float4* pb = ptr + 1 < end ? rec + 2 * static_cast<size_t>(ptr + 1) : self;
+    float ax, ay, az, bx, by, bz;
+    const float ra = test(pa, ax, ay, az);
+    const float rb = test(pb, bx, by, bz);
+    const bool ha = ra < 1.f && ra > 0.f;  // the self pair has r2 == 0 exactly
+    const bool hb = rb < 1.f && rb > 0.f;
+    if (__any_sync(0xffffffffu, ha)) pair(ha, ra, ax, ay, az, ptr);
+    if (__any_sync(0xffffffffu, hb)) pair(hb, rb, bx, by, bz, ptr + 1);
+    ptr += 2;
+    if (ptr >= end && ++k < cnt) {
+      ptr = run_j0[k][tid];
+      end = run_j1[k][tid];
+    }
+    if ((++step & 7) == 0) {
+      for (int c = 0; c < 4; ++c) {
+        sum[c].add(part[c]);
+        part[c] = 0.f;
+      }
+    }
+  }
+  for (int c = 0; c < 4; ++c) sum[c].add(part[c]);
+  const float pair_pot = sum[3].value();
   unsigned long long ni = 0;
   if (alive && g.pp_bc) {
-    // images within r_c of particles less than r_c above the cathode (rare): plain loop
+    // images within r_c of particles less than r_c above the cathode (rare): plain loop over
+    // all 25 rows around the image point; image pairs act on i only
     const double zi = static_cast<double>(pi.z) + static_cast<double>(li.z);
     if (zi - 0.5 * g.img_c < 1.0) {
       const float mz = static_cast<float>(g.img_c - zi);
@@ -254,21 +299,26 @@ __global__ void __launch_bounds__(kThreads, 10)
             ++ni;
           }
         }
-        for (int k = 0; k < 4; ++k) sum[k].add(rowv[k]);
+        for (int c = 0; c < 4; ++c) sum[c].add(rowv[c]);
       });
     }
   }
-  if (alive) fpp[i] = make_float4(sum[0].value(), sum[1].value(), sum[2].value(), sum[3].value());
-  if (energy) block_reduce_add(alive ? static_cast<double>(sum[3].value()) : 0.0, energy);
-  warp_add_u64(np, pairs);
+  if (alive) red_add_v4(fpp + i, sum[0].value(), sum[1].value(), sum[2].value(), sum[3].value());
+  // sum_i phi_i over ordered pairs: each pair's potential was taken once here, plus the images
+  if (energy)
+    block_reduce_add(alive ? static_cast<double>(sum[3].value()) + pair_pot : 0.0, energy);
+  warp_add_u64(2ull * np, pairs);
   warp_add_u64(ni, pairs + 1);
 }
 
 // ------------------------------------------------------------------------------------------
-// FP64 short range: the same lockstep walk over the 5 x 5 neighbour rows. The FP64 pair function
-// (erfc, exp, division) costs far more than finding a pair on this part, so pairs found wait in
-// a per-lane ring in shared memory and are evaluated, a batch of one per lane, whenever some
-// lane's ring is full: the pair function then runs with most lanes busy.
+// FP64 short range: each unordered pair once, as in the FP32 kernel: particle i takes the pairs
+// with j > i in sorted order (every one of the 25 neighbour rows is clipped to j > i, so this
+// holds however the row of i was rounded) and adds the reaction to j with FP64 reductions into
+// the zeroed result. Rows are walked in lockstep. The FP64 pair function (erfc, exp, division)
+// costs far more than finding a pair on this part, so pairs found wait in a per-lane ring in
+// shared memory and are evaluated, a batch of one per lane, whenever some lane's ring is full:
+// the pair function then runs with most lanes busy.
 // ------------------------------------------------------------------------------------------
 constexpr int kRing64 = 4;
 
@@ -278,13 +328,13 @@ __device__ __forceinline__ void row_range64(const Geom& g, const uint32_t* __res
   j0 = j1 = 0;
   const int ry = cy + (r % kRowSpan) - kRowReach, rz = cz + (r / kRowSpan) - kRowReach;
   if (ry < 0 || ry >= g.nc[1] || rz < 0 || rz >= g.nc[2]) return;
-  const double slack = kFilterSlack;
+  const double slack = g.slack;
   const double yl = ry * g.cw[1], yh = yl + g.cw[1], zl = rz * g.cw[2], zh = zl + g.cw[2];
-  const double dy = py < yl ? yl - py : (py > yh ? py - yh : 0.0);
-  const double dz = pz < zl ? zl - pz : (pz > zh ? pz - zh : 0.0);
+  const double dy = fmax((py < yl ? yl - py : (py > yh ? py - yh : 0.0)) - slack, 0.0);
+  const double dz = fmax((pz < zl ? zl - pz : (pz > zh ? pz - zh : 0.0)) - slack, 0.0);
   const double d2 = dy * dy + dz * dz;
-  if (d2 >= 1.0 + slack) return;
-  const double w = sqrt(fmax(1.0 - d2, 0.0)) + slack;
+  if (d2 >= 1.0) return;
+  const double w = sqrt(1.0 - d2) + slack;
   const int c0 = max(static_cast<int>(floor((px - w) * g.inv_cw[0])), 0);
   const int c1 = min(static_cast<int>(floor((px + w) * g.inv_cw[0])), g.nc[0] - 1);
   if (c0 > c1) return;
@@ -298,7 +348,9 @@ __global__ void __launch_bounds__(kThreads)
              const uint32_t* __restrict__ starts, D4* __restrict__ fpp,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
   __shared__ D4 ring_s[kThreads / 32][kRing64][32];
+  __shared__ uint32_t ringj_s[kThreads / 32][kRing64][32];
   D4(*ring)[32] = ring_s[threadIdx.x >> 5];
+  uint32_t(*ringj)[32] = ringj_s[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const uint32_t N = *total;
   const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
@@ -316,21 +368,32 @@ __global__ void __launch_bounds__(kThreads)
   auto evaluate = [&]() {
     const bool has = cnt > 0;
     D4 e = ring[head & (kRing64 - 1)][lane];
+    const uint32_t j = ringj[head & (kRing64 - 1)][lane];
     if (!has) e = D4{0.0, 0.0, 0.0, 0.5};
     double fco, pot;
     pair_terms(e.w, kappa, c2k, fco, pot);
     if (has) {
-      sum[0] += fco * e.x;
-      sum[1] += fco * e.y;
-      sum[2] += fco * e.z;
+      const double fx = fco * e.x, fy = fco * e.y, fz = fco * e.z;
+      sum[0] += fx;
+      sum[1] += fy;
+      sum[2] += fz;
       sum[3] += pot;
+      double* fj = &fpp[j].x;
+      atomicAdd(fj, -fx);
+      atomicAdd(fj + 1, -fy);
+      atomicAdd(fj + 2, -fz);
+      atomicAdd(fj + 3, pot);
     }
     head += has;
     cnt -= has;
   };
   for (int r = 0; r < kRowSpan * kRowSpan; ++r) {
     uint32_t j0 = 0, j1 = 0;
-    if (alive) row_range64(g, starts, px, py, pz, cy, cz, r, j0, j1);
+    if (alive) {
+      row_range64(g, starts, px, py, pz, cy, cz, r, j0, j1);
+      j0 = max(j0, i + 1);
+      j1 = max(j1, j0);
+    }
     const int len = static_cast<int>(j1 - j0);
     int maxlen = len;
     for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
@@ -341,6 +404,7 @@ __global__ void __launch_bounds__(kThreads)
       const double r2 = rx * rx + ry * ry + rz * rz;
       if (alive && r2 < 1.0 && r2 > 0.0) {
         ring[(head + cnt) & (kRing64 - 1)][lane] = D4{rx, ry, rz, r2};
+        ringj[(head + cnt) & (kRing64 - 1)][lane] = j;
         ++cnt;
         ++np;
       }
@@ -348,6 +412,7 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   while (__any_sync(0xffffffffu, cnt > 0)) evaluate();
+  const double pair_pot = sum[3];
   unsigned long long ni = 0;
   if (alive && g.pp_bc && pz - 0.5 * g.img_c < 1.0) {
     // images within r_c of particles less than r_c above the cathode (rare): plain loop
@@ -368,9 +433,13 @@ __global__ void __launch_bounds__(kThreads)
       }
     });
   }
-  if (alive) fpp[i] = D4{sum[0], sum[1], sum[2], sum[3]};
-  if (energy) block_reduce_add(alive ? sum[3] : 0.0, energy);
-  warp_add_u64(np, pairs);
+  if (alive) {
+    double* fi = &fpp[i].x;
+    for (int c = 0; c < 4; ++c) atomicAdd(fi + c, sum[c]);
+  }
+  // sum_i phi_i over ordered pairs: each pair's potential was taken once here, plus the images
+  if (energy) block_reduce_add(alive ? sum[3] + pair_pot : 0.0, energy);
+  warp_add_u64(2ull * np, pairs);
   warp_add_u64(ni, pairs + 1);
 }
 
@@ -500,6 +569,8 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   const uint32_t* total = c->starts + c->nkeys;
   if (c->fp32) {
+    // the kernel adds each pair's force to both particles: the result starts at zero
+    cudaMemsetAsync(c->fpp, 0, sizeof(float4) * static_cast<size_t>(n), s);
     const unsigned wblocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
     auto run = [&](auto kern) {
       kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
@@ -519,6 +590,7 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
       default: run(k_pp_f32<15>); break;
     }
   } else {
+    cudaMemsetAsync(c->fpp, 0, sizeof(D4) * static_cast<size_t>(n), s);
     k_pp_f64<<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const Rec64*>(c->recp), c->starts,
                                          static_cast<D4*>(c->fpp), c->energy_acc, c->pair_acc);
   }

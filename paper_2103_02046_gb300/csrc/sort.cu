@@ -212,10 +212,12 @@ __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
       hi[d] = static_cast<float>(xr[d]);
       lo[d] = static_cast<float>(xr[d] - static_cast<double>(hi[d]));
     }
-    // hi and lo together fill one 32-byte sector: a full-sector scattered write
+    // hi and lo together fill one 32-byte sector: a full-sector scattered write. The lo part's
+    // w holds the particle's row (rz * nc_y + ry) as the sort computed it, so the short range
+    // takes its neighbour rows from the same row the sort placed it in.
     float4* r = reinterpret_cast<float4*>(recp) + 2 * static_cast<size_t>(pos);
     r[0] = make_float4(hi[0], hi[1], hi[2], __int_as_float(static_cast<int>(i)));
-    r[1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    r[1] = make_float4(lo[0], lo[1], lo[2], __uint_as_float(key / static_cast<uint32_t>(g.nc[0])));
     reinterpret_cast<float4*>(recm)[pos] =
         make_float4(static_cast<float>(u[0]), static_cast<float>(u[1]), static_cast<float>(u[2]),
                     __uint_as_float(node));

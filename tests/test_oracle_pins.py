@@ -182,6 +182,24 @@ def test_pp_cell_list_equals_brute_force(pp_bc):
     np.testing.assert_allclose(Fs, Fc[idx], rtol=1e-15, atol=0)
 
 
+@pytest.mark.parametrize("inside", [1e-10, -1e-10])
+def test_pp_lattice_pair_count_closed_form(inside):
+    # Eq. (summation_short) takes pairs with r < r_c: on an 8^3 cubic lattice of spacing a with
+    # r_c = 2a (1 + inside), the ordered pair count is sum over offsets d (|d|^2 <= 4, or < 4 when
+    # the cutoff sits just below 2a) of the number of lattice pairs at offset d
+    a = 1e-4
+    g = np.arange(8) * a
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    h = 7 * a / 3   # auto_mesh spacing for n = 8 over a 7a box
+    P = O.auto_mesh(x, 8, rc_over_h=2 * a * (1 + inside) / h)
+    lim = 4 if inside > 0 else 3
+    expect = sum((8 - abs(i)) * (8 - abs(j)) * (8 - abs(k))
+                 for i in range(-2, 3) for j in range(-2, 3) for k in range(-2, 3)
+                 if 0 < i * i + j * j + k * k <= lim)
+    _, _, (pairs, _, _) = O.pp(x, P)
+    assert pairs == expect
+
+
 @pytest.mark.parametrize("bc", [0, 1])
 def test_pp_reduces_to_coulomb_without_screening(bc):
     # alpha -> 0 and r_c -> infinity turn the screened sum into the plain Coulomb sum.
