@@ -99,6 +99,11 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
     if (cells <= cap || nsub == 1) break;
     nsub /= 2;
   }
+  for (int d = 0; d < 3; ++d) {
+    g.cw_f[d] = static_cast<float>(g.cw[d]);
+    g.inv_cw_f[d] = static_cast<float>(g.inv_cw[d]);
+  }
+  g.slack_f = static_cast<float>(g.slack);
   g.order = p->assign_order;
   g.pm_bc = p->pm_bc;
   g.pp_bc = p->pp_bc;
@@ -178,7 +183,7 @@ cudaError_t alloc(T** ptr, size_t count) {
 void free_all(p3m_ctx* c) {
   void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recm, c->fpp,
                   c->acc, c->qpad, c->qhat, c->qhat2, c->khat_f, c->khat_i, c->fhat, c->freal,
-                  c->phihat, c->phireal, c->dfac, c->energy_acc, c->pair_acc, c->err_dev,
+                  c->phihat, c->phireal, c->dfac, c->energy_acc, c->pair_acc, c->pp_tile, c->err_dev,
                   c->ckpt, c->seg, c->lam_x, c->lam_p, c->xw, c->pw, c->tmp3, c->tmp3b,
                   c->f_work, c->red};
   for (void* b : bufs) cudaFree(b);
@@ -482,6 +487,8 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   }
   A(alloc(&c->energy_acc, 2));
   A(alloc(&c->pair_acc, 2));
+  A(alloc(&c->pp_tile, 1));
+  A(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   A(alloc(&c->err_dev, 1));
   A(alloc(&c->red, 32));
   A(alloc(&c->f_work, 3 * n_max));

@@ -58,6 +58,7 @@ struct Geom {
   // bins in FP32, the short range works from FP32 hi parts): 1e-6 of the largest mesh extent,
   // at least 1e-4, while those errors stay below 3.1e-7 of the extent.
   double slack;
+  float cw_f[3], inv_cw_f[3], slack_f;  // FP32 copies for the FP32 short range
 };
 
 // FP32 pair kernel: erfc(x) e^{x^2} on x in [0, kappa_eff] as a polynomial in t = 2 x /
@@ -173,6 +174,8 @@ struct p3m_ctx {
   // diagnostics
   double* energy_acc = nullptr;              // device [2]
   unsigned long long* pair_acc = nullptr;    // device [2]
+  uint32_t* pp_tile = nullptr;               // device [1]: next tile of the persistent short range
+  int num_sms = 0;
   int* err_dev = nullptr;                    // device error bits
   int* err_host = nullptr;                   // pinned mirror of err_dev
 

@@ -18,6 +18,7 @@
 // recompute the separation as (hi_i - hi_j) + (lo_i - lo_j), exact to FP32 relative rounding at
 // any distance. Partial sums are folded into a two-float (TwoSum) accumulator every few pairs,
 // so the per-particle sum is compensated at a small fraction of an addition per pair.
+#include <algorithm>
 #include <cmath>
 
 #include "p3m_internal.cuh"
@@ -137,6 +138,15 @@ struct PosD {
 // R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}.
 // ------------------------------------------------------------------------------------------
 constexpr int kHalfRows = kRowSpan * kRowSpan / 2 + 1;  // own row + the 12 after it
+constexpr int kPpBlocksPerSm = 10;  // resident blocks per SM (48 registers per thread)
+
+// One 32-byte record (hi and lo float4) in a single 256-bit load through the read-only path.
+// The records array is 32-byte aligned and not written while the short range runs.
+__device__ __forceinline__ void load_rec32(const float4* p, float4& h, float4& l) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(h.x), "=f"(h.y), "=f"(h.z), "=f"(h.w), "=f"(l.x), "=f"(l.y), "=f"(l.z), "=f"(l.w)
+      : "l"(p));
+}
 
 __device__ __forceinline__ void red_add_v4(float4* dst, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(a), "f"(b),
@@ -166,15 +176,15 @@ __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restr
   j0 = j1 = 0;
   const int ry = cy + (r % kRowSpan) - kRowReach, rz = cz + (r / kRowSpan) - kRowReach;
   if (ry < 0 || ry >= g.nc[1] || rz < 0 || rz >= g.nc[2]) return;
-  const float slack = static_cast<float>(g.slack);
-  const float cwy = static_cast<float>(g.cw[1]), cwz = static_cast<float>(g.cw[2]);
+  const float slack = g.slack_f;
+  const float cwy = g.cw_f[1], cwz = g.cw_f[2];
   const float yl = ry * cwy, yh = yl + cwy, zl = rz * cwz, zh = zl + cwz;
   const float dy = fmaxf((py < yl ? yl - py : (py > yh ? py - yh : 0.f)) - slack, 0.f);
   const float dz = fmaxf((pz < zl ? zl - pz : (pz > zh ? pz - zh : 0.f)) - slack, 0.f);
   const float d2 = dy * dy + dz * dz;
   if (d2 >= 1.f) return;
   const float w = sqrtf(1.f - d2) + slack;
-  const float iwx = static_cast<float>(g.inv_cw[0]);
+  const float iwx = g.inv_cw_f[0];
   const int c0 = max(static_cast<int>(floorf((px - w) * iwx)), 0);
   const int c1 = min(static_cast<int>(floorf((px + w) * iwx)), g.nc[0] - 1);
   if (c0 > c1) return;
@@ -184,129 +194,143 @@ __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restr
 }
 
 template <int kDeg>
-__global__ void __launch_bounds__(kThreads, 10)
+__global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
              const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
-             float4* __restrict__ fpp,
+             float4* __restrict__ fpp, uint32_t* __restrict__ next_tile,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
   __shared__ uint32_t run_j0[kHalfRows][kThreads], run_j1[kHalfRows][kThreads];
+  __shared__ uint32_t tile_s;
   const int tid = threadIdx.x;
   const uint32_t N = *total;
-  const uint32_t i = blockIdx.x * kThreads + tid;
-  const bool alive = i < N;
-  // lanes past the last particle walk nothing; they compare record 0 with itself (in bounds,
-  // separation exactly 0, never a pair) so that every lane can take part in the lockstep loop
-  const uint32_t ie = alive ? i : 0u;
-  const float4 pi = rec[2 * ie], li = rec[2 * ie + 1];
-  const float4* self = rec + 2 * static_cast<size_t>(ie);
-  int cnt = 0;
-  if (alive) {
-    const uint32_t row = __float_as_uint(li.w);
-    const int cy = static_cast<int>(row % static_cast<uint32_t>(g.nc[1]));
-    const int cz = static_cast<int>(row / static_cast<uint32_t>(g.nc[1]));
-    for (int r = kRowSpan * kRowSpan / 2; r < kRowSpan * kRowSpan; ++r) {
-      uint32_t j0, j1;
-      row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
-      j0 = max(j0, i + 1);  // own row: only the particles after i (a no-op for later rows)
-      if (j0 < j1) {
-        run_j0[cnt][tid] = j0;
-        run_j1[cnt][tid] = j1;
-        ++cnt;
-      }
-    }
-  }
-  uint32_t ptr = 0, end = 0;
-  if (cnt > 0) {
-    ptr = run_j0[0][tid];
-    end = run_j1[0][tid];
-  }
-  int k = 0;
-  Acc2 sum[4];
-  for (int c = 0; c < 4; ++c) sum[c].hi = sum[c].lo = 0.f;
-  float part[4] = {0.f, 0.f, 0.f, 0.f};
-  unsigned int np = 0;
-  auto test = [&](const float4* pj, float& rx, float& ry, float& rz) {
-    const float4 hj = pj[0], lj = pj[1];
-    rx = (pi.x - hj.x) + (li.x - lj.x);
-    ry = (pi.y - hj.y) + (li.y - lj.y);
-    rz = (pi.z - hj.z) + (li.z - lj.z);
-    return rx * rx + ry * ry + rz * rz;
-  };
-  auto pair = [&](bool hit, float r2, float rx, float ry, float rz, uint32_t j) {
-    float fco, pot;
-    pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
-    fco = hit ? fco : 0.f;
-    pot = hit ? pot : 0.f;
-    part[0] = fmaf(fco, rx, part[0]);
-    part[1] = fmaf(fco, ry, part[1]);
-    part[2] = fmaf(fco, rz, part[2]);
-    part[3] += pot;
-    np += hit;
-    if (hit) red_add_v4(fpp + j, -fco * rx, -fco * ry, -fco * rz, pot);
-  };
-  int step = 0;
-  while (__any_sync(0xffffffffu, ptr < end)) {
-    const float4* pa = ptr < end ? rec + 2 * static_cast<size_t>(ptr) : self;
-    const float4* pb = ptr + 1 < end ? rec + 2 * static_cast<size_t>(ptr + 1) : self;
-    float ax, ay, az, bx, by, bz;
-    const float ra = test(pa, ax, ay, az);
-    const float rb = test(pb, bx, by, bz);
-    const bool ha = ra < 1.f && ra > 0.f;  // the self pair has r2 == 0 exactly
-    const bool hb = rb < 1.f && rb > 0.f;
-    if (__any_sync(0xffffffffu, ha)) pair(ha, ra, ax, ay, az, ptr);
-    if (__any_sync(0xffffffffu, hb)) pair(hb, rb, bx, by, bz, ptr + 1);
-    ptr += 2;
-    if (ptr >= end && ++k < cnt) {
-      ptr = run_j0[k][tid];
-      end = run_j1[k][tid];
-    }
-    if ((++step & 7) == 0) {
-      for (int c = 0; c < 4; ++c) {
-        sum[c].add(part[c]);
-        part[c] = 0.f;
-      }
-    }
-  }
-  for (int c = 0; c < 4; ++c) sum[c].add(part[c]);
-  const float pair_pot = sum[3].value();
-  unsigned long long ni = 0;
-  if (alive && g.pp_bc) {
-    // images within r_c of particles less than r_c above the cathode (rare): plain loop over
-    // all 25 rows around the image point; image pairs act on i only
-    const double zi = static_cast<double>(pi.z) + static_cast<double>(li.z);
-    if (zi - 0.5 * g.img_c < 1.0) {
-      const float mz = static_cast<float>(g.img_c - zi);
-      const float ch = static_cast<float>(g.img_c);
-      const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
-      for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t ja, uint32_t jb) {
-        float rowv[4] = {0.f, 0.f, 0.f, 0.f};
-        for (uint32_t jj = ja; jj < jb; ++jj) {
-          const float4 hj = rec[2 * jj], lj = rec[2 * jj + 1];
-          const float ax = (pi.x - hj.x) + (li.x - lj.x);
-          const float ay = (pi.y - hj.y) + (li.y - lj.y);
-          const float s = pi.z + hj.z;
-          const float bp = s - pi.z;
-          const float e = (pi.z - (s - bp)) + (hj.z - bp);
-          const float az = ((s - ch) + e) + ((li.z + lj.z) - cl);
-          const float r2 = ax * ax + ay * ay + az * az;
-          if (r2 < 1.f && r2 > 0.f) {
-            float fco, pot;
-            pair_poly<kDeg>(P, r2, fco, pot);
-            rowv[0] -= fco * ax;
-            rowv[1] -= fco * ay;
-            rowv[2] -= fco * az;
-            rowv[3] -= pot;
-            ++ni;
-          }
+  double e_acc = 0.0;
+  unsigned long long np = 0, ni = 0;
+  // persistent blocks: each takes the next tile of kThreads sorted particles until none is left
+  for (;;) {
+    if (tid == 0) tile_s = atomicAdd(next_tile, 1u);
+    __syncthreads();
+    const uint32_t tile = tile_s;
+    __syncthreads();
+    if (static_cast<uint64_t>(tile) * kThreads >= N) break;
+    const uint32_t i = tile * kThreads + tid;
+    const bool alive = i < N;
+    // lanes past the last particle have no candidates; they read record 0 (in bounds) and take
+    // part in the lockstep loop with every result masked out
+    const uint32_t ie = alive ? i : 0u;
+    const float4 pi = rec[2 * ie], li = rec[2 * ie + 1];
+    int cnt = 0;
+    if (alive) {
+      const uint32_t row = __float_as_uint(li.w);
+      const int cy = static_cast<int>(row % static_cast<uint32_t>(g.nc[1]));
+      const int cz = static_cast<int>(row / static_cast<uint32_t>(g.nc[1]));
+      for (int r = kRowSpan * kRowSpan / 2; r < kRowSpan * kRowSpan; ++r) {
+        uint32_t j0, j1;
+        row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
+        j0 = max(j0, i + 1);  // own row: only the particles after i (a no-op for later rows)
+        if (j0 < j1) {
+          run_j0[cnt][tid] = j0;
+          run_j1[cnt][tid] = j1;
+          ++cnt;
         }
-        for (int c = 0; c < 4; ++c) sum[c].add(rowv[c]);
-      });
+      }
+    }
+    uint32_t ptr = 0, end = 0;
+    if (cnt > 0) {
+      ptr = run_j0[0][tid];
+      end = run_j1[0][tid];
+    }
+    int k = 0;
+    Acc2 sum[4];
+    for (int c = 0; c < 4; ++c) sum[c].hi = sum[c].lo = 0.f;
+    float part[4] = {0.f, 0.f, 0.f, 0.f};
+    auto test = [&](const float4* pj, float& rx, float& ry, float& rz) {
+      float4 hj, lj;
+      load_rec32(pj, hj, lj);
+      rx = (pi.x - hj.x) + (li.x - lj.x);
+      ry = (pi.y - hj.y) + (li.y - lj.y);
+      rz = (pi.z - hj.z) + (li.z - lj.z);
+      return rx * rx + ry * ry + rz * rz;
+    };
+    auto pair = [&](bool hit, float r2, float rx, float ry, float rz, uint32_t j) {
+      float fco, pot;
+      pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
+      fco = hit ? fco : 0.f;
+      pot = hit ? pot : 0.f;
+      part[0] = fmaf(fco, rx, part[0]);
+      part[1] = fmaf(fco, ry, part[1]);
+      part[2] = fmaf(fco, rz, part[2]);
+      part[3] += pot;
+      np += hit;
+      if (hit) red_add_v4(fpp + j, -fco * rx, -fco * ry, -fco * rz, pot);
+    };
+    int step = 0;
+    while (__any_sync(0xffffffffu, ptr < end)) {
+      // a lane without a candidate reads record 0, as every such lane does, so that the load
+      // costs the warp one extra sector at most; its result is masked out
+      const bool va = ptr < end, vb = ptr + 1 < end;
+      const float4* pa = va ? rec + 2 * static_cast<size_t>(ptr) : rec;
+      const float4* pb = vb ? rec + 2 * static_cast<size_t>(ptr + 1) : rec;
+      float ax, ay, az, bx, by, bz;
+      const float ra = test(pa, ax, ay, az);
+      const float rb = test(pb, bx, by, bz);
+      const bool ha = va && ra < 1.f && ra > 0.f;  // coincident particles (r2 == 0) are skipped
+      const bool hb = vb && rb < 1.f && rb > 0.f;
+      if (__any_sync(0xffffffffu, ha)) pair(ha, ra, ax, ay, az, ptr);
+      if (__any_sync(0xffffffffu, hb)) pair(hb, rb, bx, by, bz, ptr + 1);
+      ptr += 2;
+      if (ptr >= end && ++k < cnt) {
+        ptr = run_j0[k][tid];
+        end = run_j1[k][tid];
+      }
+      if ((++step & 7) == 0) {
+        for (int c = 0; c < 4; ++c) {
+          sum[c].add(part[c]);
+          part[c] = 0.f;
+        }
+      }
+    }
+    for (int c = 0; c < 4; ++c) sum[c].add(part[c]);
+    const float pair_pot = sum[3].value();
+    if (alive && g.pp_bc) {
+      // images within r_c of particles less than r_c above the cathode (rare): plain loop over
+      // all 25 rows around the image point; image pairs act on i only
+      const double zi = static_cast<double>(pi.z) + static_cast<double>(li.z);
+      if (zi - 0.5 * g.img_c < 1.0) {
+        const float mz = static_cast<float>(g.img_c - zi);
+        const float ch = static_cast<float>(g.img_c);
+        const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
+        for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t ja, uint32_t jb) {
+          float rowv[4] = {0.f, 0.f, 0.f, 0.f};
+          for (uint32_t jj = ja; jj < jb; ++jj) {
+            const float4 hj = rec[2 * jj], lj = rec[2 * jj + 1];
+            const float ax = (pi.x - hj.x) + (li.x - lj.x);
+            const float ay = (pi.y - hj.y) + (li.y - lj.y);
+            const float s = pi.z + hj.z;
+            const float bp = s - pi.z;
+            const float e = (pi.z - (s - bp)) + (hj.z - bp);
+            const float az = ((s - ch) + e) + ((li.z + lj.z) - cl);
+            const float r2 = ax * ax + ay * ay + az * az;
+            if (r2 < 1.f && r2 > 0.f) {
+              float fco, pot;
+              pair_poly<kDeg>(P, r2, fco, pot);
+              rowv[0] -= fco * ax;
+              rowv[1] -= fco * ay;
+              rowv[2] -= fco * az;
+              rowv[3] -= pot;
+              ++ni;
+            }
+          }
+          for (int c = 0; c < 4; ++c) sum[c].add(rowv[c]);
+        });
+      }
+    }
+    if (alive) {
+      red_add_v4(fpp + i, sum[0].value(), sum[1].value(), sum[2].value(), sum[3].value());
+      // sum_i phi_i over ordered pairs: each pair's potential was taken once here, plus images
+      e_acc += static_cast<double>(sum[3].value()) + pair_pot;
     }
   }
-  if (alive) red_add_v4(fpp + i, sum[0].value(), sum[1].value(), sum[2].value(), sum[3].value());
-  // sum_i phi_i over ordered pairs: each pair's potential was taken once here, plus the images
-  if (energy)
-    block_reduce_add(alive ? static_cast<double>(sum[3].value()) + pair_pot : 0.0, energy);
+  if (energy) block_reduce_add(e_acc, energy);
   warp_add_u64(2ull * np, pairs);
   warp_add_u64(ni, pairs + 1);
 }
@@ -357,7 +381,8 @@ __global__ void __launch_bounds__(kThreads)
   const bool alive = i < N;
   const double kappa = g.kappa_eff;
   const double c2k = 2.0 * g.kappa_eff * 0.56418958354775628695;
-  const uint32_t ie = alive ? i : 0u;  // see k_pp_f32: idle lanes compare record 0 with itself
+  // lanes past the last particle compare record 0 with itself (separation 0, never a pair)
+  const uint32_t ie = alive ? i : 0u;
   const Rec64 me = rec[ie];
   const double px = me.u[0], py = me.u[1], pz = me.u[2];
   const int cy = min(max(static_cast<int>(floor(py * g.inv_cw[1])), 0), g.nc[1] - 1);
@@ -571,10 +596,15 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
   if (c->fp32) {
     // the kernel adds each pair's force to both particles: the result starts at zero
     cudaMemsetAsync(c->fpp, 0, sizeof(float4) * static_cast<size_t>(n), s);
-    const unsigned wblocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
+    cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
+    // persistent grid of a few blocks per SM: the SM resources it leaves free let the mesh
+    // chain, on the other stream, run at the same time
+    const int64_t tiles = (n + kThreads - 1) / kThreads;
+    const unsigned wblocks = static_cast<unsigned>(
+        std::min<int64_t>(tiles, static_cast<int64_t>(kPpBlocksPerSm) * c->num_sms));
     auto run = [&](auto kern) {
       kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
-                                       c->starts, static_cast<float4*>(c->fpp),
+                                       c->starts, static_cast<float4*>(c->fpp), c->pp_tile,
                                        c->energy_acc, c->pair_acc);
     };
     switch (c->poly.deg) {
