@@ -104,6 +104,16 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
     g.inv_cw_f[d] = static_cast<float>(g.inv_cw[d]);
   }
   g.slack_f = static_cast<float>(g.slack);
+  auto df = [](double v, float out[2]) {
+    out[0] = static_cast<float>(v);
+    out[1] = static_cast<float>(v - static_cast<double>(out[0]));
+  };
+  for (int d = 0; d < 3; ++d) {
+    df(g.lo[d], g.lo_df[d]);
+    df(1.0 / g.h[d], g.inv_h_df[d]);
+  }
+  df(1.0 / g.rc, g.inv_rc_df);
+  for (int d = 0; d < 3; ++d) g.fscale_f[d] = static_cast<float>(-p->q / g.h[d]);
   g.order = p->assign_order;
   g.pm_bc = p->pm_bc;
   g.pp_bc = p->pp_bc;

@@ -59,7 +59,88 @@ struct Geom {
   // at least 1e-4, while those errors stay below 3.1e-7 of the extent.
   double slack;
   float cw_f[3], inv_cw_f[3], slack_f;  // FP32 copies for the FP32 short range
+  // double-float (hi + lo, each FP32) copies for the FP32 path's binning and records
+  float lo_df[3][2];     // mesh origin lo_d
+  float inv_rc_df[2];    // 1 / r_c
+  float inv_h_df[3][2];  // 1 / h_d
+  float fscale_f[3];     // -q / h_d in FP32
 };
+
+// ------------------------------------------------------------------------------------------
+// Double-float arithmetic: a value held as an unevaluated sum hi + lo of two floats, |lo| <=
+// ulp(hi) / 2, about 48 significant bits. The FP32 path uses it instead of FP64, whose
+// throughput on this part is a small fraction of FP32's.
+// ------------------------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+};
+
+// Exact sum a + b = s + e (Knuth's TwoSum).
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return DF{s, (a - (s - bb)) + (b - bb)};
+}
+
+// Renormalises s + e when |s| >= |e| (Dekker's Fast2Sum).
+__device__ __forceinline__ DF df_fast_two_sum(float s, float e) {
+  const float h = s + e;
+  return DF{h, e - (h - s)};
+}
+
+// (a.hi + a.lo) - (b.hi + b.lo), error about 2^-46 of the larger operand.
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+  const DF s = df_two_sum(a.hi, -b.hi);
+  return df_fast_two_sum(s.hi, s.lo + (a.lo - b.lo));
+}
+
+// (a.hi + a.lo) (c.hi + c.lo), relative error about 2^-46; the product a.hi c.hi is split
+// exactly with an FMA.
+__device__ __forceinline__ DF df_mul(DF a, const float c[2]) {
+  const float p = a.hi * c[0];
+  float e = fmaf(a.hi, c[0], -p);
+  e = fmaf(a.hi, c[1], e);
+  e = fmaf(a.lo, c[0], e);
+  return df_fast_two_sum(p, e);
+}
+
+// Exact widening of a float to double with integer operations (zero, subnormals, infinities
+// and NaN take the conversion route).
+static __device__ __noinline__ double float_to_double_slow(float v) {
+  return static_cast<double>(v);
+}
+static __device__ __noinline__ DF df_from_double_slow(double v) {
+  const float h = static_cast<float>(v);
+  return DF{h, static_cast<float>(v - static_cast<double>(h))};
+}
+
+__device__ __forceinline__ double float_to_double_exact(float v) {
+  const unsigned int b = __float_as_uint(v);
+  const unsigned int e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return float_to_double_slow(v);  // rare: a call, not predicated
+  const unsigned long long d = (static_cast<unsigned long long>(b & 0x80000000u) << 32) |
+                               (static_cast<unsigned long long>(e + 896u) << 52) |
+                               (static_cast<unsigned long long>(b & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(d));
+}
+
+// Splits a double into hi + lo with integer operations only: hi is v truncated to its leading
+// 24 significant bits (exactly a float), lo the remaining 29 bits rounded to a float, so
+// |v - hi - lo| <= 2^-48 |v|. Values whose exponent a float cannot hold (zero, below 2^-74,
+// above 2^127, not finite) take the conversion route instead.
+__device__ __forceinline__ DF df_from_double(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = static_cast<int>((b >> 52) & 0x7ffull);  // biased exponent
+  if (e < 1023 - 74 || e > 1023 + 127) return df_from_double_slow(v);  // rare: a real branch
+  const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
+  const unsigned int hb = sign | (static_cast<unsigned int>(e - 1023 + 127) << 23) |
+                          static_cast<unsigned int>((b >> 29) & 0x7fffffull);
+  const unsigned int rem = static_cast<unsigned int>(b & 0x1fffffffull);  // below hi's last bit
+  // rem * 2^(e - 1075): the scale is a normal float for e >= 949
+  const float scale = __uint_as_float(static_cast<unsigned int>(e - 1075 + 127) << 23);
+  const float lo = __uint_as_float(__float_as_uint(static_cast<float>(rem) * scale) | sign);
+  return DF{__uint_as_float(hb), lo};
+}
 
 // FP32 pair kernel: erfc(x) e^{x^2} on x in [0, kappa_eff] as a polynomial in t = 2 x /
 // kappa_eff - 1 (Horner, highest degree first), fitted at context creation.

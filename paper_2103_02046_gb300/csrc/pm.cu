@@ -449,39 +449,73 @@ __device__ __forceinline__ void grad_from_phi(const Geom& g, const double* __res
 template <typename T>
 __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
                          const typename RecT<T>::type* __restrict__ recm,
-                         const typename RecT<T>::type* __restrict__ recp, const T* __restrict__ field,
-                         size_t nreal, const void* __restrict__ fpp, double* __restrict__ f,
-                         int parts, double pp_scale) {
+                         const T* __restrict__ field, size_t nreal, void* __restrict__ fpp,
+                         int parts, float pp_scale_f, double pp_scale) {
+  // F = F^L + F^S for sorted particle i, written over its short-range entry (sorted order, so
+  // the writes are coalesced); k_unpermute then puts the forces in the caller's order
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
   Axis<T> ax[3];
   particle_axes<T>(g, recm, i, ax);
-  const long long idx = orig_index(recp, i);
-  double F[3] = {0.0, 0.0, 0.0};
-  if (parts & 2) {
-    T G[3];
-    if constexpr (sizeof(T) == 4)
+  if constexpr (sizeof(T) == 4) {
+    // FP32 path: long and short range combined in FP32
+    float F[3] = {0.f, 0.f, 0.f};
+    if (parts & 2) {
+      float G[3];
       grad_from_diff(g, field, nreal, ax, G);
-    else
+      for (int d = 0; d < 3; ++d) F[d] = g.fscale_f[d] * G[d];
+    }
+    float4* out = reinterpret_cast<float4*>(fpp) + i;
+    if (parts & 1) {
+      const float4 s = *out;
+      F[0] = fmaf(pp_scale_f, s.x, F[0]);
+      F[1] = fmaf(pp_scale_f, s.y, F[1]);
+      F[2] = fmaf(pp_scale_f, s.z, F[2]);
+    }
+    *out = make_float4(F[0], F[1], F[2], 0.f);
+  } else {
+    double F[3] = {0.0, 0.0, 0.0};
+    if (parts & 2) {
+      T G[3];
       grad_from_phi(g, field, ax, G);
-    for (int d = 0; d < 3; ++d) F[d] = g.fscale[d] * static_cast<double>(G[d]);
-  }
-  if (parts & 1) {
-    if constexpr (sizeof(T) == 4) {
-      const float4 s = reinterpret_cast<const float4*>(fpp)[i];
-      F[0] += pp_scale * s.x;
-      F[1] += pp_scale * s.y;
-      F[2] += pp_scale * s.z;
-    } else {
-      const D4 s = reinterpret_cast<const D4*>(fpp)[i];
+      for (int d = 0; d < 3; ++d) F[d] = g.fscale[d] * static_cast<double>(G[d]);
+    }
+    D4* out = reinterpret_cast<D4*>(fpp) + i;
+    if (parts & 1) {
+      const D4 s = *out;
       F[0] += pp_scale * s.x;
       F[1] += pp_scale * s.y;
       F[2] += pp_scale * s.z;
     }
+    *out = D4{F[0], F[1], F[2], 0.0};
   }
-  f[3 * idx] = F[0];
-  f[3 * idx + 1] = F[1];
-  f[3 * idx + 2] = F[2];
+}
+
+// f[i] = the force of input particle i, gathered from sorted order through its sorted position
+// (keys[i] after the scatter); particles left out of the sort (outside the mesh) get zero.
+template <typename T>
+__global__ void k_unpermute(const uint32_t* __restrict__ pos, int64_t n,
+                            const void* __restrict__ fsorted, double* __restrict__ f) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = pos[i];
+  double F[3] = {0.0, 0.0, 0.0};
+  if (k != kInvalidKey) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 s = reinterpret_cast<const float4*>(fsorted)[k];
+      F[0] = float_to_double_exact(s.x);
+      F[1] = float_to_double_exact(s.y);
+      F[2] = float_to_double_exact(s.z);
+    } else {
+      const D4 s = reinterpret_cast<const D4*>(fsorted)[k];
+      F[0] = s.x;
+      F[1] = s.y;
+      F[2] = s.z;
+    }
+  }
+  f[3 * i] = F[0];
+  f[3 * i + 1] = F[1];
+  f[3 * i + 2] = F[2];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -705,14 +739,17 @@ void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts) {
   if (n == 0) return;
   const uint32_t* total = c->starts + c->nkeys;
   const double pp_scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc);
-  if (c->fp32)
+  if (c->fp32) {
     k_interp<float><<<blocks_for(n), kThreads, 0, c->work>>>(
-        c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp),
-        static_cast<const float*>(c->freal), c->n_real, c->fpp, f, parts, pp_scale);
-  else
+        c->g, total, static_cast<const float4*>(c->recm), static_cast<const float*>(c->freal),
+        c->n_real, c->fpp, parts, static_cast<float>(pp_scale), pp_scale);
+    k_unpermute<float><<<blocks_for(n), kThreads, 0, c->work>>>(c->keys, n, c->fpp, f);
+  } else {
     k_interp<double><<<blocks_for(n), kThreads, 0, c->work>>>(
-        c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp),
-        static_cast<const double*>(c->phireal), c->n_real, c->fpp, f, parts, pp_scale);
+        c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const double*>(c->phireal),
+        c->n_real, c->fpp, parts, static_cast<float>(pp_scale), pp_scale);
+    k_unpermute<double><<<blocks_for(n), kThreads, 0, c->work>>>(c->keys, n, c->fpp, f);
+  }
 }
 
 void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, double* out) {

@@ -19,7 +19,9 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 // slow on this part) unless it lies within 1e-9 of a point where the assignment changes its
 // node (integers for CIC, half-integers for TSC); there the IEEE quotient is taken, so the node
 // decision is exactly the one the definition makes.
-__device__ __forceinline__ double mesh_coord(const Geom& g, double v, int d) {
+// Not inlined: the callers reach it only within 1e-3 of a knot, and as a call it stays a real
+// branch instead of being predicated into every thread's instruction stream (FP64 is slow here).
+static __device__ __noinline__ double mesh_coord(const Geom& g, double v, int d) {
   const double dv = v - g.lo[d];
   const double s = dv * g.inv_h[d];
   const double knot = (g.order == 2) ? floor(s + 0.5) - 0.5 : floor(s);
@@ -38,8 +40,8 @@ __device__ __forceinline__ int particle_cell(const Geom& g, const double* __rest
                                              int cell[3]) {
   int err = 0;
   for (int d = 0; d < 3; ++d) {
-    const double dv = xi[d] - g.lo[d];
-    const float f = static_cast<float>(dv);
+    // x - lo_d in double-float, rounded to FP32 (no FP64 arithmetic)
+    const float f = df_sub(df_from_double(xi[d]), DF{g.lo_df[d][0], g.lo_df[d][1]}).hi;
     if (!(f == f)) return kErrNaN;
     const float s = f * g.inv_h_f[d];
     const float b0 = (g.order == 2) ? 0.5f : 0.0f;
@@ -176,7 +178,7 @@ __global__ void k_scan_add(uint32_t* __restrict__ out, const uint32_t* __restric
 
 template <bool kFP32>
 __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
-                          const uint32_t* __restrict__ keys, const uint32_t* __restrict__ ranks,
+                          uint32_t* __restrict__ keys, const uint32_t* __restrict__ ranks,
                           const uint32_t* __restrict__ starts, void* __restrict__ recp,
                           void* __restrict__ recm) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -184,8 +186,44 @@ __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
   const uint32_t key = keys[i];
   if (key == kInvalidKey) return;
   const uint32_t pos = starts[key] + ranks[i];
-  double xr[3], u[3];
+  keys[i] = pos;  // from here on keys[i] is the sorted position of input particle i
   int c[3];
+  if (kFP32) {
+    // FP32 records from double-float arithmetic: positions in cutoff units as hi + lo (about
+    // 2^-46 relative) and TSC/CIC offsets u = s - node, s = (x - lo) / h. The node comes from
+    // s.hi unless s is within 1e-3 of a point where the node changes; there the exact FP64
+    // coordinate decides, as in the definition.
+    float hi[3], lo[3], u[3];
+    for (int d = 0; d < 3; ++d) {
+      const double v = x[3 * i + d];
+      const DF dv = df_sub(df_from_double(v), DF{g.lo_df[d][0], g.lo_df[d][1]});
+      const DF xr = df_mul(dv, g.inv_rc_df);
+      const DF sm = df_mul(dv, g.inv_h_df[d]);
+      hi[d] = xr.hi;
+      lo[d] = xr.lo;
+      const float cf = (g.order == 2) ? floorf(sm.hi + 0.5f) : floorf(sm.hi);
+      const float kl = (g.order == 2) ? cf - 0.5f : cf;
+      if (fabsf(sm.hi - kl) < 1e-3f || fabsf(sm.hi - kl - 1.f) < 1e-3f) {
+        const double se = mesh_coord(g, v, d);
+        const double cn = (g.order == 2) ? floor(se + 0.5) : floor(se);
+        u[d] = static_cast<float>(se - cn);
+        c[d] = static_cast<int>(cn);
+      } else {
+        u[d] = (sm.hi - cf) + sm.lo;  // sm.hi - cf is exact
+        c[d] = static_cast<int>(cf);
+      }
+    }
+    const uint32_t node = pack_node(c[0], c[1], c[2]);
+    // hi and lo together fill one 32-byte sector: a full-sector scattered write. The lo part's
+    // w holds the particle's row (rz * nc_y + ry) as the sort computed it, so the short range
+    // takes its neighbour rows from the same row the sort placed it in.
+    float4* r = reinterpret_cast<float4*>(recp) + 2 * static_cast<size_t>(pos);
+    r[0] = make_float4(hi[0], hi[1], hi[2], __int_as_float(static_cast<int>(i)));
+    r[1] = make_float4(lo[0], lo[1], lo[2], __uint_as_float(key / static_cast<uint32_t>(g.nc[0])));
+    reinterpret_cast<float4*>(recm)[pos] = make_float4(u[0], u[1], u[2], __uint_as_float(node));
+    return;
+  }
+  double xr[3], u[3];
   for (int d = 0; d < 3; ++d) {
     const double v = x[3 * i + d];
     const double dv = v - g.lo[d];
@@ -206,22 +244,7 @@ __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
     c[d] = static_cast<int>(cn);
   }
   const uint32_t node = pack_node(c[0], c[1], c[2]);
-  if (kFP32) {
-    float hi[3], lo[3];
-    for (int d = 0; d < 3; ++d) {
-      hi[d] = static_cast<float>(xr[d]);
-      lo[d] = static_cast<float>(xr[d] - static_cast<double>(hi[d]));
-    }
-    // hi and lo together fill one 32-byte sector: a full-sector scattered write. The lo part's
-    // w holds the particle's row (rz * nc_y + ry) as the sort computed it, so the short range
-    // takes its neighbour rows from the same row the sort placed it in.
-    float4* r = reinterpret_cast<float4*>(recp) + 2 * static_cast<size_t>(pos);
-    r[0] = make_float4(hi[0], hi[1], hi[2], __int_as_float(static_cast<int>(i)));
-    r[1] = make_float4(lo[0], lo[1], lo[2], __uint_as_float(key / static_cast<uint32_t>(g.nc[0])));
-    reinterpret_cast<float4*>(recm)[pos] =
-        make_float4(static_cast<float>(u[0]), static_cast<float>(u[1]), static_cast<float>(u[2]),
-                    __uint_as_float(node));
-  } else {
+  {
     Rec64 r;
     r.u[0] = xr[0];
     r.u[1] = xr[1];
