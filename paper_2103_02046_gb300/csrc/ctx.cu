@@ -193,9 +193,9 @@ cudaError_t alloc(T** ptr, size_t count) {
 void free_all(p3m_ctx* c) {
   void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recm, c->fpp,
                   c->acc, c->qpad, c->qhat, c->qhat2, c->khat_f, c->khat_i, c->fhat, c->freal,
-                  c->phihat, c->phireal, c->dfac, c->energy_acc, c->pair_acc, c->pp_tile, c->err_dev,
-                  c->ckpt, c->seg, c->lam_x, c->lam_p, c->xw, c->pw, c->tmp3, c->tmp3b,
-                  c->f_work, c->red};
+                  c->phihat, c->phireal, c->dfac, c->ztw, c->energy_acc, c->pair_acc,
+                  c->pp_tile, c->err_dev, c->ckpt, c->seg, c->lam_x, c->lam_p, c->xw, c->pw,
+                  c->tmp3, c->tmp3b, c->f_work, c->red};
   for (void* b : bufs) cudaFree(b);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->have_xy_f) cufftDestroy(c->plan_xy_f);
@@ -292,6 +292,20 @@ cufftResult fft_c2r(p3m_ctx* c, void* spec, void* real) {
 // Solve on the current qpad: FP64 -> potential; FP32 -> difference fields (and the potential
 // when want_phi).
 p3m_status mesh_solve(p3m_ctx* c, bool want_phi, bool want_diff, bool want_energy) {
+  if (c->zconv && want_diff && !want_phi) {
+    // FP32 forces: x-y transforms of the charged planes, the fused z solve, x-y inverses
+    if (cufftExecR2C(c->plan_xy_f, static_cast<cufftReal*>(c->qpad),
+                     static_cast<cufftComplex*>(c->qhat)) != CUFFT_SUCCESS)
+      return fail(c, P3M_ECUFFT, "cuFFT forward transform failed");
+    launch_zconv(c, want_energy);
+    for (int d = 0; d < 3; ++d) {
+      auto* spec = static_cast<cufftComplex*>(c->fhat) + d * c->n_cplx;
+      auto* real = static_cast<cufftReal*>(c->freal) + d * c->n_real;
+      if (cufftExecC2R(c->plan_xy_i, spec, real) != CUFFT_SUCCESS)
+        return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
+    }
+    return P3M_OK;
+  }
   p3m_status s = fft_r2c(c);
   if (s != P3M_OK) return s;
   if (!c->fp32) want_phi = true, want_diff = false;
@@ -580,6 +594,10 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     cufftSetStream(c->plan_xy_i, c->work);
   }
   e = build_green(c);
+  if (e == cudaSuccess && zconv_supported(c)) {
+    e = zconv_setup(c);
+    c->zconv = e == cudaSuccess;
+  }
   if (e != cudaSuccess) {
     free_all(c);
     delete c;

@@ -243,6 +243,8 @@ struct p3m_ctx {
   void* phihat = nullptr;       // potential spectrum
   void* phireal = nullptr;      // potential on the doubled mesh
   float2* dfac = nullptr;       // FP32: difference factors e^{2 pi i k/M} - 1 per axis (Mx/2+1 + My + Mz)
+  float2* ztw = nullptr;        // FP32 fused z solve: e^{-2 pi i t / Mz}, t < Mz
+  bool zconv = false;           // FP32 forces use the fused z solve
   // Pruned transforms of the doubled mesh: the charge is non-zero, and the fields are needed,
   // only in the n^3 block, so the x-y plane transforms run on the first n_z planes only and
   // the z transforms are strided 1D batches over all (kx, ky) columns.
@@ -293,6 +295,10 @@ void launch_zero_block(const p3m_ctx* c);
 void launch_deposit(const p3m_ctx* c, int64_t n);
 void launch_dipole_deposit(const p3m_ctx* c, int64_t n, const double* w);
 void launch_green_multiply(const p3m_ctx* c, bool want_phi, bool want_diff, bool want_energy);
+// fused z transforms + Green's multiply of the FP32 path (power-of-two Mz in [64, 2048])
+bool zconv_supported(const p3m_ctx* c);
+cudaError_t zconv_setup(p3m_ctx* c);
+void launch_zconv(const p3m_ctx* c, bool want_energy);
 void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts);
 void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, double* out);
 void launch_get_mesh(const p3m_ctx* c, int which, double* out);

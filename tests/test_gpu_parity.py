@@ -54,6 +54,10 @@ CASES = [
     ("open_cic", 16, 0, 0, 1, 0),
     ("cathode_influence", 16, 1, 0, 2, 1),
     ("aniso_ragged", (16, 20, 24), 1, 1, 2, 0),
+    # doubled z length a power of two >= 64: the FP32 path's fused z solve
+    ("open_tsc_32", 32, 0, 0, 2, 0),
+    ("cathode_pp_bc_aniso_z64", (20, 24, 64), 1, 1, 2, 0),
+    ("cathode_cic_influence_32", 32, 1, 0, 1, 1),
 ]
 
 
