@@ -4,7 +4,7 @@ Workload (default): uniformly filled cold sphere, N = 16,777,216 particles, R = 
 q = 1e-15 C, mesh 256^3 over the bounding box with two spacings of margin, r_c = 2h,
 kappa = 3, TSC, open boundaries; FP32 mixed path (FP64 positions, forces and reductions).
 A "step" is one force evaluation of all particles: bin + sort, short range, deposit,
-Green's-function solve, interpolation. Inputs (x: 403 MB, sorted records: 268 MB) are
+Green's-function solve, interpolation. Inputs (x: 403 MB, sorted records: 537 MB) are
 larger than the 129 MB L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--rc K]
@@ -48,7 +48,7 @@ PP_DRAM_BYTES_PER_PARTICLE = 93.076224e6 / 2097152
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rc", type=float, default=2.0, help="r_c in mesh spacings")
@@ -251,20 +251,41 @@ def run_ours(a, rank, world, local_rank):
     ctx64.close()
     del f64
 
-    # end to end through the public API: pinned host input -> device -> forces -> host
+    # end to end through the public API: pinned host input -> device -> forces -> host, every
+    # step, double-buffered: step k's upload and step k-1's download run on their own streams
+    # while step k computes (as an application streaming evaluations would run them)
     xh = torch.from_numpy(x_host).pin_memory()
-    fh = torch.empty_like(xh).pin_memory()
-    xd = torch.empty_like(xg)
-    for _ in range(2):
-        xd.copy_(xh, non_blocking=True)
-        ctx.forces(xd, out=f)
-        fh.copy_(f, non_blocking=True)
+    fh = [torch.empty_like(xh).pin_memory() for _ in range(2)]
+    xd = [torch.empty_like(xg) for _ in range(2)]
+    fd = [f, torch.empty_like(f)]
+    s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+    up_done = [torch.cuda.Event() for _ in range(2)]
+    comp_done = [torch.cuda.Event() for _ in range(2)]
+    down_done = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_steps(count):
+        for k in range(count):
+            b = k % 2
+            with torch.cuda.stream(s_up):
+                if k >= 2:
+                    s_up.wait_event(comp_done[b])      # xd[b] read by step k-2
+                xd[b].copy_(xh, non_blocking=True)
+                up_done[b].record(s_up)
+            stream.wait_event(up_done[b])
+            if k >= 2:
+                stream.wait_event(down_done[b])        # fd[b] copied out by step k-2
+            ctx.forces(xd[b], out=fd[b])
+            comp_done[b].record(stream)
+            with torch.cuda.stream(s_down):
+                s_down.wait_event(comp_done[b])
+                fh[b].copy_(fd[b], non_blocking=True)
+                down_done[b].record(s_down)
+        stream.wait_event(down_done[(count - 1) % 2])  # the last result is on the host
+
+    e2e_steps(2)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(K):
-        xd.copy_(xh, non_blocking=True)
-        ctx.forces(xd, out=f)
-        fh.copy_(f, non_blocking=True)
+    e2e_steps(K)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -289,7 +310,7 @@ def run_ours(a, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": workload_name(a), "precision": "FP32 mixed (FP64 positions, "
                    "forces, reductions)", "l2": "inputs larger than L2 (x 403 MB, sorted "
-                   "records 268 MB); no flush", "parallelism": f"replicas x{world}"},
+                   "records 537 MB); no flush", "parallelism": f"replicas x{world}"},
         "pp_pairs_per_s": pp_pairs_per_s,
         "pp_pairs_per_eval": pairs,
         "stage_ms": {k: v / K for k, v in zip(

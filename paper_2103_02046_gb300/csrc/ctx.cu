@@ -113,7 +113,10 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
     df(1.0 / g.h[d], g.inv_h_df[d]);
   }
   df(1.0 / g.rc, g.inv_rc_df);
-  for (int d = 0; d < 3; ++d) g.fscale_f[d] = static_cast<float>(-p->q / g.h[d]);
+  for (int d = 0; d < 3; ++d) {
+    g.fscale_f[d] = static_cast<float>(-p->q / g.h[d]);
+    df(g.rc / g.h[d], g.rch_df[d]);
+  }
   g.order = p->assign_order;
   g.pm_bc = p->pm_bc;
   g.pp_bc = p->pp_bc;
@@ -476,7 +479,8 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   cudaGetDevice(&c->device);
   const Geom& g = c->g;
   c->nkeys = static_cast<uint64_t>(g.nc[0]) * g.nc[1] * g.nc[2];
-  if (c->nkeys >= 0xFFFFFFF0ull) {
+  if (c->nkeys >= 0xFFFFFFF0ull ||
+      static_cast<uint64_t>(g.nc[1]) * static_cast<uint64_t>(g.nc[2]) > kRowMask) {
     delete c;
     return P3M_EINVAL;
   }
@@ -494,7 +498,7 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   A(alloc(&c->keys, n_max));
   A(alloc(&c->ranks, n_max));
   A(cudaMalloc(&c->recp, 32 * static_cast<size_t>(n_max)));
-  A(cudaMalloc(&c->recm, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
+  if (!c->fp32) A(cudaMalloc(&c->recm, 32 * static_cast<size_t>(n_max)));  // FP32: in recp
   A(cudaMalloc(&c->fpp, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
   A(alloc(&c->acc, 3 * n_max));
   A(cudaMalloc(&c->qpad, es * c->n_real));

@@ -64,7 +64,14 @@ struct Geom {
   float inv_rc_df[2];    // 1 / r_c
   float inv_h_df[3][2];  // 1 / h_d
   float fscale_f[3];     // -q / h_d in FP32
+  float rch_df[3][2];    // r_c / h_d: cutoff units -> mesh units
 };
+
+// FP32 records: the lo part's w packs the particle's row (rz nc_y + ry, below 2^26) and, in the
+// top 6 bits, a node correction of -1, 0 or +1 per axis (2 bits each, stored + 1) that turns the
+// node recomputed from the position into the exact one near a knot.
+constexpr uint32_t kRowBits = 26;
+constexpr uint32_t kRowMask = (1u << kRowBits) - 1u;
 
 // ------------------------------------------------------------------------------------------
 // Double-float arithmetic: a value held as an unevaluated sum hi + lo of two floats, |lo| <=
@@ -75,32 +82,35 @@ struct DF {
   float hi, lo;
 };
 
+// The double-float steps below use the _rn intrinsics so that the compiler cannot contract a
+// product and a sum into one FMA, which would break the exact error terms.
+
 // Exact sum a + b = s + e (Knuth's TwoSum).
 __device__ __forceinline__ DF df_two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return DF{s, (a - (s - bb)) + (b - bb)};
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
 }
 
 // Renormalises s + e when |s| >= |e| (Dekker's Fast2Sum).
 __device__ __forceinline__ DF df_fast_two_sum(float s, float e) {
-  const float h = s + e;
-  return DF{h, e - (h - s)};
+  const float h = __fadd_rn(s, e);
+  return DF{h, __fsub_rn(e, __fsub_rn(h, s))};
 }
 
 // (a.hi + a.lo) - (b.hi + b.lo), error about 2^-46 of the larger operand.
 __device__ __forceinline__ DF df_sub(DF a, DF b) {
   const DF s = df_two_sum(a.hi, -b.hi);
-  return df_fast_two_sum(s.hi, s.lo + (a.lo - b.lo));
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo)));
 }
 
 // (a.hi + a.lo) (c.hi + c.lo), relative error about 2^-46; the product a.hi c.hi is split
 // exactly with an FMA.
 __device__ __forceinline__ DF df_mul(DF a, const float c[2]) {
-  const float p = a.hi * c[0];
-  float e = fmaf(a.hi, c[0], -p);
-  e = fmaf(a.hi, c[1], e);
-  e = fmaf(a.lo, c[0], e);
+  const float p = __fmul_rn(a.hi, c[0]);
+  float e = __fmaf_rn(a.hi, c[0], -p);
+  e = __fmaf_rn(a.hi, c[1], e);
+  e = __fmaf_rn(a.lo, c[0], e);
   return df_fast_two_sum(p, e);
 }
 
@@ -227,7 +237,7 @@ struct p3m_ctx {
   uint32_t* keys = nullptr;     // [n_max] key of each input particle
   uint32_t* ranks = nullptr;    // [n_max] rank within its cell
   void* recp = nullptr;         // [n_max] sorted positions, cutoff units (2 float4 / Rec64)
-  void* recm = nullptr;         // [n_max] sorted assignment records (float4 / Rec64)
+  void* recm = nullptr;         // [n_max] FP64 path: sorted assignment records (Rec64)
   void* fpp = nullptr;          // [n_max] short-range force + potential, sorted (float4/double4)
   double* acc = nullptr;        // [3 n_max] adjoint accumulator, sorted order
 

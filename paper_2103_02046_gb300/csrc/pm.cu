@@ -144,30 +144,35 @@ __device__ __forceinline__ Axis<T> axis_weights(int order, int c, T f) {
   return a;
 }
 
-__device__ __forceinline__ void load_m(const float4* recm, uint32_t i, float u[3], uint32_t& node) {
-  const float4 r = recm[i];
-  u[0] = r.x;
-  u[1] = r.y;
-  u[2] = r.z;
-  node = __float_as_uint(r.w);
-}
-__device__ __forceinline__ void load_m(const Rec64* recm, uint32_t i, double u[3], uint32_t& node) {
-  const Rec64 r = recm[i];
-  u[0] = r.u[0];
-  u[1] = r.u[1];
-  u[2] = r.u[2];
-  node = static_cast<uint32_t>(r.idx);
+// FP32 path: the assignment node and offset per axis, recomputed from the 32-byte position
+// record (hi + lo in cutoff units) in double-float arithmetic exactly as the sort did, plus the
+// sort's correction near knots (see kRowBits).
+__device__ __forceinline__ void particle_axes(const Geom& g, const float4* __restrict__ recp,
+                                              uint32_t i, Axis<float> ax[3]) {
+  float4 h, l;
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(h.x), "=f"(h.y), "=f"(h.z), "=f"(h.w), "=f"(l.x), "=f"(l.y), "=f"(l.z), "=f"(l.w)
+      : "l"(recp + 2 * static_cast<size_t>(i)));
+  const uint32_t code = __float_as_uint(l.w) >> kRowBits;
+  const float hs[3] = {h.x, h.y, h.z}, ls[3] = {l.x, l.y, l.z};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const DF sm = df_mul(DF{hs[d], ls[d]}, g.rch_df[d]);
+    const float cf = (g.order == 2) ? floorf(sm.hi + 0.5f) : floorf(sm.hi);
+    const float c = cf + static_cast<float>(static_cast<int>((code >> (2 * d)) & 3u) - 1);
+    const float u = __fadd_rn(__fsub_rn(sm.hi, c), sm.lo);  // sm.hi - c is exact
+    ax[d] = axis_weights<float>(g.order, static_cast<int>(c), u);
+  }
 }
 
-template <typename T>
-__device__ __forceinline__ void particle_axes(const Geom& g, const typename RecT<T>::type* recm,
-                                              uint32_t i, Axis<T> ax[3]) {
-  T u[3];
-  uint32_t node;
-  load_m(recm, i, u, node);
-  ax[0] = axis_weights<T>(g.order, static_cast<int>(node & 1023u), u[0]);
-  ax[1] = axis_weights<T>(g.order, static_cast<int>((node >> 10) & 1023u), u[1]);
-  ax[2] = axis_weights<T>(g.order, static_cast<int>(node >> 20), u[2]);
+// FP64 path: offsets and packed node from the assignment record.
+__device__ __forceinline__ void particle_axes(const Geom& g, const Rec64* __restrict__ recm,
+                                              uint32_t i, Axis<double> ax[3]) {
+  const Rec64 r = recm[i];
+  const uint32_t node = static_cast<uint32_t>(r.idx);
+  ax[0] = axis_weights<double>(g.order, static_cast<int>(node & 1023u), r.u[0]);
+  ax[1] = axis_weights<double>(g.order, static_cast<int>((node >> 10) & 1023u), r.u[1]);
+  ax[2] = axis_weights<double>(g.order, static_cast<int>(node >> 20), r.u[2]);
 }
 
 __device__ __forceinline__ long long orig_index(const float4* recp, uint32_t i) {
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(kDepThreads)
     const uint32_t i = b0 + k * kDepThreads + threadIdx.x;
     if (i < N) {
       Axis<T> ax[3];
-      particle_axes<T>(g, recm, i, ax);
+      particle_axes(g, recm, i, ax);
       for (int d = 0; d < 3; ++d) {
         lmin[d] = min(lmin[d], ax[d].c);
         lmax[d] = max(lmax[d], ax[d].c + S - 1);
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(kDepThreads)
     const uint32_t i = b0 + k * kDepThreads + threadIdx.x;
     if (i >= N) continue;
     Axis<T> A[3];
-    particle_axes<T>(g, recm, i, A);
+    particle_axes(g, recm, i, A);
     T wv[3] = {T(0), T(0), T(0)};
     if (kDipole) {
       const long long idx = orig_index(recp, i);
@@ -456,7 +461,7 @@ __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
   Axis<T> ax[3];
-  particle_axes<T>(g, recm, i, ax);
+  particle_axes(g, recm, i, ax);
   if constexpr (sizeof(T) == 4) {
     // FP32 path: long and short range combined in FP32
     float F[3] = {0.f, 0.f, 0.f};
@@ -598,7 +603,7 @@ __global__ void k_vjp_gather(Geom g, const uint32_t* __restrict__ total,
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
   Axis<T> ax[3];
-  particle_axes<T>(g, recm, i, ax);
+  particle_axes(g, recm, i, ax);
   const long long idx = orig_index(recp, i);
   if (pass == 0) {
     T H[3][3];
@@ -696,7 +701,7 @@ void launch_deposit(const p3m_ctx* c, int64_t n) {
   const unsigned blocks = static_cast<unsigned>((n + kDepPerBlock - 1) / kDepPerBlock);
   if (c->fp32)
     k_deposit_tiled<float, false><<<blocks, kDepThreads, 0, c->work>>>(
-        c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp),
+        c->g, total, static_cast<const float4*>(c->recp), static_cast<const float4*>(c->recp),
         nullptr, static_cast<float*>(c->qpad));
   else
     k_deposit_tiled<double, false><<<blocks, kDepThreads, 0, c->work>>>(
@@ -710,7 +715,7 @@ void launch_dipole_deposit(const p3m_ctx* c, int64_t n, const double* w) {
   const unsigned blocks = static_cast<unsigned>((n + kDepPerBlock - 1) / kDepPerBlock);
   if (c->fp32)
     k_deposit_tiled<float, true><<<blocks, kDepThreads, 0, c->work>>>(
-        c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp), w,
+        c->g, total, static_cast<const float4*>(c->recp), static_cast<const float4*>(c->recp), w,
         static_cast<float*>(c->qpad));
   else
     k_deposit_tiled<double, true><<<blocks, kDepThreads, 0, c->work>>>(
@@ -741,7 +746,7 @@ void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts) {
   const double pp_scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc);
   if (c->fp32) {
     k_interp<float><<<blocks_for(n), kThreads, 0, c->work>>>(
-        c->g, total, static_cast<const float4*>(c->recm), static_cast<const float*>(c->freal),
+        c->g, total, static_cast<const float4*>(c->recp), static_cast<const float*>(c->freal),
         c->n_real, c->fpp, parts, static_cast<float>(pp_scale), pp_scale);
     k_unpermute<float><<<blocks_for(n), kThreads, 0, c->work>>>(c->keys, n, c->fpp, f);
   } else {
@@ -757,7 +762,7 @@ void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, d
   const uint32_t* total = c->starts + c->nkeys;
   if (c->fp32)
     k_vjp_gather<float><<<blocks_for(n), kThreads, 0, c->work>>>(
-        c->g, total, static_cast<const float4*>(c->recm), static_cast<const float4*>(c->recp),
+        c->g, total, static_cast<const float4*>(c->recp), static_cast<const float4*>(c->recp),
         static_cast<const float*>(c->freal), c->n_real, w, c->acc, out, pass);
   else
     k_vjp_gather<double><<<blocks_for(n), kThreads, 0, c->work>>>(

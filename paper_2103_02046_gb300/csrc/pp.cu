@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     const float4 pi = rec[2 * ie], li = rec[2 * ie + 1];
     int cnt = 0;
     if (alive) {
-      const uint32_t row = __float_as_uint(li.w);
+      const uint32_t row = __float_as_uint(li.w) & kRowMask;
       const int cy = static_cast<int>(row % static_cast<uint32_t>(g.nc[1]));
       const int cz = static_cast<int>(row / static_cast<uint32_t>(g.nc[1]));
       for (int r = kRowSpan * kRowSpan / 2; r < kRowSpan * kRowSpan; ++r) {

@@ -187,43 +187,40 @@ __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
   if (key == kInvalidKey) return;
   const uint32_t pos = starts[key] + ranks[i];
   keys[i] = pos;  // from here on keys[i] is the sorted position of input particle i
-  int c[3];
   if (kFP32) {
-    // FP32 records from double-float arithmetic: positions in cutoff units as hi + lo (about
-    // 2^-46 relative) and TSC/CIC offsets u = s - node, s = (x - lo) / h. The node comes from
-    // s.hi unless s is within 1e-3 of a point where the node changes; there the exact FP64
-    // coordinate decides, as in the definition.
-    float hi[3], lo[3], u[3];
+    // FP32 record (one 32-byte sector): the position in cutoff units as hi + lo from
+    // double-float arithmetic (about 2^-46 relative), the input index, the row, and per axis
+    // the node correction. The mesh kernels recompute the assignment node from hi + lo
+    // (s = (hi + lo) r_c / h, node floor(s + 1/2) for TSC, floor(s) for CIC); within 1e-3 of a
+    // point where the node changes, the exact FP64 coordinate decides, as in the definition, and
+    // the difference to the recomputed node is stored.
+    float hi[3], lo[3];
+    uint32_t code = 0;
     for (int d = 0; d < 3; ++d) {
       const double v = x[3 * i + d];
       const DF dv = df_sub(df_from_double(v), DF{g.lo_df[d][0], g.lo_df[d][1]});
       const DF xr = df_mul(dv, g.inv_rc_df);
-      const DF sm = df_mul(dv, g.inv_h_df[d]);
       hi[d] = xr.hi;
       lo[d] = xr.lo;
+      const DF sm = df_mul(xr, g.rch_df[d]);
       const float cf = (g.order == 2) ? floorf(sm.hi + 0.5f) : floorf(sm.hi);
       const float kl = (g.order == 2) ? cf - 0.5f : cf;
+      int corr = 0;
       if (fabsf(sm.hi - kl) < 1e-3f || fabsf(sm.hi - kl - 1.f) < 1e-3f) {
         const double se = mesh_coord(g, v, d);
         const double cn = (g.order == 2) ? floor(se + 0.5) : floor(se);
-        u[d] = static_cast<float>(se - cn);
-        c[d] = static_cast<int>(cn);
-      } else {
-        u[d] = (sm.hi - cf) + sm.lo;  // sm.hi - cf is exact
-        c[d] = static_cast<int>(cf);
+        corr = max(-1, min(1, static_cast<int>(cn - static_cast<double>(cf))));
       }
+      code |= static_cast<uint32_t>(corr + 1) << (2 * d);
     }
-    const uint32_t node = pack_node(c[0], c[1], c[2]);
-    // hi and lo together fill one 32-byte sector: a full-sector scattered write. The lo part's
-    // w holds the particle's row (rz * nc_y + ry) as the sort computed it, so the short range
-    // takes its neighbour rows from the same row the sort placed it in.
+    const uint32_t row = key / static_cast<uint32_t>(g.nc[0]);
     float4* r = reinterpret_cast<float4*>(recp) + 2 * static_cast<size_t>(pos);
     r[0] = make_float4(hi[0], hi[1], hi[2], __int_as_float(static_cast<int>(i)));
-    r[1] = make_float4(lo[0], lo[1], lo[2], __uint_as_float(key / static_cast<uint32_t>(g.nc[0])));
-    reinterpret_cast<float4*>(recm)[pos] = make_float4(u[0], u[1], u[2], __uint_as_float(node));
+    r[1] = make_float4(lo[0], lo[1], lo[2], __uint_as_float(row | (code << kRowBits)));
     return;
   }
   double xr[3], u[3];
+  int c[3];
   for (int d = 0; d < 3; ++d) {
     const double v = x[3 * i + d];
     const double dv = v - g.lo[d];
