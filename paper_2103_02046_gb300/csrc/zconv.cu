@@ -82,31 +82,66 @@ __device__ __forceinline__ void dft8(float2 (&u)[8], float sign) {
   u[7] = c_sub(e3, o3);
 }
 
+// dft8 for u_4 .. u_7 = 0: the even and odd 4-point DFTs each have two non-zero inputs.
+__device__ __forceinline__ void dft8_lower_inputs(float2 (&u)[8], float sign) {
+  const float2 x0 = u[0], x1 = u[1], x2 = u[2], x3 = u[3];
+  // E = DFT4(x0, x2, 0, 0), O = DFT4(x1, x3, 0, 0)
+  const float2 e0 = c_add(x0, x2), e2 = c_sub(x0, x2);
+  const float2 e1 = c_add(x0, c_mul_si(x2, sign)), e3 = c_sub(x0, c_mul_si(x2, sign));
+  float2 o0 = c_add(x1, x3), o2 = c_sub(x1, x3);
+  float2 o1 = c_add(x1, c_mul_si(x3, sign)), o3 = c_sub(x1, c_mul_si(x3, sign));
+  const float h = 0.70710678118654752440f;
+  o1 = c_scale(make_float2(o1.x - sign * o1.y, o1.y + sign * o1.x), h);
+  o2 = c_mul_si(o2, sign);
+  o3 = c_scale(make_float2(-o3.x - sign * o3.y, -o3.y + sign * o3.x), h);
+  u[0] = c_add(e0, o0);
+  u[4] = c_sub(e0, o0);
+  u[1] = c_add(e1, o1);
+  u[5] = c_sub(e1, o1);
+  u[2] = c_add(e2, o2);
+  u[6] = c_sub(e2, o2);
+  u[3] = c_add(e3, o3);
+  u[7] = c_sub(e3, o3);
+}
+
 // Shared-memory index with one pad element per 16: a half-warp reading 16 consecutive
 // elements of a column then touches 16 distinct two-bank slots, and the strided stores of the
 // Stockham passes spread over the banks.
 __host__ __device__ __forceinline__ int zpad(int i) { return i + (i >> 4); }
 
+// Pass variants: kGeneral; kFirstHalf, the first pass of a forward transform whose input is
+// zero in its upper half (the zero-padded charge column: inputs r >= R/2 of every butterfly
+// vanish; the first pass has no twiddles); kLastLower, the last pass of an inverse transform
+// of which only outputs below N/2 are kept (those are outputs r < R/2 of every butterfly).
+enum PassKind { kGeneral = 0, kFirstHalf = 1, kLastLower = 2 };
+
 // One Stockham pass of radix R on one column (and, with kTwo, the same pass on a second
 // column), for a transform of length N = 2^logN after passes whose radices multiply to
 // p = 2^logp. Butterfly i (of N / R) reads u_r = x[i + r N/R], applies the twiddles
-// e^{sign 2 pi i r k / (p R)}, k = i mod p, takes the R-point DFT and writes
-// y[(i - k) R + k + r p]. Each thread does 8 / R butterflies; reads and writes are separated
-// by a barrier, so the pass runs in place.
-template <int R, bool kTwo>
+// e^{sign 2 pi i r k / (p R)}, k = i mod p (all 1 when p = 1), takes the R-point DFT and
+// writes y[(i - k) R + k + r p]. Each thread does 8 / R butterflies; reads and writes are
+// separated by a barrier, so the pass runs in place.
+template <int R, bool kTwo, int kKind>
 __device__ __forceinline__ void stockham_pass(float2* a, float2* b, int logN, int logp, int i0,
                                               int tpc, float sign, const float2* __restrict__ tw) {
   constexpr int kB = 8 / R;
   constexpr int kLogR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+  constexpr int kIn = kKind == kFirstHalf ? R / 2 : R;    // inputs that can be non-zero
+  constexpr int kOut = kKind == kLastLower ? R / 2 : R;   // outputs that are kept
   const int T = (1 << logN) >> kLogR;
   float2 u[kB][R], v[kB][R];
 #pragma unroll
   for (int q = 0; q < kB; ++q)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int src = zpad(i0 + q * tpc + r * T);
-      u[q][r] = a[src];
-      if (kTwo) v[q][r] = b[src];
+      if (r < kIn) {
+        const int src = zpad(i0 + q * tpc + r * T);
+        u[q][r] = a[src];
+        if (kTwo) v[q][r] = b[src];
+      } else {
+        u[q][r] = make_float2(0.f, 0.f);
+        if (kTwo) v[q][r] = make_float2(0.f, 0.f);
+      }
     }
   __syncthreads();
   const int p = 1 << logp;
@@ -115,16 +150,23 @@ __device__ __forceinline__ void stockham_pass(float2* a, float2* b, int logN, in
   for (int q = 0; q < kB; ++q) {
     const int i = i0 + q * tpc;
     const int k = i & (p - 1);
+    if (kKind != kFirstHalf && logp > 0) {
 #pragma unroll
-    for (int r = 1; r < R; ++r) {
-      float2 w = tw[(r * k) << tshift];  // e^{-2 pi i r k / (p R)}
-      w.y *= -sign;                       // conjugate for the inverse (sign = +1)
-      u[q][r] = c_mul(u[q][r], w);
-      if (kTwo) v[q][r] = c_mul(v[q][r], w);
+      for (int r = 1; r < R; ++r) {
+        float2 w = tw[(r * k) << tshift];  // e^{-2 pi i r k / (p R)}
+        w.y *= -sign;                       // conjugate for the inverse (sign = +1)
+        u[q][r] = c_mul(u[q][r], w);
+        if (kTwo) v[q][r] = c_mul(v[q][r], w);
+      }
     }
     if constexpr (R == 8) {
-      dft8(u[q], sign);
-      if (kTwo) dft8(v[q], sign);
+      if constexpr (kKind == kFirstHalf) {
+        dft8_lower_inputs(u[q], sign);
+        if (kTwo) dft8_lower_inputs(v[q], sign);
+      } else {
+        dft8(u[q], sign);
+        if (kTwo) dft8(v[q], sign);
+      }
     } else if constexpr (R == 4) {
       dft4(u[q][0], u[q][1], u[q][2], u[q][3], sign);
       if (kTwo) dft4(v[q][0], v[q][1], v[q][2], v[q][3], sign);
@@ -134,7 +176,7 @@ __device__ __forceinline__ void stockham_pass(float2* a, float2* b, int logN, in
     }
     const int j = ((i - k) << kLogR) + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < kOut; ++r) {
       const int dst = zpad(j + r * p);
       a[dst] = u[q][r];
       if (kTwo) b[dst] = v[q][r];
@@ -143,15 +185,36 @@ __device__ __forceinline__ void stockham_pass(float2* a, float2* b, int logN, in
   __syncthreads();
 }
 
-// Full transform of length 2^logN (sign -1 forward, +1 inverse, unnormalised).
-template <bool kTwo>
-__device__ void column_fft(float2* a, float2* b, int logN, int i0, int tpc, float sign,
+template <bool kTwo, int kKind>
+__device__ __forceinline__ void run_pass(int R, float2* a, float2* b, int logN, int logp, int i0,
+                                         int tpc, float sign, const float2* __restrict__ tw) {
+  if (R == 8)
+    stockham_pass<8, kTwo, kKind>(a, b, logN, logp, i0, tpc, sign, tw);
+  else if (R == 4)
+    stockham_pass<4, kTwo, kKind>(a, b, logN, logp, i0, tpc, sign, tw);
+  else
+    stockham_pass<2, kTwo, kKind>(a, b, logN, logp, i0, tpc, sign, tw);
+}
+
+// Forward transform of a column that is zero in its upper half (sign -1), or inverse
+// transform (sign +1) of which only the lower half is kept; unnormalised, length 2^logN >= 64:
+// radix-8 passes, then one radix-4 or radix-2 pass when log2 N is not a multiple of 3.
+template <bool kTwo, bool kForward>
+__device__ void column_fft(float2* a, float2* b, int logN, int i0, int tpc,
                            const float2* __restrict__ tw) {
-  int logp = 0;
-  for (; logp + 3 <= logN; logp += 3)
-    stockham_pass<8, kTwo>(a, b, logN, logp, i0, tpc, sign, tw);
-  if (logN - logp == 2) stockham_pass<4, kTwo>(a, b, logN, logp, i0, tpc, sign, tw);
-  if (logN - logp == 1) stockham_pass<2, kTwo>(a, b, logN, logp, i0, tpc, sign, tw);
+  const float sign = kForward ? -1.f : 1.f;
+  const int npass = (logN + 2) / 3;
+  for (int q = 0, logp = 0; q < npass; ++q) {
+    const int logR = (logN - logp) >= 3 ? 3 : logN - logp;
+    const int R = 1 << logR;
+    if (kForward && q == 0)
+      run_pass<kTwo, kFirstHalf>(R, a, b, logN, logp, i0, tpc, sign, tw);
+    else if (!kForward && q == npass - 1)
+      run_pass<kTwo, kLastLower>(R, a, b, logN, logp, i0, tpc, sign, tw);
+    else
+      run_pass<kTwo, kGeneral>(R, a, b, logN, logp, i0, tpc, sign, tw);
+    logp += logR;
+  }
 }
 
 constexpr int kMulItems = 5;  // multiply items per thread: ceil((N/2 + 1) C / 512) <= 5
@@ -219,7 +282,7 @@ __global__ void __launch_bounds__(kZThreads, 2)
   const int c = tid / tpc, i0 = tid - c * tpc;
   float2* colA = A + c * padN;
   float2* colB = Bz + c * padN;
-  column_fft<false>(colA, nullptr, logN, i0, tpc, -1.f, tw);
+  column_fft<false, true>(colA, nullptr, logN, i0, tpc, tw);
   // Green's-function multiply, kz paired with -kz (the image term reads Q(-kz)); the columns
   // of one kz are adjacent lanes, so the kernel spectra are read along kx
   const float2* fz = dfac + Hx + My;
@@ -253,7 +316,7 @@ __global__ void __launch_bounds__(kZThreads, 2)
     }
   }
   __syncthreads();
-  column_fft<true>(colA, colB, logN, i0, tpc, 1.f, tw);
+  column_fft<true, false>(colA, colB, logN, i0, tpc, tw);
   // store the planes z < n_z of the three difference spectra
   const float2* fx = dfac;
   const float2 fyk = dfac[Hx + ky];
