@@ -38,11 +38,10 @@ FLOPS_PER_PAIR = 37.0  # algorithmic FP32 flops per in-cutoff pair (FFMA = 2, in
 KERNELS_PER_EVAL = 10  # bin, 3 scan passes, scatter, short range, deposit, Green multiply,
                        # interpolation + combination, unpermute (cuFFT's kernels not counted)
 # DRAM bytes (read + write) of one k_pp_f32<12> launch per particle, from an ncu capture of the
-# 2,097,152-particle sphere on a 128^3 mesh (93.08 MB per launch, profiles/k_pp_f32_sphere2m_128.md).
-# The kernel reads each 32-B record about once from DRAM (neighbour runs hit L2; 77 MB read for
-# 67 MB of records) and writes 16 B per particle, part of which is still in L2 when it ends, so
-# its traffic scales with the particle count at fixed density.
-PP_DRAM_BYTES_PER_PARTICLE = 93.076224e6 / 2097152
+# 2,097,152-particle sphere on a 128^3 mesh (125.4 MB per launch, profiles/k_pp_f32_sphere2m_128.md).
+# The kernel reads each 32-B record about once from DRAM (the neighbour runs and the reduction
+# targets stay in L2), so its traffic scales with the particle count at fixed density.
+PP_DRAM_BYTES_PER_PARTICLE = (110.684672e6 + 14.723072e6) / 2097152
 
 
 def parse():
@@ -318,7 +317,9 @@ def run_ours(a, rank, world, local_rank):
         "fp64": {"evals_per_s": fp64_evals, "stage_ms": dict(zip(
             ["bin_sort", "short_range", "deposit", "solve", "interp_combine", "total"], t64))},
         "error": {"fp32_vs_fp64_gpu_rel_l2": err32},
-        "roofline": {"bound": "alu", "kernel": "short range (k_pp<float>)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_pp_f32 (short range)",
+                     "limiter": "L1 data pipe ~92%, issue ~78% (ncu, "
+                                "profiles/k_pp_f32_sphere2m_128.md)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": PP_DRAM_BYTES_PER_PARTICLE * N,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
