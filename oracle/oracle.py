@@ -127,7 +127,7 @@ class Params:
     pm_bc: int = 0                   # 1 = grounded cathode in the long-range solve
     pp_bc: int = 0                   # 1 = cathode images in the short-range sum as well
     z_cathode: float = 0.0
-    influence: int = 0               # 1 = principal-alias optimal factor 1/U^2
+    influence: int = 0               # 1 = principal-alias optimal factor 1/U^2, 2 = alias sum
     q: float = 1e-15
     mass: float = 1e-15 / ELEMENTARY_CHARGE * ELECTRON_MASS
 
@@ -229,11 +229,60 @@ def green_kernels(P: Params):
         Ki[unused] = 0.0
         Ki_hat = _rfftn(Ki) * ke
     if P.influence:
-        U2 = _assignment_spectrum_sq(P)
-        Kf_hat = Kf_hat / U2
+        F = 1.0 / _assignment_spectrum_sq(P) if P.influence == 1 else alias_influence_factor(P)
+        Kf_hat = Kf_hat * F
         if Ki_hat is not None:
-            Ki_hat = Ki_hat / U2
+            Ki_hat = Ki_hat * F
     return Kf_hat, Ki_hat
+
+
+def alias_u2_sum(t, p1: int, mmax: int = 2):
+    """sum_{|m| <= mmax} sinc(t + m)^(2 p1): one axis of the alias sum of U^2 (t = k h / 2 pi,
+    p1 = assignment order + 1); the denominator of eq. (Ghfinal) is the product over axes."""
+    return sum(np.sinc(t + m) ** (2 * p1) for m in range(-mmax, mmax + 1))
+
+
+def alias_influence_factor(P: Params, mmax: int = 2):
+    """Optimal influence function of eq. (Ghfinal) with its alias sums, as a factor on the
+    sampled kernel spectra, on the rfft layout of the doubled mesh:
+
+        F(k) = sum_m U^2(k_m) R(k_m) / [ R(k) (sum_m U^2(k_m))^2 ],   k_m = k + 2 pi m / h,
+
+    |m_d| <= mmax, U(k) = prod_d sinc(k_d h_d / 2)^(p+1) the assignment function (point
+    particles) and R(k) = exp(-|k|^2 / (4 alpha^2)) / |k|^2 the long-range reference kernel (its
+    constant factor cancels). Keeping only m = 0 gives 1/U^2 (influence = 1); F(0) = 1."""
+    nx, ny, nz = P.n
+    Mx, My, Mz = 2 * nx, 2 * ny, 2 * nz
+    p1 = P.assign_order + 1
+    alpha = P.a
+    t = [np.arange(Mx // 2 + 1) / Mx, np.fft.fftfreq(My, 1.0 / My) / My,
+         np.fft.fftfreq(Mz, 1.0 / Mz) / Mz]            # k_d h_d / (2 pi), signed
+    shape = [(1, 1, Mx // 2 + 1), (1, My, 1), (Mz, 1, 1)]
+    num = np.zeros((Mz, My, Mx // 2 + 1))
+    den = np.ones((Mz, My, Mx // 2 + 1))
+    u2 = []   # per axis and alias: U_d^2, exp(-q_d^2 / 4 alpha^2), q_d^2
+    for d in range(3):
+        rows = []
+        for m in range(-mmax, mmax + 1):
+            tm = t[d] + m
+            q = 2.0 * np.pi * tm / P.h[d]
+            rows.append((np.sinc(tm) ** (2 * p1), np.exp(-q * q / (4.0 * alpha * alpha)), q * q))
+        u2.append(rows)
+        den = den * alias_u2_sum(t[d], p1, mmax).reshape(shape[d])
+    for mz in u2[2]:
+        for my in u2[1]:
+            for mx in u2[0]:
+                w = (mx[0] * mx[1]).reshape(shape[0]) * (my[0] * my[1]).reshape(shape[1]) * \
+                    (mz[0] * mz[1]).reshape(shape[2])
+                q2 = mx[2].reshape(shape[0]) + my[2].reshape(shape[1]) + mz[2].reshape(shape[2])
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    num = num + np.where(q2 > 0.0, w / q2, 0.0)
+    q2 = sum(u2[d][mmax][2].reshape(shape[d]) for d in range(3))
+    rk = np.exp(-q2 / (4.0 * alpha * alpha))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        F = num * q2 / (rk * den * den)
+    F[0, 0, 0] = 1.0   # limit k -> 0: the m = 0 term dominates, every other U(k_m) vanishes
+    return F
 
 
 def _assignment_spectrum_sq(P: Params):
