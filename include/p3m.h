@@ -65,7 +65,9 @@ typedef struct p3m_params {
   int32_t pp_bc;         /* 0 = short range in free space (the paper's prescription),
                             1 = cathode images also in the short-range sum */
   double z_cathode;      /* cathode plane z [m] (eq. (symmetry_planar_cathode) at z = z_cathode) */
-  int32_t influence;     /* 0 = sampled G^L, 1 = principal-alias optimal factor (Sec. 3.1.2) */
+  int32_t influence;     /* 0 = sampled G^L; optimal influence function of eq. (Ghfinal) as a
+                            factor on the sampled kernels: 1 = principal alias only (1/U^2),
+                            2 = alias sums over |m_d| <= 2 (computed once in p3m_create) */
   int32_t precision;     /* p3m_precision */
   int32_t deterministic; /* reserved, must be 0 */
   int32_t adj_slots;     /* checkpoint slots for p3m_backward (0 disables the reverse pass) */

@@ -50,7 +50,7 @@ p3m_status validate(const p3m_params* p, std::string* why) {
   if (p->assign_order != 1 && p->assign_order != 2) { *why = "assign_order must be 1 or 2"; return P3M_EINVAL; }
   if ((p->pm_bc != 0 && p->pm_bc != 1) || (p->pp_bc != 0 && p->pp_bc != 1)) { *why = "pm_bc/pp_bc must be 0 or 1"; return P3M_EINVAL; }
   if (!std::isfinite(p->z_cathode)) { *why = "z_cathode must be finite"; return P3M_EINVAL; }
-  if (p->influence != 0 && p->influence != 1) { *why = "influence must be 0 or 1"; return P3M_EINVAL; }
+  if (p->influence < 0 || p->influence > 2) { *why = "influence must be 0, 1 or 2"; return P3M_EINVAL; }
   if (p->precision != P3M_FP64 && p->precision != P3M_FP32_MIXED) { *why = "precision must be 0 or 1"; return P3M_EINVAL; }
   if (p->deterministic != 0) { *why = "deterministic must be 0"; return P3M_EINVAL; }
   if (p->adj_slots < 0 || p->adj_segment < 0 || (p->adj_slots > 0 && p->adj_segment < 1)) { *why = "adj_slots/adj_segment invalid"; return P3M_EINVAL; }

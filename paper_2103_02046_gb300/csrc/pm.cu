@@ -78,6 +78,43 @@ __device__ double infl_factor(const Geom& g, int kx, int ky, int kz) {
   return 1.0 / (U * U);
 }
 
+// Optimal influence function of eq. (Ghfinal) with its alias sums, as a factor on the sampled
+// kernel spectra: sum_m U^2(k_m) R(k_m) / [R(k) (sum_m U^2(k_m))^2], k_m = k + 2 pi m / h,
+// |m_d| <= 2, U = prod_d sinc(k_d h_d / 2)^(order + 1), R(k) = e^{-k^2 / (4 alpha^2)} / k^2;
+// 1 at k = 0. Computed once per context, in FP64.
+constexpr int kAlias = 2;
+__device__ double alias_factor(const Geom& g, int kx, int ky, int kz) {
+  const int kk[3] = {kx, ky < g.M[1] / 2 + 1 ? ky : ky - g.M[1],
+                     kz < g.M[2] / 2 + 1 ? kz : kz - g.M[2]};
+  if (kk[0] == 0 && kk[1] == 0 && kk[2] == 0) return 1.0;
+  const double pi = 3.14159265358979323846;
+  const double inv4a2 = 1.0 / (4.0 * g.alpha * g.alpha);
+  double a[3][2 * kAlias + 1], q2[3][2 * kAlias + 1], den = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    double su = 0.0;
+    for (int m = -kAlias; m <= kAlias; ++m) {
+      const double t = static_cast<double>(kk[d]) / g.M[d] + m;
+      const double sc = (t == 0.0) ? 1.0 : sinpi(t) / (pi * t);
+      double u2 = 1.0;
+      for (int o = 0; o <= g.order; ++o) u2 *= sc * sc;
+      const double q = 2.0 * pi * t / g.h[d];
+      q2[d][m + kAlias] = q * q;
+      a[d][m + kAlias] = u2 * exp(-q * q * inv4a2);
+      su += u2;
+    }
+    den *= su;
+  }
+  double num = 0.0;
+  for (int mz = 0; mz <= 2 * kAlias; ++mz)
+    for (int my = 0; my <= 2 * kAlias; ++my)
+      for (int mx = 0; mx <= 2 * kAlias; ++mx) {
+        const double qq = q2[0][mx] + q2[1][my] + q2[2][mz];  // > 0 since k != 0
+        num += a[0][mx] * a[1][my] * a[2][mz] / qq;
+      }
+  const double qk = q2[0][kAlias] + q2[1][kAlias] + q2[2][kAlias];
+  return num * qk / (exp(-qk * inv4a2) * den * den);
+}
+
 template <typename T>
 __global__ void k_finish_kernels(Geom g, const double2* __restrict__ Sf,
                                  const double2* __restrict__ Si, T* __restrict__ kf,
@@ -91,7 +128,8 @@ __global__ void k_finish_kernels(Geom g, const double2* __restrict__ Sf,
   const int ky = static_cast<int>((idx / Hx) % g.M[1]);
   const int kz = static_cast<int>(idx / (static_cast<size_t>(Hx) * g.M[1]));
   double sc = scale;
-  if (influence) sc *= infl_factor(g, kx, ky, kz);
+  if (influence == 1) sc *= infl_factor(g, kx, ky, kz);
+  if (influence == 2) sc *= alias_factor(g, kx, ky, kz);
   kf[idx] = static_cast<T>(Sf[idx].x * sc);  // the free kernel is even in every axis: real spectrum
   if (Si) {
     // fold the phase of the z-reversal: Qrev^(k) = e^{-2 pi i kz (nz - 1)/Mz} Q^(kx, ky, -kz)

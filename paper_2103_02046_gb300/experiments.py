@@ -3,6 +3,7 @@
   python -m paper_2103_02046_gb300.experiments boundary   # cathode BC in the short range vs mesh error
   python -m paper_2103_02046_gb300.experiments energy     # leapfrog energy drift and momentum
   python -m paper_2103_02046_gb300.experiments gradient   # adjoint gradient vs finite differences
+  python -m paper_2103_02046_gb300.experiments influence  # P3M error vs exact Coulomb per kernel
 
 Each prints one JSON line. Everything runs through the C ABI (``p3m``); no oracle is used.
 
@@ -169,12 +170,69 @@ def gradient(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps:
             "precision": precision, "J": J0, "directions": res, "seconds_gradient": t_grad}
 
 
+def _coulomb_direct(x, targets, q, z_cathode=None, chunk=8):
+    """Exact Coulomb force on the particles `targets` from all of x (FP64, torch on the GPU), with
+    the grounded-plane images (charge -q at the mirror point) when z_cathode is given."""
+    k_e = 8.9875517923e9
+    out = torch.zeros((len(targets), 3), dtype=torch.float64, device=x.device)
+    for a in range(0, len(targets), chunk):
+        t = x[targets[a:a + chunk]]
+        d = t[:, None, :] - x[None, :, :]
+        r2 = (d * d).sum(-1)
+        r2[r2 == 0] = float("inf")            # the particle itself
+        out[a:a + chunk] = k_e * q * q * (d / r2[..., None] ** 1.5).sum(1)
+        if z_cathode is not None:
+            xi = x.clone()
+            xi[:, 2] = 2.0 * z_cathode - xi[:, 2]
+            d = t[:, None, :] - xi[None, :, :]
+            r2 = (d * d).sum(-1)
+            out[a:a + chunk] -= k_e * q * q * (d / r2[..., None] ** 1.5).sum(1)
+    return out
+
+
+def influence(precision: int = m.FP64, n_particles: int = 0):
+    """P3M force error against the exact Coulomb force (with images) for the plain sampled
+    kernel (influence 0), the principal-alias optimal factor (1) and the alias sums of
+    eq. (Ghfinal) (2): the 4096-particle Gaussian above the cathode (16^3 mesh, all particles)
+    and the 4,194,304-particle core + halo bunch (128^3, r_c = 3h, 2048 sampled targets)."""
+    out = {"experiment": "influence", "precision": precision, "cases": []}
+    g4 = B.lift_to_plane(B.gaussian(4096, (1e-3, 1e-3, 1e-3), 0), 0.0, 0.15e-3)
+    halo = dict(B.WORKLOADS["halo4m"])
+    x5 = B.positions(halo, 4_194_304)
+    h128 = m.auto_mesh(_cuda(x5), m.Params(n=(128,) * 3)).h[2]
+    x5 = B.lift_to_plane(x5, 0.0, h128)
+    for name, x, n, rc, sample in (("gauss4096_cathode_16", g4, 16, 2.0, None),
+                                   ("halo4m_cathode_128", x5, 128, 3.0, 2048)):
+        xg = _cuda(x)
+        targets = (torch.arange(len(x), device="cuda") if sample is None else
+                   torch.from_numpy(B.subsample(len(x), sample, seed=12345)).cuda())
+        case = {"case": name, "n": len(x), "mesh": n, "targets": len(targets), "rel_l2": {}}
+        exact = None
+        for infl in (0, 1, 2):
+            prm = m.auto_mesh(xg, m.Params(n=(n,) * 3, rc_over_h=rc, pm_bc=1, z_cathode=0.0,
+                                           influence=infl, precision=precision))
+            t0 = time.time()
+            ctx = m.Context(prm, len(x))
+            ctx.sync()
+            t_create = time.time() - t0
+            f = ctx.forces(xg)
+            ctx.sync()
+            ctx.close()
+            if exact is None:
+                exact = _coulomb_direct(xg, targets, prm.q, z_cathode=0.0)
+            case["rel_l2"][infl] = _rel(f[targets], exact)
+            case[f"create_s_{infl}"] = t_create
+        out["cases"].append(case)
+    return out
+
+
 def main(argv):
     which = argv[1] if len(argv) > 1 else "boundary"
     kw = {"precision": m.FP64 if "--fp64" in argv else m.FP32_MIXED}
     if "--n" in argv:
         kw["n_particles"] = int(argv[argv.index("--n") + 1])
-    fn = {"boundary": boundary, "energy": energy, "gradient": gradient}[which]
+    fn = {"boundary": boundary, "energy": energy, "gradient": gradient,
+          "influence": influence}[which]
     print(json.dumps(fn(**kw)), flush=True)
 
 

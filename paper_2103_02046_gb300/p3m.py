@@ -121,7 +121,7 @@ class Params:
     pm_bc: int = 0
     pp_bc: int = 0
     z_cathode: float = 0.0
-    influence: int = 0
+    influence: int = 0  # 0 sampled kernel, 1 principal alias 1/U^2, 2 alias sums (eq. (Ghfinal))
     precision: int = FP64
     deterministic: int = 0
     adj_slots: int = 0

@@ -58,6 +58,9 @@ CASES = [
     ("open_tsc_32", 32, 0, 0, 2, 0),
     ("cathode_pp_bc_aniso_z64", (20, 24, 64), 1, 1, 2, 0),
     ("cathode_cic_influence_32", 32, 1, 0, 1, 1),
+    # optimal influence function with its alias sums, on the cuFFT and the fused z solve
+    ("cathode_alias_influence", 16, 1, 0, 2, 2),
+    ("open_alias_influence_32", 32, 0, 0, 2, 2),
 ]
 
 
@@ -216,7 +219,8 @@ def test_edge_cases():
 def test_invalid_params_refused():
     m = p3m()
     for bad in (dict(n=(4, 16, 16)), dict(assign_order=3), dict(h=(0.0, 1e-5, 1e-5)),
-                dict(precision=7), dict(q=0.0), dict(rc_over_h=0.2)):
+                dict(precision=7), dict(q=0.0), dict(rc_over_h=0.2),
+                dict(influence=3)):
         with pytest.raises(m.P3MError) as ei:
             m.Context(m.Params(**bad), 10)
         assert ei.value.status == m.P3M_EINVAL
