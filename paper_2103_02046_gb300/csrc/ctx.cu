@@ -182,6 +182,7 @@ PairPoly fit_pair_poly(double kappa) {
     if (err < 2e-7) break;
   }
   pp.kappa2_log2e = static_cast<float>(kappa * kappa * 1.4426950408889634);
+  pp.kappa2 = static_cast<float>(kappa * kappa);
   pp.c2k = static_cast<float>(2.0 * kappa / std::sqrt(kPi));
   return pp;
 }

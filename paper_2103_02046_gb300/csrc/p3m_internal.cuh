@@ -159,6 +159,7 @@ struct PairPoly {
   int deg;
   float c[kMaxPoly];
   float kappa2_log2e;  // kappa_eff^2 log2(e): e^{-kappa^2 rho^2} = 2^{-kappa2_log2e rho^2}
+  float kappa2;        // kappa_eff^2
   float c2k;           // 2 kappa_eff / sqrt(pi)
   float max_abs_err;   // fit error of erfc over [0, kappa_eff] (reported, not used)
 };

@@ -637,7 +637,8 @@ __global__ void k_vjp_gather(Geom g, const uint32_t* __restrict__ total,
                              const typename RecT<T>::type* __restrict__ recp,
                              const T* __restrict__ field, size_t nreal,
                              const double* __restrict__ w, double* __restrict__ acc,
-                             double* __restrict__ out, int pass) {
+                             double* __restrict__ out, int pass,
+                             const float4* __restrict__ pp_vjp, double pp_scale) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
   Axis<T> ax[3];
@@ -650,10 +651,20 @@ __global__ void k_vjp_gather(Geom g, const uint32_t* __restrict__ total,
     else
       hess_from_phi(g, field, ax, H);
     const double wv[3] = {w[3 * idx], w[3 * idx + 1], w[3 * idx + 2]};
+    // short-range part: already in acc (FP64 path) or, FP32 path, in pp_vjp (cutoff units)
+    double sr[3] = {0.0, 0.0, 0.0};
+    if (pp_vjp) {
+      const float4 v = pp_vjp[i];
+      sr[0] = pp_scale * v.x;
+      sr[1] = pp_scale * v.y;
+      sr[2] = pp_scale * v.z;
+    } else {
+      for (int d = 0; d < 3; ++d) sr[d] = acc[3 * i + d];
+    }
     for (int d = 0; d < 3; ++d) {
       double hw = 0.0;
       for (int e = 0; e < 3; ++e) hw += static_cast<double>(H[d][e]) * (g.inv_h[d] * g.inv_h[e]) * wv[e];
-      acc[3 * i + d] += -g.q * hw;
+      acc[3 * i + d] = sr[d] - g.q * hw;
     }
   } else {
     T G[3];
@@ -801,11 +812,13 @@ void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, d
   if (c->fp32)
     k_vjp_gather<float><<<blocks_for(n), kThreads, 0, c->work>>>(
         c->g, total, static_cast<const float4*>(c->recp), static_cast<const float4*>(c->recp),
-        static_cast<const float*>(c->freal), c->n_real, w, c->acc, out, pass);
+        static_cast<const float*>(c->freal), c->n_real, w, c->acc, out, pass,
+        static_cast<const float4*>(c->fpp),
+        c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc * c->g.rc));
   else
     k_vjp_gather<double><<<blocks_for(n), kThreads, 0, c->work>>>(
         c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp),
-        static_cast<const double*>(c->phireal), c->n_real, w, c->acc, out, pass);
+        static_cast<const double*>(c->phireal), c->n_real, w, c->acc, out, pass, nullptr, 0.0);
 }
 
 void launch_get_mesh(const p3m_ctx* c, int which, double* out) {

@@ -105,11 +105,8 @@ __device__ __forceinline__ void for_rows(const Geom& g, const uint32_t* __restri
 }
 
 // ------------------------------------------------------------------------------------------
-// Position access: FP32 hi (+ lo remainder on demand), FP64 exact.
+// Position access for the FP64 adjoint kernel.
 // ------------------------------------------------------------------------------------------
-struct PosF {
-  const float4* __restrict__ r;  // [2 n]: hi parts at 2j (w = index bits), lo parts at 2j + 1
-};
 struct PosD {
   const Rec64* __restrict__ r;
 };
@@ -336,6 +333,170 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
 }
 
 // ------------------------------------------------------------------------------------------
+// FP32 vector-Jacobian product of the short-range force map, each unordered pair once: for a
+// pair (i, j), j > i, with d = xi_i - xi_j and H(d) = fco(rho) I + dfr(rho) d d^T (the pair
+// energy's Hessian, even in d), i gets H(d) (w_i - w_j) and j gets its negative. Same walk as
+// k_pp_f32 (persistent blocks, runs in shared memory, 256-bit record loads); w in sorted
+// order as float4 (ws). The result goes to acc4 (zeroed, cutoff units); image pairs (pp_bc)
+// act on i only: acc_i -= H(d)(w_i - S w_j), d = xi_i - S xi_j.
+// ------------------------------------------------------------------------------------------
+template <int kDeg>
+__device__ __forceinline__ void pair_hess_poly(const PairPoly& P, float r2, float& fco,
+                                               float& dfr) {
+  const float rinv = rsqrtf(r2);
+  const float rho = r2 * rinv;
+  const float t = fmaf(2.f, rho, -1.f);
+  float R = P.c[kDeg];
+#pragma unroll
+  for (int m = kDeg - 1; m >= 0; --m) R = fmaf(R, t, P.c[m]);
+  const float ex = exp2f(-P.kappa2_log2e * r2);
+  const float pot = R * ex * rinv;           // erfc(kappa rho) / rho
+  const float cex = P.c2k * ex;
+  const float A = pot + cex;                 // rho^2 times the force coefficient
+  const float rinv2 = rinv * rinv;
+  fco = A * rinv2;
+  // dA/drho = -c2k e/rho - erfc/rho^2 - 2 kappa^2 rho c2k e; dfr = (dA/rho^2 - 2 A/rho^3)/rho
+  const float dA = -(cex + pot) * rinv - 2.f * P.kappa2 * rho * cex;
+  dfr = (dA - 2.f * A * rinv) * rinv2 * rinv;
+}
+
+template <int kDeg>
+__global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
+    k_pp_vjp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
+                 const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
+                 const float4* __restrict__ ws, float4* __restrict__ acc4,
+                 uint32_t* __restrict__ next_tile) {
+  __shared__ uint32_t run_j0[kHalfRows][kThreads], run_j1[kHalfRows][kThreads];
+  __shared__ uint32_t tile_s;
+  const int tid = threadIdx.x;
+  const uint32_t N = *total;
+  for (;;) {
+    if (tid == 0) tile_s = atomicAdd(next_tile, 1u);
+    __syncthreads();
+    const uint32_t tile = tile_s;
+    __syncthreads();
+    if (static_cast<uint64_t>(tile) * kThreads >= N) break;
+    const uint32_t i = tile * kThreads + tid;
+    const bool alive = i < N;
+    const uint32_t ie = alive ? i : 0u;
+    const float4 pi = rec[2 * ie], li = rec[2 * ie + 1];
+    const float4 wi = ws[ie];
+    int cnt = 0;
+    if (alive) {
+      const uint32_t row = __float_as_uint(li.w) & kRowMask;
+      const int cy = static_cast<int>(row % static_cast<uint32_t>(g.nc[1]));
+      const int cz = static_cast<int>(row / static_cast<uint32_t>(g.nc[1]));
+      for (int r = kRowSpan * kRowSpan / 2; r < kRowSpan * kRowSpan; ++r) {
+        uint32_t j0, j1;
+        row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
+        j0 = max(j0, i + 1);
+        if (j0 < j1) {
+          run_j0[cnt][tid] = j0;
+          run_j1[cnt][tid] = j1;
+          ++cnt;
+        }
+      }
+    }
+    uint32_t ptr = 0, end = 0;
+    if (cnt > 0) {
+      ptr = run_j0[0][tid];
+      end = run_j1[0][tid];
+    }
+    int k = 0;
+    Acc2 sum[3];
+    for (int c = 0; c < 3; ++c) sum[c].hi = sum[c].lo = 0.f;
+    float part[3] = {0.f, 0.f, 0.f};
+    auto pair = [&](bool hit, float r2, float rx, float ry, float rz, uint32_t j) {
+      float fco, dfr;
+      pair_hess_poly<kDeg>(P, hit ? r2 : 0.5f, fco, dfr);
+      const float4 wj = ws[hit ? j : ie];
+      const float v0 = wi.x - wj.x, v1 = wi.y - wj.y, v2 = wi.z - wj.z;
+      const float dv = hit ? dfr * (rx * v0 + ry * v1 + rz * v2) : 0.f;
+      fco = hit ? fco : 0.f;
+      const float c0 = fmaf(fco, v0, dv * rx), c1 = fmaf(fco, v1, dv * ry),
+                  c2 = fmaf(fco, v2, dv * rz);
+      part[0] += c0;
+      part[1] += c1;
+      part[2] += c2;
+      if (hit) red_add_v4(acc4 + j, -c0, -c1, -c2, 0.f);
+    };
+    int step = 0;
+    while (__any_sync(0xffffffffu, ptr < end)) {
+      const bool va = ptr < end, vb = ptr + 1 < end;
+      const float4* pa = va ? rec + 2 * static_cast<size_t>(ptr) : rec;
+      const float4* pb = vb ? rec + 2 * static_cast<size_t>(ptr + 1) : rec;
+      float4 ha, la, hb, lb;
+      load_rec32(pa, ha, la);
+      load_rec32(pb, hb, lb);
+      const float ax = (pi.x - ha.x) + (li.x - la.x), ay = (pi.y - ha.y) + (li.y - la.y),
+                  az = (pi.z - ha.z) + (li.z - la.z);
+      const float bx = (pi.x - hb.x) + (li.x - lb.x), by = (pi.y - hb.y) + (li.y - lb.y),
+                  bz = (pi.z - hb.z) + (li.z - lb.z);
+      const float ra = ax * ax + ay * ay + az * az, rb = bx * bx + by * by + bz * bz;
+      const bool hita = va && ra < 1.f && ra > 0.f;
+      const bool hitb = vb && rb < 1.f && rb > 0.f;
+      if (__any_sync(0xffffffffu, hita)) pair(hita, ra, ax, ay, az, ptr);
+      if (__any_sync(0xffffffffu, hitb)) pair(hitb, rb, bx, by, bz, ptr + 1);
+      ptr += 2;
+      if (ptr >= end && ++k < cnt) {
+        ptr = run_j0[k][tid];
+        end = run_j1[k][tid];
+      }
+      if ((++step & 7) == 0) {
+        for (int c = 0; c < 3; ++c) {
+          sum[c].add(part[c]);
+          part[c] = 0.f;
+        }
+      }
+    }
+    for (int c = 0; c < 3; ++c) sum[c].add(part[c]);
+    if (alive && g.pp_bc) {
+      const double zi = static_cast<double>(pi.z) + static_cast<double>(li.z);
+      if (zi - 0.5 * g.img_c < 1.0) {
+        const float mz = static_cast<float>(g.img_c - zi);
+        const float ch = static_cast<float>(g.img_c);
+        const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
+        for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t ja, uint32_t jb) {
+          float rowv[3] = {0.f, 0.f, 0.f};
+          for (uint32_t jj = ja; jj < jb; ++jj) {
+            const float4 hj = rec[2 * jj], lj = rec[2 * jj + 1];
+            const float ax = (pi.x - hj.x) + (li.x - lj.x);
+            const float ay = (pi.y - hj.y) + (li.y - lj.y);
+            const float s = pi.z + hj.z;
+            const float bp = s - pi.z;
+            const float e = (pi.z - (s - bp)) + (hj.z - bp);
+            const float az = ((s - ch) + e) + ((li.z + lj.z) - cl);
+            const float r2 = ax * ax + ay * ay + az * az;
+            if (r2 < 1.f && r2 > 0.f) {
+              float fco, dfr;
+              pair_hess_poly<kDeg>(P, r2, fco, dfr);
+              const float4 wj = ws[jj];
+              const float v0 = wi.x - wj.x, v1 = wi.y - wj.y, v2 = wi.z + wj.z;  // w_i - S w_j
+              const float dv = dfr * (ax * v0 + ay * v1 + az * v2);
+              rowv[0] -= fmaf(fco, v0, dv * ax);
+              rowv[1] -= fmaf(fco, v1, dv * ay);
+              rowv[2] -= fmaf(fco, v2, dv * az);
+            }
+          }
+          for (int c = 0; c < 3; ++c) sum[c].add(rowv[c]);
+        });
+      }
+    }
+    if (alive) red_add_v4(acc4 + i, sum[0].value(), sum[1].value(), sum[2].value(), 0.f);
+  }
+}
+
+// w (input order, FP64) -> ws (sorted order, float4): the weights the FP32 VJP pairs read.
+__global__ void k_gather_w(const uint32_t* __restrict__ total, const float4* __restrict__ rec,
+                           const double* __restrict__ w, float4* __restrict__ ws) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *total) return;
+  const long long idx = __float_as_int(rec[2 * i].w);
+  ws[i] = make_float4(static_cast<float>(w[3 * idx]), static_cast<float>(w[3 * idx + 1]),
+                      static_cast<float>(w[3 * idx + 2]), 0.f);
+}
+
+// ------------------------------------------------------------------------------------------
 // FP64 short range: each unordered pair once, as in the FP32 kernel: particle i takes the pairs
 // with j > i in sorted order (every one of the 25 neighbour rows is clipped to j > i, so this
 // holds however the row of i was rounded) and adds the reaction to j with FP64 reductions into
@@ -485,102 +646,61 @@ __device__ __forceinline__ void pair_hess(T r2, T kappa, T c2k, T& fco, T& dfr) 
   dfr = (dA / r2 - T(2) * A / (r2 * r)) / r;
 }
 
-template <typename T, typename Pos>
+// FP64 vector-Jacobian product of the short-range force map (every ordered pair, one thread
+// per particle): acc_i = scale sum_j H(d_ij) (w_i - w_j) - scale sum_j H(d_ij') (w_i - S w_j)
+// over image pairs (pp_bc).
 __global__ void __launch_bounds__(kThreads)
-    k_pp_vjp(Geom g, const uint32_t* __restrict__ total, Pos pos,
+    k_pp_vjp(Geom g, const uint32_t* __restrict__ total, PosD pos,
              const uint32_t* __restrict__ starts, const double* __restrict__ w,
              double* __restrict__ acc, double scale) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
-  const T kappa = static_cast<T>(g.kappa_eff);
-  const T c2k = static_cast<T>(2.0 * g.kappa_eff * 0.56418958354775628695);
-  T pi[3], li[3] = {T(0), T(0), T(0)};
-  long long idx;
-  if constexpr (sizeof(T) == 4) {
-    const float4 h = pos.r[2 * i], l = pos.r[2 * i + 1];
-    pi[0] = h.x; pi[1] = h.y; pi[2] = h.z;
-    li[0] = l.x; li[1] = l.y; li[2] = l.z;
-    idx = __float_as_int(h.w);
-  } else {
-    const Rec64 r = pos.r[i];
-    pi[0] = r.u[0]; pi[1] = r.u[1]; pi[2] = r.u[2];
-    idx = r.idx;
-  }
-  const T wi[3] = {static_cast<T>(w[3 * idx]), static_cast<T>(w[3 * idx + 1]),
-                   static_cast<T>(w[3 * idx + 2])};
+  const double kappa = g.kappa_eff;
+  const double c2k = 2.0 * g.kappa_eff * 0.56418958354775628695;
+  const Rec64 me = pos.r[i];
+  const double pi[3] = {me.u[0], me.u[1], me.u[2]};
+  const long long idx = me.idx;
+  const double wi[3] = {w[3 * idx], w[3 * idx + 1], w[3 * idx + 2]};
   double out[3] = {0.0, 0.0, 0.0};
-  auto sep = [&](uint32_t j, bool image, T& rx, T& ry, T& rz, long long& jdx) {
-    if constexpr (sizeof(T) == 4) {
-      const float4 hj = pos.r[2 * j], lj = pos.r[2 * j + 1];
-      jdx = __float_as_int(hj.w);
-      rx = (pi[0] - hj.x) + (li[0] - lj.x);
-      ry = (pi[1] - hj.y) + (li[1] - lj.y);
-      if (!image) {
-        rz = (pi[2] - hj.z) + (li[2] - lj.z);
-      } else {
-        const float ch = static_cast<float>(g.img_c);
-        const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
-        const float s = pi[2] + hj.z;
-        const float bp = s - pi[2];
-        const float e = (pi[2] - (s - bp)) + (hj.z - bp);
-        rz = ((s - ch) + e) + ((li[2] + lj.z) - cl);
-      }
-    } else {
-      const Rec64 rj = pos.r[j];
-      jdx = rj.idx;
-      rx = pi[0] - rj.u[0];
-      ry = pi[1] - rj.u[1];
-      rz = image ? pi[2] + rj.u[2] - static_cast<T>(g.img_c) : pi[2] - rj.u[2];
-    }
-  };
-  for_rows<T>(g, starts, pi[0], pi[1], pi[2], [&](uint32_t j0, uint32_t j1) {
-    T row[3] = {T(0), T(0), T(0)};
+  for_rows<double>(g, starts, pi[0], pi[1], pi[2], [&](uint32_t j0, uint32_t j1) {
     for (uint32_t j = j0; j < j1; ++j) {
       if (j == i) continue;
-      T rx, ry, rz;
-      long long jdx;
-      sep(j, false, rx, ry, rz, jdx);
-      const T r2 = rx * rx + ry * ry + rz * rz;
-      if (r2 < T(1) && r2 > T(0)) {
-        T fco, dfr;
+      const Rec64 rj = pos.r[j];
+      const double rx = pi[0] - rj.u[0], ry = pi[1] - rj.u[1], rz = pi[2] - rj.u[2];
+      const double r2 = rx * rx + ry * ry + rz * rz;
+      if (r2 < 1.0 && r2 > 0.0) {
+        double fco, dfr;
         pair_hess(r2, kappa, c2k, fco, dfr);
-        const T v0 = wi[0] - static_cast<T>(w[3 * jdx]);
-        const T v1 = wi[1] - static_cast<T>(w[3 * jdx + 1]);
-        const T v2 = wi[2] - static_cast<T>(w[3 * jdx + 2]);
-        const T dv = rx * v0 + ry * v1 + rz * v2;
-        row[0] += fco * v0 + dfr * dv * rx;
-        row[1] += fco * v1 + dfr * dv * ry;
-        row[2] += fco * v2 + dfr * dv * rz;
+        const double v0 = wi[0] - w[3 * rj.idx];
+        const double v1 = wi[1] - w[3 * rj.idx + 1];
+        const double v2 = wi[2] - w[3 * rj.idx + 2];
+        const double dv = rx * v0 + ry * v1 + rz * v2;
+        out[0] += fco * v0 + dfr * dv * rx;
+        out[1] += fco * v1 + dfr * dv * ry;
+        out[2] += fco * v2 + dfr * dv * rz;
       }
     }
-    for (int d = 0; d < 3; ++d) out[d] += static_cast<double>(row[d]);
   });
-  if (g.pp_bc) {
-    const double zi = static_cast<double>(pi[2]) + static_cast<double>(li[2]);
-    if (zi - 0.5 * g.img_c < 1.0) {
-      const T mz = static_cast<T>(g.img_c - zi);
-      for_rows<T>(g, starts, pi[0], pi[1], mz, [&](uint32_t j0, uint32_t j1) {
-        T row[3] = {T(0), T(0), T(0)};
-        for (uint32_t j = j0; j < j1; ++j) {
-          T rx, ry, rz;
-          long long jdx;
-          sep(j, true, rx, ry, rz, jdx);
-          const T r2 = rx * rx + ry * ry + rz * rz;
-          if (r2 < T(1) && r2 > T(0)) {
-            T fco, dfr;
-            pair_hess(r2, kappa, c2k, fco, dfr);
-            const T v0 = wi[0] - static_cast<T>(w[3 * jdx]);
-            const T v1 = wi[1] - static_cast<T>(w[3 * jdx + 1]);
-            const T v2 = wi[2] + static_cast<T>(w[3 * jdx + 2]);  // w_i - S w_j
-            const T dv = rx * v0 + ry * v1 + rz * v2;
-            row[0] -= fco * v0 + dfr * dv * rx;
-            row[1] -= fco * v1 + dfr * dv * ry;
-            row[2] -= fco * v2 + dfr * dv * rz;
-          }
+  if (g.pp_bc && pi[2] - 0.5 * g.img_c < 1.0) {
+    for_rows<double>(g, starts, pi[0], pi[1], g.img_c - pi[2], [&](uint32_t j0, uint32_t j1) {
+      for (uint32_t j = j0; j < j1; ++j) {
+        const Rec64 rj = pos.r[j];
+        const double rx = pi[0] - rj.u[0], ry = pi[1] - rj.u[1];
+        const double rz = pi[2] + rj.u[2] - g.img_c;
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        if (r2 < 1.0 && r2 > 0.0) {
+          double fco, dfr;
+          pair_hess(r2, kappa, c2k, fco, dfr);
+          const double v0 = wi[0] - w[3 * rj.idx];
+          const double v1 = wi[1] - w[3 * rj.idx + 1];
+          const double v2 = wi[2] + w[3 * rj.idx + 2];  // w_i - S w_j
+          const double dv = rx * v0 + ry * v1 + rz * v2;
+          out[0] -= fco * v0 + dfr * dv * rx;
+          out[1] -= fco * v1 + dfr * dv * ry;
+          out[2] -= fco * v2 + dfr * dv * rz;
         }
-        for (int d = 0; d < 3; ++d) out[d] += static_cast<double>(row[d]);
-      });
-    }
+      }
+    });
   }
   acc[3 * i] = scale * out[0];
   acc[3 * i + 1] = scale * out[1];
@@ -630,15 +750,38 @@ void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s)
   if (n == 0) return;
   const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   const uint32_t* total = c->starts + c->nkeys;
-  // d/dxi of (k_e q^2 / r_c^2) f(rho): one more factor 1/r_c
-  const double scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc * c->g.rc);
-  if (c->fp32)
-    k_pp_vjp<float, PosF><<<blocks, kThreads, 0, s>>>(
-        c->g, total, PosF{static_cast<const float4*>(c->recp)}, c->starts, w, c->acc,
-        scale);
-  else
-    k_pp_vjp<double, PosD><<<blocks, kThreads, 0, s>>>(
+  if (c->fp32) {
+    // weights in sorted order (in acc, free until the mesh gather), result in fpp (cutoff
+    // units; the mesh gather scales it)
+    float4* ws = reinterpret_cast<float4*>(c->acc);
+    k_gather_w<<<blocks, kThreads, 0, s>>>(total, static_cast<const float4*>(c->recp), w, ws);
+    cudaMemsetAsync(c->fpp, 0, sizeof(float4) * static_cast<size_t>(n), s);
+    cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
+    const unsigned wblocks = static_cast<unsigned>(
+        std::min<int64_t>(blocks, static_cast<int64_t>(kPpBlocksPerSm) * c->num_sms));
+    auto run = [&](auto kern) {
+      kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total,
+                                        static_cast<const float4*>(c->recp), c->starts, ws,
+                                        static_cast<float4*>(c->fpp), c->pp_tile);
+    };
+    switch (c->poly.deg) {
+      case 6: run(k_pp_vjp_f32<6>); break;
+      case 7: run(k_pp_vjp_f32<7>); break;
+      case 8: run(k_pp_vjp_f32<8>); break;
+      case 9: run(k_pp_vjp_f32<9>); break;
+      case 10: run(k_pp_vjp_f32<10>); break;
+      case 11: run(k_pp_vjp_f32<11>); break;
+      case 12: run(k_pp_vjp_f32<12>); break;
+      case 13: run(k_pp_vjp_f32<13>); break;
+      case 14: run(k_pp_vjp_f32<14>); break;
+      default: run(k_pp_vjp_f32<15>); break;
+    }
+  } else {
+    // d/dxi of (k_e q^2 / r_c^2) f(rho): one more factor 1/r_c
+    const double scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc * c->g.rc);
+    k_pp_vjp<<<blocks, kThreads, 0, s>>>(
         c->g, total, PosD{static_cast<const Rec64*>(c->recp)}, c->starts, w, c->acc, scale);
+  }
 }
 
 }  // namespace p3m

@@ -4,6 +4,7 @@
   python -m paper_2103_02046_gb300.experiments energy     # leapfrog energy drift and momentum
   python -m paper_2103_02046_gb300.experiments gradient   # adjoint gradient vs finite differences
   python -m paper_2103_02046_gb300.experiments influence  # P3M error vs exact Coulomb per kernel
+  python -m paper_2103_02046_gb300.experiments error_measure --fp64  # eq. (error_measure) vs height
 
 Each prints one JSON line. Everything runs through the C ABI (``p3m``); no oracle is used.
 
@@ -226,13 +227,89 @@ def influence(precision: int = m.FP64, n_particles: int = 0):
     return out
 
 
+def error_measure(precision: int = m.FP64, n_particles: int = 0):
+    """Error measure of eq. (error_measure) for one particle at height z above the grounded
+    cathode (Sec. 3.1.1), on the GPU path. The potential of the source at a probe point x is
+    read from energies, P3M being linear in the charges: phi(x) = (U(source + probe) -
+    U(source) - U(probe)) / q. Over a grid of probe points in the domain above the cathode:
+      E_bc(z)      = sum_x |phi(pp_bc = 0) - phi(pp_bc = 1)|^2 dV  (the short-range boundary
+                     term the paper neglects), against the paper's closed form: the image's
+                     screened potential k_e q erfc(alpha r)/r, r = |x - S(xi)| < r_c;
+      E_mesh(z, h) = sum_x |phi(pp_bc = 1) - Phi(x)|^2 dV, Phi the exact potential with image,
+                     for h = r_c/2, r_c/4, r_c/8 (r_c fixed).
+    The paper's claim: E_bc vanishes once no probe's image is within r_c (z >= r_c), and the
+    particle's own image acts only below r_c/2."""
+    from scipy.special import erfc as _erfc
+    k_e = 8.9875517923e9
+    q = B.macro_charge()
+    rc = 1e-4
+    kappa = 3.0
+    alpha = kappa / rc
+    heights = [0.05, 0.1, 0.2, 0.3, 0.45, 0.55, 0.75, 1.0, 1.25]
+    step = rc / 3
+    gx = np.arange(-3, 4) * step
+    gz = (np.arange(0, 8) + 0.5) * step
+    probes_all = np.stack(np.meshgrid(gx, gx, gz, indexing="ij"), -1).reshape(-1, 3)
+    dV = step ** 3
+    out = {"experiment": "error_measure", "precision": precision, "r_c": rc, "kappa": kappa,
+           "probe_step_over_rc": 1 / 3, "rows": []}
+    meshes = [("h=rc/2", 2.0), ("h=rc/4", 4.0), ("h=rc/8", 8.0)]
+    ctxs = {}
+    for name, rch in meshes:
+        h = rc / rch
+        n = int(math.ceil(3.0 * rc / h)) + 5
+        lo = (-1.5 * rc - 2 * h, -1.5 * rc - 2 * h, -2 * h)
+        for pp_bc in (0, 1):
+            prm = m.Params(n=(n, n, n), lo=lo, h=(h, h, h), rc_over_h=rch, kappa=kappa,
+                           pm_bc=1, pp_bc=pp_bc, z_cathode=0.0, precision=precision, q=q)
+            ctxs[(name, pp_bc)] = m.Context(prm, 2)
+    cache = {}
+
+    def energy(ctx_key, pts):
+        key = (ctx_key, tuple(np.round(np.asarray(pts).ravel() / rc, 9)))
+        if key not in cache:
+            _, e = ctxs[ctx_key].forces(_cuda(np.asarray(pts)), energy=True)
+            cache[key] = float(e.sum())
+        return cache[key]
+
+    for zs in heights:
+        xi = np.array([0.0, 0.0, zs * rc])
+        probes = probes_all[probes_all[:, 2] <= xi[2] + rc]
+        probes = probes[np.linalg.norm(probes - xi, axis=1) > 0.25 * rc]  # off the source
+        d = probes - xi
+        di = probes - xi * np.array([1, 1, -1])
+        r, ri = np.linalg.norm(d, axis=1), np.linalg.norm(di, axis=1)
+        exact = k_e * q * (1 / r - 1 / ri)
+        img = np.where(ri < rc, k_e * q * _erfc(alpha * ri) / ri, 0.0)
+        row = {"z_over_rc": zs, "probes": len(probes),
+               "E_bc_closed": float((img ** 2).sum() * dV), "E_mesh": {}, "E_total_pp_bc0": {}}
+        for name, _ in meshes:
+            phi = {}
+            for pp_bc in (0, 1):
+                key = (name, pp_bc)
+                us = energy(key, [xi])
+                phi[pp_bc] = np.array([(energy(key, [xi, x]) - us - energy(key, [x])) / q
+                                       for x in probes])
+            if name == meshes[0][0]:
+                row["E_bc_gpu"] = float(((phi[0] - phi[1]) ** 2).sum() * dV)
+            else:
+                row.setdefault("E_bc_gpu_other_meshes", []).append(
+                    float(((phi[0] - phi[1]) ** 2).sum() * dV))
+            row["E_mesh"][name] = float(((phi[1] - exact) ** 2).sum() * dV)
+            row["E_total_pp_bc0"][name] = float(((phi[0] - exact) ** 2).sum() * dV)
+        out["rows"].append(row)
+    for c in ctxs.values():
+        c.close()
+    return out
+
+
 def main(argv):
     which = argv[1] if len(argv) > 1 else "boundary"
     kw = {"precision": m.FP64 if "--fp64" in argv else m.FP32_MIXED}
     if "--n" in argv:
         kw["n_particles"] = int(argv[argv.index("--n") + 1])
     fn = {"boundary": boundary, "energy": energy, "gradient": gradient,
-          "influence": influence}[which]
+          "influence": influence, "error_measure": error_measure}[which]
     print(json.dumps(fn(**kw)), flush=True)
 
 
