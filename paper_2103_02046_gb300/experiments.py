@@ -5,6 +5,7 @@
   python -m paper_2103_02046_gb300.experiments gradient   # adjoint gradient vs finite differences
   python -m paper_2103_02046_gb300.experiments influence  # P3M error vs exact Coulomb per kernel
   python -m paper_2103_02046_gb300.experiments error_measure --fp64  # eq. (error_measure) vs height
+  python -m paper_2103_02046_gb300.experiments action     # discrete EL residual, action stationarity
 
 Each prints one JSON line. Everything runs through the C ABI (``p3m``); no oracle is used.
 
@@ -303,13 +304,64 @@ def error_measure(precision: int = m.FP64, n_particles: int = 0):
     return out
 
 
+def action(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps: int = 20):
+    """Discrete-action diagnostics (eq. (full_p3m_lagrangian) with the leapfrog patch of
+    eq. (leapfrog)) along a trajectory of the 1,048,576-particle Gaussian bunch (64^3, r_c = 2h,
+    dt = 1e-12 s): the discrete Euler-Lagrange residual M (x^{n+1} - 2x^n + x^{n-1})/dt^2 - F(x^n)
+    (F the force the step used), relative to max |F|; the discrete action
+    S_d = dt sum_n [sum_i M |x^{n+1}_i - x^n_i|^2 / (2 dt^2) - U(x^n)], U the P3M energy; and its
+    central difference along a random variation of the interior points, relative to the kinetic
+    part's, on the trajectory and off it."""
+    x, p = _grad_bunch(n_particles)
+    xg, pg = _cuda(x), _cuda(p)
+    prm = m.auto_mesh(_cuda(x * 1.05), m.Params(n=(64,) * 3, rc_over_h=2.0, precision=precision))
+    ctx = m.Context(prm, n_particles)
+    dt, M = 1e-12, prm.mass
+    f = ctx.forces(xg)
+    X, F = [xg.clone()], [f.clone()]
+    for _ in range(steps):
+        f = ctx.push(xg, pg, dt, 1, f)
+        X.append(xg.clone())
+        F.append(f.clone())
+    res = max(float((M * (X[k + 1] - 2 * X[k] + X[k - 1]) / dt ** 2 - F[k]).abs().max()) /
+              float(F[k].abs().max()) for k in range(1, steps))
+
+    def U(y):
+        _, e = ctx.forces(y, energy=True)
+        return float(e.sum())
+
+    def S(Xs):
+        return dt * sum(0.5 * M * float(((Xs[k + 1] - Xs[k]) ** 2).sum()) / dt ** 2 - U(Xs[k])
+                        for k in range(len(Xs) - 1))
+
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    V = [torch.zeros_like(xg)] + [torch.randn(xg.shape, dtype=xg.dtype, device="cuda",
+                                              generator=gen) for _ in range(steps - 1)] + \
+        [torch.zeros_like(xg)]
+    kin = dt * sum(abs(float((M * (X[k] - X[k - 1]) / dt ** 2 * V[k]).sum()))
+                   for k in range(1, steps))
+    eps = 1e-9
+
+    def dS(Xs):
+        return (S([a + eps * v for a, v in zip(Xs, V)]) -
+                S([a - eps * v for a, v in zip(Xs, V)])) / (2 * eps)
+
+    on = dS(X)
+    off = dS([a + 1e-7 * v for a, v in zip(X, V)])
+    S0 = S(X)
+    ctx.sync()
+    return {"experiment": "action", "n": n_particles, "steps": steps, "precision": precision,
+            "el_residual_max_rel": res, "S_d": S0, "dS_on_trajectory_rel": on / kin,
+            "dS_off_trajectory_rel": off / kin}
+
+
 def main(argv):
     which = argv[1] if len(argv) > 1 else "boundary"
     kw = {"precision": m.FP64 if "--fp64" in argv else m.FP32_MIXED}
     if "--n" in argv:
         kw["n_particles"] = int(argv[argv.index("--n") + 1])
     fn = {"boundary": boundary, "energy": energy, "gradient": gradient,
-          "influence": influence, "error_measure": error_measure}[which]
+          "influence": influence, "error_measure": error_measure, "action": action}[which]
     print(json.dumps(fn(**kw)), flush=True)
 
 

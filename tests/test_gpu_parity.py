@@ -243,6 +243,31 @@ def test_push_parity(precision):
     assert rel(fg, fT) <= 10 * tol
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_push_satisfies_discrete_euler_lagrange(precision):
+    # eq. (disc_euler_lagrange_eqn) with the leapfrog patch of eq. (leapfrog): the GPU
+    # trajectory satisfies M (x^{n+1} - 2 x^n + x^{n-1}) / dt^2 = F(x^n) up to the rounding of
+    # the FP64 positions, with F(x^n) the force the step used (returned by the push); in FP64 a
+    # fresh evaluation at x^n gives the same force
+    x0 = B.gaussian(2048, (1e-3, 1e-3, 1e-3), 41)
+    P = O.auto_mesh(x0 * 1.5, 16, rc_over_h=2.0)
+    ctx = p3m().Context(gpu_params(P, precision), len(x0))
+    xg, pg = cuda(x0), torch.zeros_like(cuda(x0))
+    f = ctx.forces(xg)
+    dt = math.sqrt(1e-7 / (float(f.abs().max()) / P.mass))
+    X, F = [xg.clone()], [f.clone()]
+    for _ in range(6):
+        f = ctx.push(xg, pg, dt, 1, f)
+        X.append(xg.clone())
+        F.append(f.clone())
+    for n in range(1, 6):
+        r = P.mass * (X[n + 1] - 2 * X[n] + X[n - 1]) / dt ** 2 - F[n]
+        assert float(r.abs().max()) <= 1e-9 * float(F[n].abs().max())
+        if precision == 0:
+            assert rel(ctx.forces(X[n]), F[n].cpu().numpy()) <= 1e-13
+    ctx.sync()
+
+
 def test_emittance_parity():
     x = B.gaussian(3000, (1e-3, 2e-3, 3e-3), 24)
     p = B.thermal_momenta(3000, 1e-24, 25) + 1e-21 * x

@@ -442,3 +442,52 @@ def test_alias_influence_minimises_force_error(which):
         Fc, _ = O.coulomb_brute(x, P)
         err.append(O.rel_l2(O.forces(x, P).F, Fc))
     assert err[2] < 0.95 * err[1] < 0.95 * err[0]
+
+
+def _leapfrog_trajectory():
+    x0 = B.gaussian(300, (1e-3, 1e-3, 1e-3), 41)
+    P = O.auto_mesh(x0 * 1.5, 8, rc_over_h=2.0)
+    a = np.abs(O.forces(x0, P).F).max() / P.mass
+    dt = math.sqrt(1e-7 / a)            # dt^2 times the largest acceleration: 1e-7 m
+    states = []
+    O.push(x0, np.zeros_like(x0), dt, 6, P, states=states)
+    return P, dt, [s[0] for s in states]
+
+
+def test_kdk_satisfies_discrete_euler_lagrange():
+    # eq. (disc_euler_lagrange_eqn) with the leapfrog patch of eq. (leapfrog): for L_d(x^n, x^{n+1})
+    # = L(x^n, (x^{n+1} - x^n)/dt) the discrete EL equation is M (x^{n+1} - 2 x^n + x^{n-1})/dt^2
+    # = F(x^n); the kick-drift-kick trajectory satisfies it up to rounding
+    P, dt, X = _leapfrog_trajectory()
+    for n in range(1, len(X) - 1):
+        Fn = O.forces(X[n], P).F
+        r = P.mass * (X[n + 1] - 2 * X[n] + X[n - 1]) / dt ** 2 - Fn
+        assert np.abs(r).max() <= 1e-9 * np.abs(Fn).max()
+
+
+def test_discrete_action_is_stationary_on_the_trajectory():
+    # S_d = dt sum_n [ M |x^{n+1} - x^n|^2 / (2 dt^2) - U(x^n) ] with U the P3M energy: its
+    # derivative along a variation of the interior points vanishes on the leapfrog trajectory
+    # (Hamilton's principle, discrete), and not off it
+    P, dt, X = _leapfrog_trajectory()
+
+    def S(Xs):
+        tot = 0.0
+        for n in range(len(Xs) - 1):
+            R = O.forces(Xs[n], P)
+            tot += 0.5 * P.mass * ((Xs[n + 1] - Xs[n]) ** 2).sum() / dt ** 2 - (R.U_pp + R.U_pm)
+        return tot * dt
+
+    rng = np.random.default_rng(3)
+    V = [np.zeros_like(X[0])] + [rng.standard_normal(X[0].shape) for _ in X[1:-1]] + \
+        [np.zeros_like(X[0])]
+    kin = dt * sum(abs((P.mass * (X[n] - X[n - 1]) / dt ** 2 * V[n]).sum())
+                   for n in range(1, len(X) - 1))
+
+    def dS(Xs, eps=1e-9):
+        return (S([a + eps * v for a, v in zip(Xs, V)]) -
+                S([a - eps * v for a, v in zip(Xs, V)])) / (2 * eps)
+
+    assert abs(dS(X)) <= 1e-6 * kin
+    Y = [a + 1e-7 * v for a, v in zip(X, V)]
+    assert abs(dS(Y)) >= 1.0 * kin
