@@ -124,7 +124,7 @@ class Params:
     kappa: float = 3.0               # alpha = kappa / r_c unless alpha > 0
     alpha: float = 0.0
     assign_order: int = 2            # 1 = CIC, 2 = TSC
-    pm_bc: int = 0                   # 1 = grounded cathode in the long-range solve
+    pm_bc: int = 0                   # 1 = grounded cathode plane, 2 = grounded box (long range)
     pp_bc: int = 0                   # 1 = cathode images in the short-range sum as well
     z_cathode: float = 0.0
     influence: int = 0               # 1 = principal-alias optimal factor 1/U^2, 2 = alias sum
@@ -221,7 +221,7 @@ def green_kernels(P: Params):
     Kf[unused] = 0.0
     Kf_hat = _rfftn(Kf) * ke
     Ki_hat = None
-    if P.pm_bc:
+    if P.pm_bc == 1:
         d = P.lo[2] - P.z_cathode
         Zi = (2.0 * d + (mz + nz - 1) * P.h[2])[:, None, None]
         r = np.sqrt(X * X + Y * Y + Zi * Zi)
@@ -315,17 +315,70 @@ def _irfftn(a, shape):
 
 def solve(Q, P: Params, kernels=None):
     """Mesh potential phi = k_e [K_f (*) Q - K_i (*) Q_rev] restricted to the n^3 block
-    (eq. (phi_L); image part only with the cathode). Q_rev[.,.,j] = Q[.,.,n_z - 1 - j]."""
+    (eq. (phi_L); image part only with the cathode). Q_rev[.,.,j] = Q[.,.,n_z - 1 - j].
+    With the grounded box (pm_bc = 2), the discrete-Laplacian solve of ``box_solve``."""
+    if P.pm_bc == 2:
+        return box_solve(Q, P)
     nx, ny, nz = P.n
     shape = (2 * nz, 2 * ny, 2 * nx)
     Kf_hat, Ki_hat = kernels if kernels is not None else green_kernels(P)
     pad = np.zeros(shape)
     pad[:nz, :ny, :nx] = Q
     phi = _irfftn(_rfftn(pad) * Kf_hat, shape)[:nz, :ny, :nx]
-    if P.pm_bc:
+    if P.pm_bc == 1:
         pad[:nz, :ny, :nx] = Q[::-1, :, :]
         phi = phi - _irfftn(_rfftn(pad) * Ki_hat, shape)[:nz, :ny, :nx]
     return np.ascontiguousarray(phi)
+
+
+def box_laplacian_eigenvalues(P: Params):
+    """Eigenvalues of the discrete Laplacian D_xyz of eq. (3dim_second_order_fin_diff) on the
+    interior nodes of a box with phi = 0 on its faces (nodes 0 and n_d - 1): for the sine mode
+    j_d = 1 .. N_d (N_d = n_d - 2), sum_d (2 cos(pi j_d / (N_d + 1)) - 2) / h_d^2, as [z, y, x]."""
+    lam = 0.0
+    shape = [(1, 1, -1), (1, -1, 1), (-1, 1, 1)]
+    for d in range(3):
+        N = P.n[d] - 2
+        j = np.arange(1, N + 1)
+        lam = lam + ((2.0 * np.cos(np.pi * j / (N + 1)) - 2.0) / P.h[d] ** 2).reshape(shape[d])
+    return lam
+
+
+def box_solve(Q, P: Params):
+    """Long-range potential in a grounded box (Sec. 3.1, fig. boundary_gauss_seidel_results):
+    the discrete Poisson equation D_xyz phi = -rho_L / eps0 of eq. (def_G_L) on the interior
+    nodes, phi = 0 on the six faces, rho_L = Q / (h_x h_y h_z) screened by the Gaussian of the
+    charge splitting, applied in the sine basis as gamma^(k) = exp(-|k|^2 / (4 alpha^2)),
+    k_d = pi j_d / ((N_d + 1) h_d). Solved with type-1 sine transforms (each diagonalises D_xyz
+    with these boundary values)."""
+    from scipy.fft import dstn, idstn
+    nx, ny, nz = P.n
+    lam = box_laplacian_eigenvalues(P)
+    k2 = 0.0
+    shape = [(1, 1, -1), (1, -1, 1), (-1, 1, 1)]
+    for d in range(3):
+        N = P.n[d] - 2
+        k = np.pi * np.arange(1, N + 1) / ((N + 1) * P.h[d])
+        k2 = k2 + (k * k).reshape(shape[d])
+    gam = np.exp(-k2 / (4.0 * P.a * P.a))
+    vol = P.h[0] * P.h[1] * P.h[2]
+    rho = _f64(Q)[1:-1, 1:-1, 1:-1] / vol          # Q holds charges (q included)
+    phi_hat = -gam * dstn(rho, type=1) / (EPS0 * lam)
+    phi = np.zeros((nz, ny, nx))
+    phi[1:-1, 1:-1, 1:-1] = idstn(phi_hat, type=1)
+    return phi
+
+
+def box_valid(x, P: Params):
+    """In the grounded box every particle's assignment support must lie on interior nodes:
+    TSC nearest node in [2, n - 3], CIC lower node in [1, n - 3]."""
+    s = (_f64(x) - np.asarray(P.lo)) / np.asarray(P.h)
+    n = np.asarray(P.n)
+    if P.assign_order == 2:
+        c = np.floor(s + 0.5)
+        return np.all((c >= 2) & (c <= n - 3), axis=1)
+    c = np.floor(s)
+    return np.all((c >= 1) & (c <= n - 3), axis=1)
 
 
 def mesh_direct(Q, P: Params):
@@ -417,6 +470,8 @@ def forces(x, P: Params, sample=None, kernels=None, parts=3):
     Q = phi_m = None
     bad = 0
     U_pm = 0.0
+    if P.pm_bc == 2 and not np.all(box_valid(x, P)):
+        raise ValueError("a particle's assignment support reaches the grounded box's faces")
     if parts & 2:
         Q, bad = deposit(x, P)
         phi_m = solve(Q, P, kernels)
