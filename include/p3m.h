@@ -61,7 +61,11 @@ typedef struct p3m_params {
   double kappa;          /* Ewald parameter a = kappa / r_c (eq. (ewald_split)) unless alpha > 0 */
   double alpha;          /* explicit Ewald parameter [1/m]; <= 0 selects kappa / r_c */
   int32_t assign_order;  /* 1 = cloud-in-cell (eq. (interpolation_splines_b0)), 2 = TSC */
-  int32_t pm_bc;         /* 0 = open boundaries, 1 = grounded cathode in the long-range solve */
+  int32_t pm_bc;         /* 0 = open boundaries, 1 = grounded cathode plane z = z_cathode in the
+                            long-range solve, 2 = grounded box: phi = 0 on the mesh's six faces
+                            (nodes 0 and n_d - 1), discrete-Laplacian long range of eq. (def_G_L);
+                            FP64 path, pp_bc = 0, influence = 0; every particle's assignment
+                            support must stay on interior nodes (else P3M_ERANGE) */
   int32_t pp_bc;         /* 0 = short range in free space (the paper's prescription),
                             1 = cathode images also in the short-range sum */
   double z_cathode;      /* cathode plane z [m] (eq. (symmetry_planar_cathode) at z = z_cathode) */

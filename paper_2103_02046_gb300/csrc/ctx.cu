@@ -48,7 +48,11 @@ p3m_status validate(const p3m_params* p, std::string* why) {
   if (!(p->rc_over_h >= 0.25) || !std::isfinite(p->rc_over_h)) { *why = "rc_over_h must be >= 0.25"; return P3M_EINVAL; }
   if (!(p->alpha > 0.0) && !finite_pos(p->kappa)) { *why = "kappa must be > 0 (or alpha > 0)"; return P3M_EINVAL; }
   if (p->assign_order != 1 && p->assign_order != 2) { *why = "assign_order must be 1 or 2"; return P3M_EINVAL; }
-  if ((p->pm_bc != 0 && p->pm_bc != 1) || (p->pp_bc != 0 && p->pp_bc != 1)) { *why = "pm_bc/pp_bc must be 0 or 1"; return P3M_EINVAL; }
+  if (p->pm_bc < 0 || p->pm_bc > 2 || (p->pp_bc != 0 && p->pp_bc != 1)) { *why = "pm_bc must be 0, 1 or 2 and pp_bc 0 or 1"; return P3M_EINVAL; }
+  if (p->pm_bc == 2 && (p->precision != P3M_FP64 || p->pp_bc != 0 || p->influence != 0)) {
+    *why = "the grounded box (pm_bc = 2) runs on the FP64 path with pp_bc = 0, influence = 0";
+    return P3M_EINVAL;
+  }
   if (!std::isfinite(p->z_cathode)) { *why = "z_cathode must be finite"; return P3M_EINVAL; }
   if (p->influence < 0 || p->influence > 2) { *why = "influence must be 0, 1 or 2"; return P3M_EINVAL; }
   if (p->precision != P3M_FP64 && p->precision != P3M_FP32_MIXED) { *why = "precision must be 0 or 1"; return P3M_EINVAL; }
@@ -197,7 +201,8 @@ cudaError_t alloc(T** ptr, size_t count) {
 void free_all(p3m_ctx* c) {
   void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recm, c->fpp,
                   c->acc, c->qpad, c->qhat, c->qhat2, c->khat_f, c->khat_i, c->fhat, c->freal,
-                  c->phihat, c->phireal, c->dfac, c->ztw, c->energy_acc, c->pair_acc,
+                  c->phihat, c->phireal, c->dfac, c->ztw, c->box_real, c->box_spec, c->box_mult,
+                  c->energy_acc, c->pair_acc,
                   c->pp_tile, c->err_dev, c->ckpt, c->seg, c->lam_x, c->lam_p, c->xw, c->pw,
                   c->tmp3, c->tmp3b, c->f_work, c->red};
   for (void* b : bufs) cudaFree(b);
@@ -205,6 +210,8 @@ void free_all(p3m_ctx* c) {
   if (c->have_xy_f) cufftDestroy(c->plan_xy_f);
   if (c->have_z) cufftDestroy(c->plan_z);
   if (c->have_xy_i) cufftDestroy(c->plan_xy_i);
+  if (c->have_box_f) cufftDestroy(c->plan_box_f);
+  if (c->have_box_i) cufftDestroy(c->plan_box_i);
   if (c->s_pp) cudaStreamDestroy(c->s_pp);
   if (c->work) cudaStreamDestroy(c->work);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -296,6 +303,12 @@ cufftResult fft_c2r(p3m_ctx* c, void* spec, void* real) {
 // Solve on the current qpad: FP64 -> potential; FP32 -> difference fields (and the potential
 // when want_phi).
 p3m_status mesh_solve(p3m_ctx* c, bool want_phi, bool want_diff, bool want_energy) {
+  if (c->g.pm_bc == 2) {  // grounded box (FP64): the potential, on the interior nodes
+    const p3m_status s = box_solve(c, want_energy);
+    if (s != P3M_OK) return fail(c, s, "grounded-box solve failed");
+    c->phi_valid = true;
+    return P3M_OK;
+  }
   if (c->zconv && want_diff && !want_phi) {
     // FP32 forces: x-y transforms of the charged planes, the fused z solve, x-y inverses
     if (cufftExecR2C(c->plan_xy_f, static_cast<cufftReal*>(c->qpad),
@@ -506,7 +519,7 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   A(cudaMalloc(&c->qhat, 2 * es * c->n_cplx));
   A(cudaMalloc(&c->qhat2, 2 * es * c->n_cplx));
   A(cudaMalloc(&c->khat_f, es * c->n_cplx));
-  if (g.pm_bc) A(cudaMalloc(&c->khat_i, 2 * es * c->n_cplx));
+  if (g.pm_bc == 1) A(cudaMalloc(&c->khat_i, 2 * es * c->n_cplx));
   A(cudaMalloc(&c->phihat, 2 * es * c->n_cplx));
   A(cudaMalloc(&c->phireal, es * c->n_real));
   if (c->fp32) {
@@ -598,7 +611,16 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     cufftSetStream(c->plan_z, c->work);
     cufftSetStream(c->plan_xy_i, c->work);
   }
-  e = build_green(c);
+  e = g.pm_bc == 2 ? cudaSuccess : build_green(c);
+  if (e == cudaSuccess && g.pm_bc == 2) {
+    const p3m_status bs = box_setup(c);
+    if (bs != P3M_OK) {
+      free_all(c);
+      delete c;
+      cudaGetLastError();
+      return bs;
+    }
+  }
   if (e == cudaSuccess && zconv_supported(c)) {
     e = zconv_setup(c);
     c->zconv = e == cudaSuccess;

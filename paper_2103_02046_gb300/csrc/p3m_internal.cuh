@@ -168,6 +168,11 @@ __host__ __device__ inline uint32_t cell_key(const Geom& g, int cx, int cy, int 
   return (static_cast<uint32_t>(cz) * g.nc[1] + cy) * g.nc[0] + cx;
 }
 
+// element (x, y, z) of a real field on the doubled mesh (x fastest)
+__host__ __device__ inline size_t real_index(const Geom& g, int x, int y, int z) {
+  return (static_cast<size_t>(z) * g.M[1] + y) * g.M[0] + x;
+}
+
 __host__ __device__ inline uint32_t pack_node(int cx, int cy, int cz) {
   return static_cast<uint32_t>(cx) | (static_cast<uint32_t>(cy) << 10) |
          (static_cast<uint32_t>(cz) << 20);
@@ -255,6 +260,12 @@ struct p3m_ctx {
   void* phireal = nullptr;      // potential on the doubled mesh
   float2* dfac = nullptr;       // FP32: difference factors e^{2 pi i k/M} - 1 per axis (Mx/2+1 + My + Mz)
   float2* ztw = nullptr;        // FP32 fused z solve: e^{-2 pi i t / Mz}, t < Mz
+  // grounded box (pm_bc = 2, FP64): odd extension (2(n-1))^3, its half spectrum, multiplier
+  double* box_real = nullptr;
+  double2* box_spec = nullptr;
+  double* box_mult = nullptr;
+  cufftHandle plan_box_f = 0, plan_box_i = 0;
+  bool have_box_f = false, have_box_i = false;
   bool zconv = false;           // FP32 forces use the fused z solve
   // Pruned transforms of the doubled mesh: the charge is non-zero, and the fields are needed,
   // only in the n^3 block, so the x-y plane transforms run on the first n_z planes only and
@@ -310,6 +321,9 @@ void launch_green_multiply(const p3m_ctx* c, bool want_phi, bool want_diff, bool
 bool zconv_supported(const p3m_ctx* c);
 cudaError_t zconv_setup(p3m_ctx* c);
 void launch_zconv(const p3m_ctx* c, bool want_energy);
+// grounded box (pm_bc = 2): discrete-Laplacian solve of the deposit into phireal
+p3m_status box_setup(p3m_ctx* c);
+p3m_status box_solve(p3m_ctx* c, bool want_energy);
 void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts);
 void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, double* out);
 void launch_get_mesh(const p3m_ctx* c, int which, double* out);

@@ -31,9 +31,6 @@ inline unsigned blocks_for(uint64_t n, int t = kThreads) {
   return static_cast<unsigned>((n + t - 1) / t);
 }
 
-__device__ __forceinline__ size_t real_index(const Geom& g, int x, int y, int z) {
-  return (static_cast<size_t>(z) * g.M[1] + y) * g.M[0] + x;
-}
 
 // ---------------------------------------------------------------------------------------------
 // Green's-function spectra (built once per geometry, in FP64)
@@ -710,7 +707,7 @@ cudaError_t build_green(p3m_ctx* c) {
   };
   if ((err = cudaMalloc(&samp, sizeof(double) * nreal)) != cudaSuccess) return fail(err);
   if ((err = cudaMalloc(&sf, sizeof(double2) * ncplx)) != cudaSuccess) return fail(err);
-  if (g.pm_bc && (err = cudaMalloc(&si, sizeof(double2) * ncplx)) != cudaSuccess) return fail(err);
+  if (g.pm_bc == 1 && (err = cudaMalloc(&si, sizeof(double2) * ncplx)) != cudaSuccess) return fail(err);
   if (cufftPlan3d(&plan, g.M[2], g.M[1], g.M[0], CUFFT_D2Z) != CUFFT_SUCCESS)
     return fail(cudaErrorUnknown);
   have_plan = true;
@@ -718,7 +715,7 @@ cudaError_t build_green(p3m_ctx* c) {
   k_sample_kernel<<<blocks_for(nreal), kThreads, 0, c->work>>>(g, samp, 0);
   if (cufftExecD2Z(plan, samp, reinterpret_cast<cufftDoubleComplex*>(sf)) != CUFFT_SUCCESS)
     return fail(cudaErrorUnknown);
-  if (g.pm_bc) {
+  if (g.pm_bc == 1) {
     k_sample_kernel<<<blocks_for(nreal), kThreads, 0, c->work>>>(g, samp, 1);
     if (cufftExecD2Z(plan, samp, reinterpret_cast<cufftDoubleComplex*>(si)) != CUFFT_SUCCESS)
       return fail(cudaErrorUnknown);

@@ -44,20 +44,22 @@ __device__ __forceinline__ int particle_cell(const Geom& g, const double* __rest
     const float f = df_sub(df_from_double(xi[d]), DF{g.lo_df[d][0], g.lo_df[d][1]}).hi;
     if (!(f == f)) return kErrNaN;
     const float s = f * g.inv_h_f[d];
-    const float b0 = (g.order == 2) ? 0.5f : 0.0f;
-    const float b1 = static_cast<float>(g.n[d]) - ((g.order == 2) ? 1.5f : 1.0f);
+    // in the grounded box the support must also stay off the face nodes: one node less per side
+    const int box = g.pm_bc == 2 ? 1 : 0;
+    const float b0 = ((g.order == 2) ? 0.5f : 0.0f) + box;
+    const float b1 = static_cast<float>(g.n[d] - box) - ((g.order == 2) ? 1.5f : 1.0f);
     bool ok;
     if (fabsf(s - b0) < 1e-3f || fabsf(s - b1) < 1e-3f) {
       const double se = mesh_coord(g, xi[d], d);
       const double c = (g.order == 2) ? floor(se + 0.5) : floor(se);
-      ok = c >= ((g.order == 2) ? 1.0 : 0.0) && c <= static_cast<double>(g.n[d] - 2);
+      ok = c >= ((g.order == 2) ? 1.0 : 0.0) + box && c <= static_cast<double>(g.n[d] - 2 - box);
     } else {
       ok = s >= b0 && s < b1;
     }
     if (!ok) err = kErrRange;
     cell[d] = min(max(static_cast<int>(floorf(f * g.inv_cell_f[d])), 0), g.nc[d] - 1);
   }
-  if (g.pm_bc && !(xi[2] > g.zc)) err = kErrRange;
+  if (g.pm_bc == 1 && !(xi[2] > g.zc)) err = kErrRange;
   return err;
 }
 

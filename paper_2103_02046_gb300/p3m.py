@@ -118,7 +118,7 @@ class Params:
     kappa: float = 3.0
     alpha: float = 0.0
     assign_order: int = 2
-    pm_bc: int = 0
+    pm_bc: int = 0  # 0 open, 1 grounded cathode plane, 2 grounded box (FP64)
     pp_bc: int = 0
     z_cathode: float = 0.0
     influence: int = 0  # 0 sampled kernel, 1 principal alias 1/U^2, 2 alias sums (eq. (Ghfinal))

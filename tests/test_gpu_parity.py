@@ -160,6 +160,59 @@ def test_lattice_pairs_at_cutoff(precision):
     assert rel(f_pp, ref.F_pp) <= TOL[precision]
 
 
+def _box_case():
+    # a bunch inside a grounded box of 20 x 24 x 28 nodes (h = 0.1 mm), supports off the faces
+    x = B.gaussian(3000, (0.2e-3, 0.25e-3, 0.3e-3), 51)
+    h = 1e-4
+    n = (20, 24, 28)
+    lo = tuple(-(nd - 1) * h / 2 for nd in n)
+    P = O.Params(n=n, lo=lo, h=(h, h, h), pm_bc=2, rc_over_h=2.0)
+    return x[O.box_valid(x, P)], P
+
+
+def test_grounded_box_parity():
+    x, P = _box_case()
+    ref = O.forces(x, P)
+    ctx = p3m().Context(gpu_params(P, 0), len(x))
+    xg = cuda(x)
+    f_pm = ctx.forces(xg, parts=2)
+    f, e = ctx.forces(xg, energy=True)
+    phi = ctx.get_mesh(1)
+    ctx.sync()
+    assert rel(f_pm, ref.F_pm) <= 1e-12
+    assert rel(f, ref.F) <= 1e-12
+    assert rel(phi, ref.phi_mesh) <= 1e-12
+    e = e.cpu().numpy()
+    assert e[1] == pytest.approx(ref.U_pm, rel=1e-11)
+    w = np.random.default_rng(52).standard_normal(x.shape)
+    v = ctx.force_vjp(xg, cuda(w))
+    ctx.sync()
+    assert rel(v, O.force_vjp(x, w, P)) <= 1e-11
+
+
+def test_grounded_box_refusals_and_faces():
+    m = p3m()
+    x, P = _box_case()
+    for bad in (dict(precision=1), dict(pp_bc=1), dict(influence=1)):
+        kw = dict(n=P.n, lo=P.lo, h=P.h, rc_over_h=P.rc_over_h, pm_bc=2, precision=0)
+        kw.update(bad)
+        with pytest.raises(m.P3MError) as ei:
+            m.Context(m.Params(**kw), 10)
+        assert ei.value.status == m.P3M_EINVAL
+    ctx = m.Context(gpu_params(P, 0), len(x))
+    # TSC support reaching the face nodes: the nearest node is 1
+    xb = x[:20].copy()
+    xb[3, 2] = P.lo[2] + 1.2 * P.h[2]
+    fb = ctx.forces(cuda(xb))
+    with pytest.raises(m.P3MError) as ei:
+        ctx.sync()
+    assert ei.value.status == m.P3M_ERANGE
+    assert torch.all(fb[3] == 0)
+    f = ctx.forces(cuda(x[:20]))
+    ctx.sync()
+    assert rel(f, O.forces(x[:20], P).F) <= 1e-12
+
+
 def test_auto_mesh_matches_oracle():
     m = p3m()
     x = B.gaussian(5000, (1e-3, 2e-3, 3e-3), 21)
