@@ -128,6 +128,7 @@ class Params:
     pp_bc: int = 0                   # 1 = cathode images in the short-range sum as well
     z_cathode: float = 0.0
     influence: int = 0               # 1 = principal-alias optimal factor 1/U^2, 2 = alias sum
+    force_diff: int = 0              # 1 = central-difference mesh gradient (not the W derivative)
     q: float = 1e-15
     mass: float = 1e-15 / ELEMENTARY_CHARGE * ELECTRON_MASS
 
@@ -370,8 +371,9 @@ def box_solve(Q, P: Params):
 
 
 def box_valid(x, P: Params):
-    """In the grounded box every particle's assignment support must lie on interior nodes:
-    TSC nearest node in [2, n - 3], CIC lower node in [1, n - 3]."""
+    """Every particle's assignment support on nodes 1 .. n - 2 (the grounded box's interior, and
+    the nodes where central differences of phi exist): TSC nearest node in [2, n - 3], CIC
+    lower node in [1, n - 3]."""
     s = (_f64(x) - np.asarray(P.lo)) / np.asarray(P.h)
     n = np.asarray(P.n)
     if P.assign_order == 2:
@@ -400,6 +402,45 @@ def interp(x, phi, P: Params):
     bad = lib().oracle_interp(len(x), _p(x), P.q, _p(phi), _p(n), _p(lo), _p(h), P.assign_order,
                               _p(F), _p(pa))
     return F, pa, int(bad)
+
+
+def _weights_1d(s, order):
+    """Nodes and weights of one axis: TSC (nearest node c, offsets c-1..c+1) or CIC (c, c+1)."""
+    if order == 2:
+        c = np.floor(s + 0.5)
+        u = s - c
+        return c - 1, np.stack([0.5 * (0.5 - u) ** 2, 0.75 - u * u, 0.5 * (0.5 + u) ** 2], -1)
+    c = np.floor(s)
+    f = s - c
+    return c, np.stack([1.0 - f, f], -1)
+
+
+def interp_central(x, phi, P: Params):
+    """Alternative long-range force: the mesh field by central differences,
+    E_d(g) = -(phi_{g + e_d} - phi_{g - e_d}) / (2 h_d), interpolated with the assignment
+    function, F_i = q sum_g W(x_g - xi_i) E(g). The support must keep one node off the mesh
+    edge (``box_valid``)."""
+    x = _f64(x)
+    phi = _f64(phi)
+    s = (x - np.asarray(P.lo)) / np.asarray(P.h)
+    F = np.zeros_like(x)
+    base, w = [], []
+    for d in range(3):
+        b, wd = _weights_1d(s[:, d], P.assign_order)
+        base.append(b.astype(np.int64))
+        w.append(wd)
+    S = w[0].shape[1]
+    for c in range(S):
+        for b in range(S):
+            for a in range(S):
+                gx, gy, gz = base[0] + a, base[1] + b, base[2] + c
+                W = w[0][:, a] * w[1][:, b] * w[2][:, c]
+                E = [-(phi[gz, gy, gx + 1] - phi[gz, gy, gx - 1]) / (2 * P.h[0]),
+                     -(phi[gz, gy + 1, gx] - phi[gz, gy - 1, gx]) / (2 * P.h[1]),
+                     -(phi[gz + 1, gy, gx] - phi[gz - 1, gy, gx]) / (2 * P.h[2])]
+                for d in range(3):
+                    F[:, d] += P.q * W * E[d]
+    return F
 
 
 # ------------------------------------------------------------------------------------------
@@ -470,12 +511,14 @@ def forces(x, P: Params, sample=None, kernels=None, parts=3):
     Q = phi_m = None
     bad = 0
     U_pm = 0.0
-    if P.pm_bc == 2 and not np.all(box_valid(x, P)):
-        raise ValueError("a particle's assignment support reaches the grounded box's faces")
+    if (P.pm_bc == 2 or P.force_diff) and not np.all(box_valid(x, P)):
+        raise ValueError("a particle's assignment support reaches the mesh's edge nodes")
     if parts & 2:
         Q, bad = deposit(x, P)
         phi_m = solve(Q, P, kernels)
         F_pm, phi_pm, _ = interp(xs, phi_m, P)
+        if P.force_diff:
+            F_pm = interp_central(xs, phi_m, P)
         U_pm = 0.5 * float(np.sum(Q * phi_m))
     F_pp = np.zeros((n_out, 3))
     phi_pp = np.zeros(n_out)

@@ -6,6 +6,7 @@
   python -m paper_2103_02046_gb300.experiments influence  # P3M error vs exact Coulomb per kernel
   python -m paper_2103_02046_gb300.experiments error_measure --fp64  # eq. (error_measure) vs height
   python -m paper_2103_02046_gb300.experiments action     # discrete EL residual, action stationarity
+  python -m paper_2103_02046_gb300.experiments box_potentials [--save f.npz]  # grounded-box figure
 
 Each prints one JSON line. Everything runs through the C ABI (``p3m``); no oracle is used.
 
@@ -355,13 +356,81 @@ def action(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps: i
             "dS_off_trajectory_rel": off / kin}
 
 
+def box_potentials(precision: int = m.FP64, n_particles: int = 0, save: str = ""):
+    """The three potentials of the paper's grounded-box figure (fig. boundary_gauss_seidel_results)
+    for two opposite charges in a grounded box of 50^3 nodes (h = 0.1 mm, r_c = 2h, kappa = 3):
+    phi^L from the box solve (pm_bc = 2), phi^S = k_e q erfc(alpha r)/r, and phi^tot, the discrete
+    Poisson solution of the unscreened assigned charges (the same solve with the screening
+    switched off). The API carries one charge value, so +q at A and -q at B come from two
+    single-charge solves (P3M is linear in the charges). Reports, on the nodes farther than 2 r_c
+    from both charges, the relative L2 difference between phi^S + phi^L and phi^tot, and the
+    reach of phi^S; saves the mid-plane slices to `save` (.npz) when given."""
+    from scipy.special import erfc as _erfc
+    k_e = 8.9875517923e9
+    n, h = 50, 1e-4
+    q = B.macro_charge()
+    lo = (0.0, 0.0, 0.0)
+    centre = np.array([24.5, 24.5, 24.5]) * h
+    A = centre + np.array([-6.0, 0.0, 0.0]) * h + np.array([0.0, 0.5, 0.5]) * h
+    Bp = centre + np.array([6.0, 0.0, 0.0]) * h + np.array([0.0, 0.5, 0.5]) * h
+
+    def potential(pos, screened=True):
+        prm = m.Params(n=(n, n, n), lo=lo, h=(h, h, h), rc_over_h=2.0, pm_bc=2, precision=m.FP64,
+                       q=q, alpha=0.0 if screened else 1e14)
+        ctx = m.Context(prm, 1)
+        ctx.deposit(_cuda(pos[None, :]))
+        ctx.solve()
+        phi = ctx.get_mesh(1).cpu().numpy()      # [z, y, x]
+        ctx.sync()
+        ctx.close()
+        return phi
+
+    phiL = potential(A) - potential(Bp)
+    phiT = potential(A, False) - potential(Bp, False)
+    g = np.arange(n) * h
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    nodes = np.stack([X, Y, Z], -1)
+    rc = 2 * h
+    alpha = 3.0 / rc
+
+    def short(c):
+        r = np.linalg.norm(nodes - c, axis=-1)
+        return np.where(r > 0, k_e * q * _erfc(alpha * r) / np.maximum(r, 1e-30), 0.0)
+
+    phiS = short(A) - short(Bp)
+    far = (np.linalg.norm(nodes - A, axis=-1) > 2 * rc) & (np.linalg.norm(nodes - Bp, axis=-1) > 2 * rc)
+    inner = np.zeros_like(far)
+    inner[1:-1, 1:-1, 1:-1] = True
+    mask = far & inner
+    diff = (phiS + phiL - phiT)[mask]
+    out = {"experiment": "box_potentials", "n": n, "h": h, "r_c": rc,
+           "rel_l2_phiS_plus_phiL_vs_phiTot_far": float(np.linalg.norm(diff) /
+                                                        np.linalg.norm(phiT[mask])),
+           "max_abs_phiS_beyond_rc_over_max_phiL": float(
+               np.abs(phiS[~((np.linalg.norm(nodes - A, axis=-1) <= rc) |
+                             (np.linalg.norm(nodes - Bp, axis=-1) <= rc))]).max() /
+               np.abs(phiL).max()),
+           "faces_max_abs_phiL": float(max(np.abs(phiL[0]).max(), np.abs(phiL[-1]).max(),
+                                           np.abs(phiL[:, 0]).max(), np.abs(phiL[:, -1]).max(),
+                                           np.abs(phiL[:, :, 0]).max(), np.abs(phiL[:, :, -1]).max())),
+           "max_abs": {"phiL": float(np.abs(phiL).max()), "phiS": float(np.abs(phiS).max()),
+                       "phiTot": float(np.abs(phiT).max())}}
+    if save:
+        zc = 24
+        np.savez(save, phiL=phiL[zc], phiS=phiS[zc], phiTot=phiT[zc], h=h)
+    return out
+
+
 def main(argv):
     which = argv[1] if len(argv) > 1 else "boundary"
     kw = {"precision": m.FP64 if "--fp64" in argv else m.FP32_MIXED}
     if "--n" in argv:
         kw["n_particles"] = int(argv[argv.index("--n") + 1])
+    if "--save" in argv:
+        kw["save"] = argv[argv.index("--save") + 1]
     fn = {"boundary": boundary, "energy": energy, "gradient": gradient,
-          "influence": influence, "error_measure": error_measure, "action": action}[which]
+          "influence": influence, "error_measure": error_measure, "action": action,
+          "box_potentials": box_potentials}[which]
     print(json.dumps(fn(**kw)), flush=True)
 
 

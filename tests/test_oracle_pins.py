@@ -535,3 +535,37 @@ def test_box_wall_image_attraction(dn):
     expect = -O.coulomb_k() * P.q ** 2 * (1 / (2 * d) ** 2 - 1 / (2 * top) ** 2)
     assert abs(F[2] / expect - 1) <= 0.05
     assert abs(F[0]) <= 1e-12 * abs(F[2]) and abs(F[1]) <= 1e-12 * abs(F[2])
+
+
+# ------------------------------------------------------------------------------------------
+# central-difference mesh gradient (alternative long-range force)
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [1, 2])
+def test_central_difference_force_conserves_momentum(order):
+    # with the same assignment for charge and force, a symmetric Green's function G and the
+    # antisymmetric difference operator D: sum_i F_i = -Q^T D G Q = 0; the analytic-derivative
+    # force carries the grid self-force and does not conserve momentum
+    x = B.gaussian(2000, (1e-3, 1.2e-3, 0.8e-3), 61)
+    for fd, bound in ((1, 1e-11), (0, None)):
+        P = O.auto_mesh(x, 16, force_diff=fd, assign_order=order)
+        F = O.forces(x, P, parts=2).F_pm
+        ratio = np.abs(F.sum(0)).max() / np.abs(F).max()
+        if bound:
+            assert ratio <= bound
+        else:
+            assert ratio >= 1e-3
+
+
+def test_central_difference_force_exact_for_quadratic_potentials():
+    # central differences are exact for quadratics and TSC reproduces linear functions, so
+    # phi = a.x gives F = -q a and phi = sum_d b_d x_d^2 / 2 gives F_d = -q b_d xi_d exactly
+    x = B.gaussian(500, (1e-3, 1.2e-3, 0.8e-3), 62)
+    P = O.auto_mesh(x, 16, force_diff=1)
+    g = [np.arange(P.n[d]) * P.h[d] + P.lo[d] for d in range(3)]
+    Z, Y, X = np.meshgrid(g[2], g[1], g[0], indexing="ij")
+    a = np.array([3.0, -2.0, 1.5])
+    F = O.interp_central(x, a[0] * X + a[1] * Y + a[2] * Z, P)
+    assert np.abs(F + P.q * a).max() <= 1e-13 * P.q * np.abs(a).max()
+    b = np.array([2.0, 1.0, -3.0])
+    F = O.interp_central(x, 0.5 * (b[0] * X ** 2 + b[1] * Y ** 2 + b[2] * Z ** 2), P)
+    assert np.abs(F + P.q * b * x).max() <= 1e-13 * np.abs(P.q * b * x).max()
