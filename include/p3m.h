@@ -78,6 +78,13 @@ typedef struct p3m_params {
   int32_t adj_segment;   /* steps per checkpoint segment in p3m_backward */
   double q;              /* macro-particle charge [C] (all particles equal) */
   double mass;           /* macro-particle mass [kg] */
+  int32_t force_diff;    /* long-range force: 0 = analytic derivative of the assignment function
+                            (the variational force of eq. (eom_p3m_coord), default), 1 = central
+                            differences of the mesh potential, -(phi_{g+e} - phi_{g-e}) / 2h,
+                            interpolated with the assignment function (conserves momentum; not
+                            variational, so p3m_force_vjp and p3m_backward refuse it with
+                            P3M_ESTATE); every particle's assignment support must then keep one
+                            node off the mesh edge (else P3M_ERANGE) */
 } p3m_params;
 
 typedef struct p3m_ctx p3m_ctx; /* opaque; owns all scratch memory */

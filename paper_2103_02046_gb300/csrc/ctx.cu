@@ -57,6 +57,7 @@ p3m_status validate(const p3m_params* p, std::string* why) {
   if (p->influence < 0 || p->influence > 2) { *why = "influence must be 0, 1 or 2"; return P3M_EINVAL; }
   if (p->precision != P3M_FP64 && p->precision != P3M_FP32_MIXED) { *why = "precision must be 0 or 1"; return P3M_EINVAL; }
   if (p->deterministic != 0) { *why = "deterministic must be 0"; return P3M_EINVAL; }
+  if (p->force_diff != 0 && p->force_diff != 1) { *why = "force_diff must be 0 or 1"; return P3M_EINVAL; }
   if (p->adj_slots < 0 || p->adj_segment < 0 || (p->adj_slots > 0 && p->adj_segment < 1)) { *why = "adj_slots/adj_segment invalid"; return P3M_EINVAL; }
   if (!std::isfinite(p->q) || p->q == 0.0) { *why = "q must be finite and nonzero"; return P3M_EINVAL; }
   if (!finite_pos(p->mass)) { *why = "mass must be > 0"; return P3M_EINVAL; }
@@ -123,6 +124,7 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   }
   g.order = p->assign_order;
   g.pm_bc = p->pm_bc;
+  g.force_diff = p->force_diff;
   g.pp_bc = p->pp_bc;
   g.zc = p->z_cathode;
   g.img_c = 2.0 * (p->z_cathode - p->lo[2]) / g.rc;
@@ -433,6 +435,7 @@ p3m_status p3m_default_params(p3m_params* p) {
   p->pp_bc = 0;
   p->z_cathode = 0.0;
   p->influence = 0;
+  p->force_diff = 0;
   p->precision = P3M_FP64;
   p->deterministic = 0;
   p->adj_slots = 0;
@@ -732,6 +735,8 @@ p3m_status p3m_push(p3m_ctx* c, double* x, double* p, int64_t n, double dt, int3
 p3m_status p3m_force_vjp(p3m_ctx* c, const double* x, int64_t n, const double* w, double* out) {
   if (!c) return P3M_EINVAL;
   if ((!x || !w || !out) && n > 0) return fail(c, P3M_EINVAL, "NULL argument");
+  if (c->g.force_diff)
+    return fail(c, P3M_ESTATE, "the adjoint needs the variational force (force_diff = 0)");
   p3m_status s = take_deferred(c);
   if (s != P3M_OK) return s;
   if ((s = check_n(c, n)) != P3M_OK) return s;
@@ -747,6 +752,8 @@ p3m_status p3m_backward(p3m_ctx* c, const double* x0, const double* p0, int64_t 
   if ((!x0 || !p0 || !gx_T || !gp_T || !gx0 || !gp0) && n > 0)
     return fail(c, P3M_EINVAL, "NULL argument");
   if (c->prm.adj_slots <= 0) return fail(c, P3M_ESTATE, "context created with adj_slots = 0");
+  if (c->g.force_diff)
+    return fail(c, P3M_ESTATE, "the adjoint needs the variational force (force_diff = 0)");
   const int C = c->prm.adj_segment;
   if (nsteps < 1 || static_cast<int64_t>(c->prm.adj_slots) * C < nsteps || !std::isfinite(dt))
     return fail(c, P3M_EINVAL, "nsteps must be in [1, adj_slots * adj_segment]");

@@ -41,6 +41,7 @@ struct Geom {
   int nc[3];     // cells per axis
   int order;     // 1 CIC, 2 TSC
   int pm_bc, pp_bc;
+  int force_diff;  // 1: long-range force from central differences of the mesh potential
   double lo[3], h[3];
   double rc, alpha, zc;
   double q, mass, ke;

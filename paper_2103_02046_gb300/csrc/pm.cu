@@ -486,6 +486,42 @@ __device__ __forceinline__ void grad_from_phi(const Geom& g, const double* __res
     }
 }
 
+// Central-difference field, interpolated with W (force_diff = 1): G_d = sum_g W (phi_{g+e_d} -
+// phi_{g-e_d}) / 2 in mesh units (F = -q G / h as for the analytic derivative). FP32 from the
+// forward differences D_d(g) = phi_{g+e_d} - phi_g, FP64 from phi.
+__device__ __forceinline__ void grad_central_diff(const Geom& g, const float* __restrict__ D,
+                                                  size_t nreal, const Axis<float> ax[3],
+                                                  float G[3]) {
+  const int S = g.order == 2 ? 3 : 2;
+  const size_t stride[3] = {1, static_cast<size_t>(g.M[0]),
+                            static_cast<size_t>(g.M[0]) * g.M[1]};
+  G[0] = G[1] = G[2] = 0.f;
+  for (int c = 0; c < S; ++c)
+    for (int b = 0; b < S; ++b)
+      for (int a = 0; a < S; ++a) {
+        const float W = ax[0].w[a] * ax[1].w[b] * ax[2].w[c];
+        const size_t r = real_index(g, ax[0].c + a, ax[1].c + b, ax[2].c + c);
+        for (int d = 0; d < 3; ++d) G[d] += W * (D[d * nreal + r] + D[d * nreal + r - stride[d]]);
+      }
+  for (int d = 0; d < 3; ++d) G[d] *= 0.5f;
+}
+
+__device__ __forceinline__ void grad_central_phi(const Geom& g, const double* __restrict__ phi,
+                                                 const Axis<double> ax[3], double G[3]) {
+  const int S = g.order == 2 ? 3 : 2;
+  const size_t stride[3] = {1, static_cast<size_t>(g.M[0]),
+                            static_cast<size_t>(g.M[0]) * g.M[1]};
+  G[0] = G[1] = G[2] = 0.0;
+  for (int c = 0; c < S; ++c)
+    for (int b = 0; b < S; ++b)
+      for (int a = 0; a < S; ++a) {
+        const double W = ax[0].w[a] * ax[1].w[b] * ax[2].w[c];
+        const size_t r = real_index(g, ax[0].c + a, ax[1].c + b, ax[2].c + c);
+        for (int d = 0; d < 3; ++d) G[d] += W * (phi[r + stride[d]] - phi[r - stride[d]]);
+      }
+  for (int d = 0; d < 3; ++d) G[d] *= 0.5;
+}
+
 template <typename T>
 __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
                          const typename RecT<T>::type* __restrict__ recm,
@@ -502,7 +538,10 @@ __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
     float F[3] = {0.f, 0.f, 0.f};
     if (parts & 2) {
       float G[3];
-      grad_from_diff(g, field, nreal, ax, G);
+      if (g.force_diff)
+        grad_central_diff(g, field, nreal, ax, G);
+      else
+        grad_from_diff(g, field, nreal, ax, G);
       for (int d = 0; d < 3; ++d) F[d] = g.fscale_f[d] * G[d];
     }
     float4* out = reinterpret_cast<float4*>(fpp) + i;
@@ -517,7 +556,10 @@ __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
     double F[3] = {0.0, 0.0, 0.0};
     if (parts & 2) {
       T G[3];
-      grad_from_phi(g, field, ax, G);
+      if (g.force_diff)
+        grad_central_phi(g, field, ax, G);
+      else
+        grad_from_phi(g, field, ax, G);
       for (int d = 0; d < 3; ++d) F[d] = g.fscale[d] * static_cast<double>(G[d]);
     }
     D4* out = reinterpret_cast<D4*>(fpp) + i;

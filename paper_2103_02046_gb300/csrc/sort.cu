@@ -44,8 +44,9 @@ __device__ __forceinline__ int particle_cell(const Geom& g, const double* __rest
     const float f = df_sub(df_from_double(xi[d]), DF{g.lo_df[d][0], g.lo_df[d][1]}).hi;
     if (!(f == f)) return kErrNaN;
     const float s = f * g.inv_h_f[d];
-    // in the grounded box the support must also stay off the face nodes: one node less per side
-    const int box = g.pm_bc == 2 ? 1 : 0;
+    // in the grounded box, and for central differences of phi, the support must also stay off
+    // the edge nodes: one node less per side
+    const int box = (g.pm_bc == 2 || g.force_diff) ? 1 : 0;
     const float b0 = ((g.order == 2) ? 0.5f : 0.0f) + box;
     const float b1 = static_cast<float>(g.n[d] - box) - ((g.order == 2) ? 1.5f : 1.0f);
     bool ok;

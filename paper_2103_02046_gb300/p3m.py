@@ -48,6 +48,7 @@ class CParams(ctypes.Structure):
         ("adj_segment", ctypes.c_int32),
         ("q", ctypes.c_double),
         ("mass", ctypes.c_double),
+        ("force_diff", ctypes.c_int32),
     ]
 
 
@@ -128,6 +129,7 @@ class Params:
     adj_segment: int = 0
     q: float = 1e-15
     mass: float = 1e-15 / 1.602176634e-19 * 9.1093837015e-31
+    force_diff: int = 0  # 1 = central-difference mesh gradient (not the variational force)
 
     def to_c(self) -> CParams:
         c = CParams()

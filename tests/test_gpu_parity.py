@@ -4,6 +4,7 @@ on the same seeded inputs.
 Tolerances (relative L2 over all components): FP64 path 1e-12, FP32 mixed path 1e-5; the
 in-cutoff pair count is an integer decided in FP64 on both sides and must match exactly.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -211,6 +212,41 @@ def test_grounded_box_refusals_and_faces():
     f = ctx.forces(cuda(x[:20]))
     ctx.sync()
     assert rel(f, O.forces(x[:20], P).F) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n,order,pm_bc", [(16, 2, 1), (32, 2, 0), (32, 1, 0)],
+                         ids=["cathode16", "open32_tsc", "open32_cic"])
+def test_central_difference_force_parity(precision, n, order, pm_bc):
+    x = bunch_4k(pm_bc == 1)
+    P = O.auto_mesh(x, n, rc_over_h=2.0, pm_bc=pm_bc, z_cathode=0.0, assign_order=order,
+                    force_diff=1)
+    ref = O.forces(x, P)
+    ctx = p3m().Context(gpu_params(P, precision, force_diff=1), len(x))
+    xg = cuda(x)
+    f_pm = ctx.forces(xg, parts=2)
+    f = ctx.forces(xg)
+    ctx.sync()
+    assert rel(f_pm, ref.F_pm) <= TOL[precision]
+    assert rel(f, ref.F) <= TOL[precision]
+    # momentum: with open boundaries sum_i F^L_i = 0 for central differences (up to rounding of
+    # the path); the cathode's image attraction is an external force
+    if pm_bc == 0:
+        s = float(f_pm.sum(0).abs().max()) / float(f_pm.abs().max())
+        assert s <= (1e-10 if precision == 0 else 1e-4)
+    with pytest.raises(p3m().P3MError) as ei:
+        ctx.force_vjp(xg, torch.ones_like(xg))
+    assert ei.value.status == p3m().P3M_ESTATE
+
+
+def test_central_difference_force_in_the_grounded_box():
+    x, P = _box_case()
+    P = dataclasses.replace(P, force_diff=1)
+    ref = O.forces(x, P)
+    ctx = p3m().Context(gpu_params(P, 0, force_diff=1), len(x))
+    f = ctx.forces(cuda(x))
+    ctx.sync()
+    assert rel(f, ref.F) <= 1e-12
 
 
 def test_auto_mesh_matches_oracle():
