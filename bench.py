@@ -38,10 +38,10 @@ FLOPS_PER_PAIR = 37.0  # algorithmic FP32 flops per in-cutoff pair (FFMA = 2, in
 KERNELS_PER_EVAL = 10  # bin, 3 scan passes, scatter, short range, deposit, Green multiply,
                        # interpolation + combination, unpermute (cuFFT's kernels not counted)
 # DRAM bytes (read + write) of one k_pp_f32<12> launch per particle, from an ncu capture of the
-# 2,097,152-particle sphere on a 128^3 mesh (125.4 MB per launch, profiles/k_pp_f32_sphere2m_128.md).
+# 2,097,152-particle sphere on a 128^3 mesh (123.9 MB per launch, profiles/k_pp_f32_sphere2m_128.md).
 # The kernel reads each 32-B record about once from DRAM (the neighbour runs and the reduction
 # targets stay in L2), so its traffic scales with the particle count at fixed density.
-PP_DRAM_BYTES_PER_PARTICLE = (110.684672e6 + 14.723072e6) / 2097152
+PP_DRAM_BYTES_PER_PARTICLE = (110.77248e6 + 13.134336e6) / 2097152
 
 
 def parse():
@@ -318,7 +318,7 @@ def run_ours(a, rank, world, local_rank):
             ["bin_sort", "short_range", "deposit", "solve", "interp_combine", "total"], t64))},
         "error": {"fp32_vs_fp64_gpu_rel_l2": err32},
         "roofline": {"bound": "alu", "kernel": "k_pp_f32 (short range)",
-                     "limiter": "L1 data pipe ~92%, issue ~78% (ncu, "
+                     "limiter": "instruction issue ~77%, L1 data pipe ~61% (ncu, "
                                 "profiles/k_pp_f32_sphere2m_128.md)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": PP_DRAM_BYTES_PER_PARTICLE * N,

@@ -112,30 +112,43 @@ struct PosD {
 };
 
 // ------------------------------------------------------------------------------------------
-// FP32 short range: each unordered pair once (Newton's third law), lanes walking their own
-// candidate lists in lockstep.
+// FP32 short range: each unordered pair once (Newton's third law), each lane holding two
+// particles and walking their candidate lists in lockstep with the other lanes.
 //
 // Pairs: particle i takes the pairs (i, j) with j > i in sorted order. Sorted order is row-major
 // over (z row, y row, x cell), so these are the later part of i's own row and the 12 neighbour
 // rows after it (dz > 0, or dz = 0 and dy > 0) -- 13 of the 25 rows. i's row is the one the sort
 // put it in (stored with the record), so every pair is taken by exactly one of its particles.
-// The force on i accumulates in registers; the reaction -f goes to j by one vector reduction
-// (red.global.add.v4.f32) into the zeroed result array, and i's own sum is added the same way
-// at the end.
 //
-// Walk: each lane first writes its non-empty candidate runs (at most 13) to shared memory, then
-// the warp steps through them together, two candidates per lane per step; a lane moves on to its
-// next run as soon as one ends, so a warp takes as many steps as its longest lane's total
-// rather than the sum over rows of each row's longest run. Lanes with nothing left re-read their
-// own record (separation 0, never a pair). Control flow is warp-uniform: the pair function runs,
-// predicated, whenever any lane holds a pair. Separations are exact to FP32 relative rounding
-// ((hi_i - hi_j) + (lo_i - lo_j)). FP32 partial sums are folded into a two-float (TwoSum)
-// accumulator every 8 steps.
+// Lanes: lane l of a tile holds the sorted particles a = 2l and b = 2l + 1 (adjacent in sorted
+// order, so nearly always in the same row and a quarter cutoff apart or less). Per neighbour row
+// the lane walks the hull of the two particles' runs and tests every loaded record against
+// both: one 256-bit load serves two particles, which halves the record traffic of the short
+// range (the L1 data pipe bounds this kernel). Each pair is still taken exactly once: a pair
+// (i, j) counts only when j > i and |xi_i - xi_j| < r_c, and the hull holds no record twice.
+// When a and b lie in different rows (a row boundary) the lane keeps both run lists, each
+// tested against its own particle only.
+//
+// The force on a and b accumulates in registers; the reaction on j (both particles' share) goes
+// to j by one predicated vector reduction (red.global.add.v4.f32) into the zeroed result array,
+// and a's and b's own sums are added the same way at the end.
+//
+// Walk: each lane first writes its non-empty runs (at most 13, or 26 across a row boundary) to
+// shared memory, then the warp steps through them together, two records per lane per step; a
+// lane moves on to its next run as soon as one ends. Lanes with nothing left re-read record 0
+// with every result masked. The step is straight-line code: the pair function runs for every
+// lane and candidate and its results are selected by the hit predicate, since with 64 lane
+// candidates per step some lane nearly always holds a pair. Separations are exact to FP32
+// relative rounding ((hi_i - hi_j) + (lo_i - lo_j)). FP32 partial sums are folded into a
+// two-float (TwoSum) accumulator every 8 steps.
 // The pair function uses one ex2 for both e^{-kappa^2 rho^2} terms and the fitted polynomial
-// R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}.
+// R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}; rsqrt and ex2 are the
+// hardware approximations (flush-to-zero: every argument here is a normal number).
 // ------------------------------------------------------------------------------------------
 constexpr int kHalfRows = kRowSpan * kRowSpan / 2 + 1;  // own row + the 12 after it
-constexpr int kPpBlocksPerSm = 10;  // resident blocks per SM (48 registers per thread)
+constexpr int kPairRuns = 2 * kHalfRows;           // a's and b's runs across a row boundary
+constexpr int kPpBlocksPerSm = 6;    // resident blocks per SM of the short range (80 registers)
+constexpr int kVjpBlocksPerSm = 10;  // resident blocks per SM of its adjoint (48 registers)
 
 // One 32-byte record (hi and lo float4) in a single 256-bit load through the read-only path.
 // The records array is 32-byte aligned and not written while the short range runs.
@@ -149,6 +162,43 @@ __device__ __forceinline__ void red_add_v4(float4* dst, float a, float b, float 
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(a), "f"(b),
                "f"(c), "f"(d)
                : "memory");
+}
+
+// predicated form: the reduction happens only where p holds (no branch around it)
+__device__ __forceinline__ void red_add_v4_if(bool p, float4* dst, float a, float b, float c,
+                                              float d) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t"
+      "@q red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(dst),
+      "f"(a), "f"(b), "f"(c), "f"(d), "r"(static_cast<int>(p))
+      : "memory");
+}
+
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// pair_poly on the hardware approximations; r2 in (0, 1]
+template <int kDeg>
+__device__ __forceinline__ void pair_poly_hw(const PairPoly& P, float r2, float& fco,
+                                             float& pot) {
+  const float rinv = rsqrt_ftz(r2);
+  const float rho = r2 * rinv;
+  const float t = fmaf(2.f, rho, -1.f);
+  float R = P.c[kDeg];
+#pragma unroll
+  for (int m = kDeg - 1; m >= 0; --m) R = fmaf(R, t, P.c[m]);
+  const float ex = ex2_ftz(-P.kappa2_log2e * r2);
+  pot = R * ex * rinv;
+  fco = fmaf(P.c2k, ex, pot) * (rinv * rinv);
 }
 
 template <int kDeg>
@@ -196,135 +246,198 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
              const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
              float4* __restrict__ fpp, uint32_t* __restrict__ next_tile,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
-  __shared__ uint32_t run_j0[kHalfRows][kThreads], run_j1[kHalfRows][kThreads];
+  constexpr uint32_t kTile = 2 * kThreads;  // particles per tile
+  constexpr int kFirst = kRowSpan * kRowSpan / 2, kLast = kRowSpan * kRowSpan;  // half shell
+  __shared__ uint32_t run_j0[kPairRuns][kThreads], run_j1[kPairRuns][kThreads];
   __shared__ uint32_t tile_s;
   const int tid = threadIdx.x;
   const uint32_t N = *total;
   double e_acc = 0.0;
   unsigned long long np = 0, ni = 0;
-  // persistent blocks: each takes the next tile of kThreads sorted particles until none is left
+  // persistent blocks: each takes the next tile of kTile sorted particles until none is left
+  // (the block's four warps work on adjacent particles, which share most of their neighbours
+  // in L1)
   for (;;) {
     if (tid == 0) tile_s = atomicAdd(next_tile, 1u);
     __syncthreads();
     const uint32_t tile = tile_s;
     __syncthreads();
-    if (static_cast<uint64_t>(tile) * kThreads >= N) break;
-    const uint32_t i = tile * kThreads + tid;
-    const bool alive = i < N;
-    // lanes past the last particle have no candidates; they read record 0 (in bounds) and take
-    // part in the lockstep loop with every result masked out
-    const uint32_t ie = alive ? i : 0u;
-    const float4 pi = rec[2 * ie], li = rec[2 * ie + 1];
-    int cnt = 0;
-    if (alive) {
-      const uint32_t row = __float_as_uint(li.w) & kRowMask;
-      const int cy = static_cast<int>(row % static_cast<uint32_t>(g.nc[1]));
-      const int cz = static_cast<int>(row / static_cast<uint32_t>(g.nc[1]));
-      for (int r = kRowSpan * kRowSpan / 2; r < kRowSpan * kRowSpan; ++r) {
+    if (static_cast<uint64_t>(tile) * kTile >= N) break;
+    const uint32_t ia = tile * kTile + 2 * tid, ib = ia + 1;
+    const bool alive_a = ia < N, alive_b = ib < N;
+    // lanes past the last particle read record 0 (in bounds) and take part in the lockstep
+    // loop with every result masked out
+    const uint32_t ea = alive_a ? ia : 0u, eb = alive_b ? ib : ea;
+    const float4 pa = rec[2 * ea], la = rec[2 * ea + 1];
+    const float4 pb = rec[2 * eb], lb = rec[2 * eb + 1];
+    // runs: with a and b in one row, the hull of their two runs per neighbour row (tested
+    // against both); otherwise a's runs [0, split) and b's runs [split, cnt)
+    int cnt = 0, split = 0;
+    bool same = true;
+    if (alive_a) {
+      const uint32_t row_a = __float_as_uint(la.w) & kRowMask;
+      const uint32_t row_b = __float_as_uint(lb.w) & kRowMask;
+      same = !alive_b || row_a == row_b;
+      const int cya = static_cast<int>(row_a % static_cast<uint32_t>(g.nc[1]));
+      const int cza = static_cast<int>(row_a / static_cast<uint32_t>(g.nc[1]));
+      for (int r = kFirst; r < kLast; ++r) {
         uint32_t j0, j1;
-        row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
-        j0 = max(j0, i + 1);  // own row: only the particles after i (a no-op for later rows)
+        row_range(g, starts, pa.x, pa.y, pa.z, cya, cza, r, j0, j1);
+        j0 = max(j0, ia + 1);  // own row: only the particles after a (a no-op for later rows)
+        if (same && alive_b) {
+          uint32_t k0, k1;
+          row_range(g, starts, pb.x, pb.y, pb.z, cya, cza, r, k0, k1);
+          k0 = max(k0, ib + 1);
+          if (k0 < k1) {
+            j0 = j0 < j1 ? min(j0, k0) : k0;
+            j1 = max(j1, k1);
+          }
+        }
         if (j0 < j1) {
           run_j0[cnt][tid] = j0;
           run_j1[cnt][tid] = j1;
           ++cnt;
         }
       }
+      split = cnt;
+      if (!same) {
+        const int cyb = static_cast<int>(row_b % static_cast<uint32_t>(g.nc[1]));
+        const int czb = static_cast<int>(row_b / static_cast<uint32_t>(g.nc[1]));
+        for (int r = kFirst; r < kLast; ++r) {
+          uint32_t j0, j1;
+          row_range(g, starts, pb.x, pb.y, pb.z, cyb, czb, r, j0, j1);
+          j0 = max(j0, ib + 1);
+          if (j0 < j1) {
+            run_j0[cnt][tid] = j0;
+            run_j1[cnt][tid] = j1;
+            ++cnt;
+          }
+        }
+      }
     }
     uint32_t ptr = 0, end = 0;
+    int k = 0;
     if (cnt > 0) {
       ptr = run_j0[0][tid];
       end = run_j1[0][tid];
     }
-    int k = 0;
-    Acc2 sum[4];
-    for (int c = 0; c < 4; ++c) sum[c].hi = sum[c].lo = 0.f;
-    float part[4] = {0.f, 0.f, 0.f, 0.f};
-    auto test = [&](const float4* pj, float& rx, float& ry, float& rz) {
-      float4 hj, lj;
-      load_rec32(pj, hj, lj);
-      rx = (pi.x - hj.x) + (li.x - lj.x);
-      ry = (pi.y - hj.y) + (li.y - lj.y);
-      rz = (pi.z - hj.z) + (li.z - lj.z);
-      return rx * rx + ry * ry + rz * rz;
-    };
-    auto pair = [&](bool hit, float r2, float rx, float ry, float rz, uint32_t j) {
-      float fco, pot;
-      pair_poly<kDeg>(P, hit ? r2 : 0.5f, fco, pot);
-      fco = hit ? fco : 0.f;
-      pot = hit ? pot : 0.f;
-      part[0] = fmaf(fco, rx, part[0]);
-      part[1] = fmaf(fco, ry, part[1]);
-      part[2] = fmaf(fco, rz, part[2]);
-      part[3] += pot;
-      np += hit;
-      if (hit) red_add_v4(fpp + j, -fco * rx, -fco * ry, -fco * rz, pot);
+    bool ta = same || split > 0;                  // the current run is tested against a
+    bool tb = alive_b && (same || split == 0);    // ... and against b
+    Acc2 sa[4], sb[4];
+    for (int c = 0; c < 4; ++c) sa[c].hi = sa[c].lo = sb[c].hi = sb[c].lo = 0.f;
+    float qa[4] = {0.f, 0.f, 0.f, 0.f}, qb[4] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t np_part = 0;
+    // one candidate record j (hj, lj) against a and b
+    auto cand = [&](bool v, uint32_t j, const float4& hj, const float4& lj) {
+      const float ax = (pa.x - hj.x) + (la.x - lj.x);
+      const float ay = (pa.y - hj.y) + (la.y - lj.y);
+      const float az = (pa.z - hj.z) + (la.z - lj.z);
+      const float bx = (pb.x - hj.x) + (lb.x - lj.x);
+      const float by = (pb.y - hj.y) + (lb.y - lj.y);
+      const float bz = (pb.z - hj.z) + (lb.z - lj.z);
+      const float r2a = ax * ax + ay * ay + az * az;
+      const float r2b = bx * bx + by * by + bz * bz;
+      // coincident particles (r2 == 0) are skipped
+      const bool ha = v && ta && r2a < 1.f && r2a > 0.f;
+      const bool hb = v && tb && r2b < 1.f && r2b > 0.f;
+      float fa, ua, fb, ub;
+      pair_poly_hw<kDeg>(P, ha ? r2a : 0.5f, fa, ua);
+      pair_poly_hw<kDeg>(P, hb ? r2b : 0.5f, fb, ub);
+      fa = ha ? fa : 0.f;
+      ua = ha ? ua : 0.f;
+      fb = hb ? fb : 0.f;
+      ub = hb ? ub : 0.f;
+      const float fax = fa * ax, fay = fa * ay, faz = fa * az;
+      const float fbx = fb * bx, fby = fb * by, fbz = fb * bz;
+      qa[0] += fax;
+      qa[1] += fay;
+      qa[2] += faz;
+      qa[3] += ua;
+      qb[0] += fbx;
+      qb[1] += fby;
+      qb[2] += fbz;
+      qb[3] += ub;
+      np_part += static_cast<uint32_t>(ha) + static_cast<uint32_t>(hb);
+      red_add_v4_if(ha || hb, fpp + j, -(fax + fbx), -(fay + fby), -(faz + fbz), ua + ub);
     };
     int step = 0;
     while (__any_sync(0xffffffffu, ptr < end)) {
       // a lane without a candidate reads record 0, as every such lane does, so that the load
-      // costs the warp one extra sector at most; its result is masked out
+      // costs the warp one extra sector at most; its results are masked out
       const bool va = ptr < end, vb = ptr + 1 < end;
-      const float4* pa = va ? rec + 2 * static_cast<size_t>(ptr) : rec;
-      const float4* pb = vb ? rec + 2 * static_cast<size_t>(ptr + 1) : rec;
-      float ax, ay, az, bx, by, bz;
-      const float ra = test(pa, ax, ay, az);
-      const float rb = test(pb, bx, by, bz);
-      const bool ha = va && ra < 1.f && ra > 0.f;  // coincident particles (r2 == 0) are skipped
-      const bool hb = vb && rb < 1.f && rb > 0.f;
-      if (__any_sync(0xffffffffu, ha)) pair(ha, ra, ax, ay, az, ptr);
-      if (__any_sync(0xffffffffu, hb)) pair(hb, rb, bx, by, bz, ptr + 1);
+      const uint32_t ja = va ? ptr : 0u, jb = vb ? ptr + 1 : 0u;
+      float4 h0, l0, h1, l1;  // both loads in flight before either record is used
+      load_rec32(rec + 2 * static_cast<size_t>(ja), h0, l0);
+      load_rec32(rec + 2 * static_cast<size_t>(jb), h1, l1);
+      cand(va, ja, h0, l0);
+      cand(vb, jb, h1, l1);
       ptr += 2;
       if (ptr >= end && ++k < cnt) {
         ptr = run_j0[k][tid];
         end = run_j1[k][tid];
+        ta = same || k < split;
+        tb = alive_b && (same || k >= split);
       }
       if ((++step & 7) == 0) {
         for (int c = 0; c < 4; ++c) {
-          sum[c].add(part[c]);
-          part[c] = 0.f;
+          sa[c].add(qa[c]);
+          sb[c].add(qb[c]);
+          qa[c] = qb[c] = 0.f;
         }
+        np += np_part;
+        np_part = 0;
       }
     }
-    for (int c = 0; c < 4; ++c) sum[c].add(part[c]);
-    const float pair_pot = sum[3].value();
-    if (alive && g.pp_bc) {
-      // images within r_c of particles less than r_c above the cathode (rare): plain loop over
-      // all 25 rows around the image point; image pairs act on i only
+    for (int c = 0; c < 4; ++c) {
+      sa[c].add(qa[c]);
+      sb[c].add(qb[c]);
+    }
+    np += np_part;
+    const float pair_pot_a = sa[3].value(), pair_pot_b = sb[3].value();
+    // images within r_c of particles less than r_c above the cathode (rare): plain loop over
+    // all 25 rows around the image point; image pairs act on the particle only
+    auto images = [&](const float4 pi, const float4 li, Acc2* sum) {
       const double zi = static_cast<double>(pi.z) + static_cast<double>(li.z);
-      if (zi - 0.5 * g.img_c < 1.0) {
-        const float mz = static_cast<float>(g.img_c - zi);
-        const float ch = static_cast<float>(g.img_c);
-        const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
-        for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t ja, uint32_t jb) {
-          float rowv[4] = {0.f, 0.f, 0.f, 0.f};
-          for (uint32_t jj = ja; jj < jb; ++jj) {
-            const float4 hj = rec[2 * jj], lj = rec[2 * jj + 1];
-            const float ax = (pi.x - hj.x) + (li.x - lj.x);
-            const float ay = (pi.y - hj.y) + (li.y - lj.y);
-            const float s = pi.z + hj.z;
-            const float bp = s - pi.z;
-            const float e = (pi.z - (s - bp)) + (hj.z - bp);
-            const float az = ((s - ch) + e) + ((li.z + lj.z) - cl);
-            const float r2 = ax * ax + ay * ay + az * az;
-            if (r2 < 1.f && r2 > 0.f) {
-              float fco, pot;
-              pair_poly<kDeg>(P, r2, fco, pot);
-              rowv[0] -= fco * ax;
-              rowv[1] -= fco * ay;
-              rowv[2] -= fco * az;
-              rowv[3] -= pot;
-              ++ni;
-            }
+      if (zi - 0.5 * g.img_c >= 1.0) return;
+      const float mz = static_cast<float>(g.img_c - zi);
+      const float ch = static_cast<float>(g.img_c);
+      const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
+      for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t ja, uint32_t jb) {
+        float rowv[4] = {0.f, 0.f, 0.f, 0.f};
+        for (uint32_t jj = ja; jj < jb; ++jj) {
+          const float4 hj = rec[2 * jj], lj = rec[2 * jj + 1];
+          const float ax = (pi.x - hj.x) + (li.x - lj.x);
+          const float ay = (pi.y - hj.y) + (li.y - lj.y);
+          const float s = pi.z + hj.z;
+          const float bp = s - pi.z;
+          const float e = (pi.z - (s - bp)) + (hj.z - bp);
+          const float az = ((s - ch) + e) + ((li.z + lj.z) - cl);
+          const float r2 = ax * ax + ay * ay + az * az;
+          if (r2 < 1.f && r2 > 0.f) {
+            float fco, pot;
+            pair_poly<kDeg>(P, r2, fco, pot);
+            rowv[0] -= fco * ax;
+            rowv[1] -= fco * ay;
+            rowv[2] -= fco * az;
+            rowv[3] -= pot;
+            ++ni;
           }
-          for (int c = 0; c < 4; ++c) sum[c].add(rowv[c]);
-        });
-      }
+        }
+        for (int c = 0; c < 4; ++c) sum[c].add(rowv[c]);
+      });
+    };
+    if (g.pp_bc) {
+      if (alive_a) images(pa, la, sa);
+      if (alive_b) images(pb, lb, sb);
     }
-    if (alive) {
-      red_add_v4(fpp + i, sum[0].value(), sum[1].value(), sum[2].value(), sum[3].value());
-      // sum_i phi_i over ordered pairs: each pair's potential was taken once here, plus images
-      e_acc += static_cast<double>(sum[3].value()) + pair_pot;
+    // sum_i phi_i over ordered pairs: each pair's potential was taken once here, plus images
+    if (alive_a) {
+      red_add_v4(fpp + ia, sa[0].value(), sa[1].value(), sa[2].value(), sa[3].value());
+      e_acc += static_cast<double>(sa[3].value()) + pair_pot_a;
+    }
+    if (alive_b) {
+      red_add_v4(fpp + ib, sb[0].value(), sb[1].value(), sb[2].value(), sb[3].value());
+      e_acc += static_cast<double>(sb[3].value()) + pair_pot_b;
     }
   }
   if (energy) block_reduce_add(e_acc, energy);
@@ -361,7 +474,7 @@ __device__ __forceinline__ void pair_hess_poly(const PairPoly& P, float r2, floa
 }
 
 template <int kDeg>
-__global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
+__global__ void __launch_bounds__(kThreads, kVjpBlocksPerSm)
     k_pp_vjp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
                  const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
                  const float4* __restrict__ ws, float4* __restrict__ acc4,
@@ -719,7 +832,7 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
     cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
     // persistent grid of a few blocks per SM: the SM resources it leaves free let the mesh
     // chain, on the other stream, run at the same time
-    const int64_t tiles = (n + kThreads - 1) / kThreads;
+    const int64_t tiles = (n + 2 * kThreads - 1) / (2 * kThreads);  // two particles a thread
     const unsigned wblocks = static_cast<unsigned>(
         std::min<int64_t>(tiles, static_cast<int64_t>(kPpBlocksPerSm) * c->num_sms));
     auto run = [&](auto kern) {
@@ -758,7 +871,7 @@ void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s)
     cudaMemsetAsync(c->fpp, 0, sizeof(float4) * static_cast<size_t>(n), s);
     cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
     const unsigned wblocks = static_cast<unsigned>(
-        std::min<int64_t>(blocks, static_cast<int64_t>(kPpBlocksPerSm) * c->num_sms));
+        std::min<int64_t>(blocks, static_cast<int64_t>(kVjpBlocksPerSm) * c->num_sms));
     auto run = [&](auto kern) {
       kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total,
                                         static_cast<const float4*>(c->recp), c->starts, ws,

@@ -161,6 +161,35 @@ def test_lattice_pairs_at_cutoff(precision):
     assert rel(f_pp, ref.F_pp) <= TOL[precision]
 
 
+@pytest.mark.parametrize("layout", ["counts", "sparse_rows"])
+def test_fp32_short_range_lane_pairs(layout):
+    # the FP32 short range holds two adjacent sorted particles per lane: odd counts (a lane
+    # whose second particle does not exist), a single particle, and neighbours that the sort put
+    # in different cell rows (each particle then walks its own runs) must all give every pair
+    # exactly once
+    if layout == "counts":
+        x4 = bunch_4k(False)
+        P = O.auto_mesh(x4, 16, rc_over_h=2.0)
+        core = x4[np.argsort(np.linalg.norm(x4, axis=1))]  # densest first: many pairs
+        sets = [core[:n] for n in (1, 2, 3, 255, 256, 257, 513)]
+    else:
+        # about one particle per cell row, so most lanes straddle a row boundary
+        x = np.random.default_rng(7).uniform(-1e-3, 1e-3, size=(301, 3))
+        P = O.auto_mesh(x, 16, rc_over_h=1.0)
+        sets = [x, x[:300]]
+    ctx = p3m().Context(gpu_params(P, 1), max(len(s) for s in sets))
+    for x in sets:
+        ref = O.forces(x, P)
+        f_pp = ctx.forces(cuda(x), parts=1).cpu().numpy()
+        npairs, _ = ctx.pair_count()
+        ctx.sync()
+        err = np.linalg.norm(f_pp - ref.F_pp)
+        assert err <= TOL[1] * np.linalg.norm(ref.F_pp) or (ref.pairs == 0 and err == 0.0)
+        assert abs(npairs - ref.pairs) <= max(2, 1e-5 * ref.pairs)
+        if layout == "counts" and len(x) >= 255:
+            assert ref.pairs > 0
+
+
 def _box_case():
     # a bunch inside a grounded box of 20 x 24 x 28 nodes (h = 0.1 mm), supports off the faces
     x = B.gaussian(3000, (0.2e-3, 0.25e-3, 0.3e-3), 51)
