@@ -3,6 +3,7 @@
   python -m paper_2103_02046_gb300.experiments boundary   # cathode BC in the short range vs mesh error
   python -m paper_2103_02046_gb300.experiments energy     # leapfrog energy drift and momentum
   python -m paper_2103_02046_gb300.experiments gradient   # adjoint gradient vs finite differences
+  python -m paper_2103_02046_gb300.experiments gradient_coords --fp64  # ... on single coordinates
   python -m paper_2103_02046_gb300.experiments influence  # P3M error vs exact Coulomb per kernel
   python -m paper_2103_02046_gb300.experiments error_measure --fp64  # eq. (error_measure) vs height
   python -m paper_2103_02046_gb300.experiments action     # discrete EL residual, action stationarity
@@ -26,6 +27,12 @@ Each prints one JSON line. Everything runs through the C ABI (``p3m``); no oracl
   central finite differences along two directions that change J at first order (dilations of
   x0 and of p0 about their means), relative step 1e-6 in FP64 and 1e-3 in FP32 (the evaluation
   order of the FP32 force sums is not fixed, which leaves J reproducible to about 1e-7).
+* gradient_coords: the same bunch and schedule at 16,384 particles, FP64: the reverse pass
+  against central finite differences on 64 randomly chosen single coordinates (positions and
+  momenta), step 1e-6 times that component's rms spread. A single coordinate moves only its own
+  pairs, so within the step no pair crosses the hard cutoff r_c (where the short-range force
+  jumps) and the difference quotient measures the derivative the reverse pass computes. Also
+  the FP32 mixed reverse pass against the FP64 one over all 6N coordinates.
 """
 from __future__ import annotations
 
@@ -171,6 +178,69 @@ def gradient(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps:
     return {"experiment": "gradient", "n": n_particles, "steps": steps, "dt": dt,
             "checkpoint_every": every,
             "precision": precision, "J": J0, "directions": res, "seconds_gradient": t_grad}
+
+
+def gradient_coords(precision: int = m.FP64, n_particles: int = 16_384, steps: int = 200,
+                    every: int = 20, coords: int = 64, dt: float = 2.5e-13, eps_rel: float = 1e-6,
+                    seed: int = 0):
+    """Reverse-pass gradient of J against central finite differences on randomly chosen single
+    coordinates (positions and momenta), step eps_rel times that component's rms spread; and the
+    FP32 mixed path's reverse pass against the FP64 one on every coordinate."""
+    x, p = _grad_bunch(n_particles)
+    base = dict(n=(64,) * 3, rc_over_h=2.0, adj_slots=(steps + every - 1) // every,
+                adj_segment=every)
+    prm = m.auto_mesh(_cuda(x * 1.05), m.Params(precision=precision, **base))
+    ctx = m.Context(prm, n_particles)
+    x0, p0 = _cuda(x), _cuda(p)
+
+    def J(c, xa, pa):
+        xx, pp = xa.clone(), pa.clone()
+        c.push(xx, pp, dt, steps)
+        return float(c.emittance(xx, pp).sum()), xx, pp
+
+    def adjoint(c):
+        _, xT, pT = J(c, x0, p0)
+        _, gxT, gpT = c.emittance(xT, pT, grad=True)
+        gx, gp = c.backward(x0, p0, dt, steps, gxT, gpT)
+        c.sync()
+        return torch.cat([gx.reshape(-1), gp.reshape(-1)])
+
+    t0 = time.time()
+    g = adjoint(ctx)
+    t_grad = time.time() - t0
+    rng = np.random.default_rng(seed)
+    picks = rng.choice(6 * n_particles, size=coords, replace=False)
+    scale = np.concatenate([x.std(axis=0), p.std(axis=0)])
+    fd, ad = [], []
+    t0 = time.time()
+    for k in picks:
+        half, r = divmod(int(k), 3 * n_particles)  # half 0: positions, 1: momenta
+        i, d = divmod(r, 3)
+        h = eps_rel * float(scale[3 * half + d])
+        vals = []
+        for sgn in (1.0, -1.0):
+            xx, pp = x0.clone(), p0.clone()
+            (xx if half == 0 else pp)[i, d] += sgn * h
+            vals.append(J(ctx, xx, pp)[0])
+        fd.append((vals[0] - vals[1]) / (2 * h))
+        ad.append(float(g[k]))
+    t_fd = time.time() - t0
+    fd, ad = np.array(fd), np.array(ad)
+    rel = np.abs(fd - ad) / np.maximum(np.abs(fd), 1e-300)
+    out = {"experiment": "gradient_coords", "n": n_particles, "steps": steps, "dt": dt,
+           "checkpoint_every": every, "precision": precision, "coords": coords,
+           "eps_rel": eps_rel, "rel_l2_over_coords": float(np.linalg.norm(fd - ad)
+                                                          / np.linalg.norm(fd)),
+           "max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
+           "coords_above_1e-4": int((rel > 1e-4).sum()),
+           "seconds_gradient": t_grad, "seconds_fd": t_fd}
+    if precision == m.FP64:
+        ctx.close()
+        c32 = m.Context(m.auto_mesh(_cuda(x * 1.05), m.Params(precision=m.FP32_MIXED, **base)),
+                        n_particles)
+        g32 = adjoint(c32)
+        out["fp32_adjoint_vs_fp64_rel_l2"] = float((g32 - g).norm() / g.norm())
+    return out
 
 
 def _coulomb_direct(x, targets, q, z_cathode=None, chunk=8):
@@ -429,6 +499,7 @@ def main(argv):
     if "--save" in argv:
         kw["save"] = argv[argv.index("--save") + 1]
     fn = {"boundary": boundary, "energy": energy, "gradient": gradient,
+          "gradient_coords": gradient_coords,
           "influence": influence, "error_measure": error_measure, "action": action,
           "box_potentials": box_potentials}[which]
     print(json.dumps(fn(**kw)), flush=True)
