@@ -205,6 +205,7 @@ def run_ours(a, rank, world, local_rank):
         ctx.forces(xg, out=f)
     ctx.sync()
     pairs, _ = ctx.pair_count()
+    candidates = ctx.candidate_count()  # (particle, record) distance tests of the short range
     K = a.steps
     pp_ms = []
     stage = np.zeros(6)
@@ -312,6 +313,9 @@ def run_ours(a, rank, world, local_rank):
                    "records 537 MB); no flush", "parallelism": f"replicas x{world}"},
         "pp_pairs_per_s": pp_pairs_per_s,
         "pp_pairs_per_eval": pairs,
+        # each unordered pair is found from one side: pairs / 2 of the candidates are in range
+        "pp_candidates_per_eval": candidates,
+        "pp_in_cutoff_fraction": (pairs / 2) / candidates if candidates else None,
         "stage_ms": {k: v / K for k, v in zip(
             ["bin_sort", "short_range", "deposit", "solve", "interp_combine", "total"], stage)},
         "fp64": {"evals_per_s": fp64_evals, "stage_ms": dict(zip(

@@ -141,6 +141,16 @@ p3m_status p3m_forces(p3m_ctx* ctx, const double* x, int64_t n, double* f, doubl
  * that included the short range. Synchronises the context's stream. */
 p3m_status p3m_pair_count(p3m_ctx* ctx, int64_t* pairs, int64_t* image_pairs);
 
+/* Candidate tests of the short range on the particles of the last binning (the last forces,
+ * deposit or push call): the number of (particle, record) pairs the neighbour search hands to
+ * the distance test. Each unordered pair is looked at from one side only, so this bounds
+ * pairs / 2 from above; the ratio is the search's efficiency. The FP32 path recounts them from
+ * the sorted records on request (its short range carries no counter); the FP64 path's short
+ * range counts as it runs (so there: the last evaluation that included the short range).
+ * *candidates is written on success; synchronises the context's stream. P3M_EINVAL for a NULL
+ * argument. */
+p3m_status p3m_candidate_count(p3m_ctx* ctx, int64_t* candidates);
+
 /* Leapfrog, eq. (leapfrog) with the Stoermer form of eq. (eom_p3m_coord), as kick-drift-kick
  * (a reading: the paper leaves the start-up open):
  *   p += dt/2 F(x);  x += dt p / mass;  p += dt/2 F(x)   per step, nsteps >= 0 steps.

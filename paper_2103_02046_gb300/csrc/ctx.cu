@@ -349,7 +349,7 @@ p3m_status forces_impl(p3m_ctx* c, const double* x, int64_t n, double* f, double
                        int parts) {
   cudaStream_t st = c->work;
   cudaMemsetAsync(c->energy_acc, 0, 2 * sizeof(double), st);
-  cudaMemsetAsync(c->pair_acc, 0, 2 * sizeof(unsigned long long), st);
+  cudaMemsetAsync(c->pair_acc, 0, 3 * sizeof(unsigned long long), st);
   cudaEventRecord(c->tev[0], st);
   sort_particles(c, x, n, f);
   cudaEventRecord(c->tev[1], st);
@@ -531,7 +531,7 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     A(alloc(&c->dfac, static_cast<size_t>(g.M[0] / 2 + 1 + g.M[1] + g.M[2])));
   }
   A(alloc(&c->energy_acc, 2));
-  A(alloc(&c->pair_acc, 2));
+  A(alloc(&c->pair_acc, 3));
   A(alloc(&c->pp_tile, 1));
   A(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   A(alloc(&c->err_dev, 1));
@@ -716,6 +716,20 @@ p3m_status p3m_pair_count(p3m_ctx* c, int64_t* pairs, int64_t* image_pairs) {
   if (e != cudaSuccess) return cuda_fail(c, e, "p3m_pair_count");
   *pairs = static_cast<int64_t>(v[0]);
   if (image_pairs) *image_pairs = static_cast<int64_t>(v[1]);
+  return P3M_OK;
+}
+
+p3m_status p3m_candidate_count(p3m_ctx* c, int64_t* candidates) {
+  if (!c || !candidates) return P3M_EINVAL;
+  unsigned long long v = 0;
+  enter(c);
+  launch_pp_count(c, c->last_n, c->pair_acc + 2, c->work);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&v, c->pair_acc + 2, sizeof(v), cudaMemcpyDeviceToHost, c->work);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
+  if (e != cudaSuccess) return cuda_fail(c, e, "p3m_candidate_count");
+  *candidates = static_cast<int64_t>(v);
   return P3M_OK;
 }
 

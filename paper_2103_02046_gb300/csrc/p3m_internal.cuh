@@ -279,7 +279,7 @@ struct p3m_ctx {
 
   // diagnostics
   double* energy_acc = nullptr;              // device [2]
-  unsigned long long* pair_acc = nullptr;    // device [2]
+  unsigned long long* pair_acc = nullptr;    // device [3]: pairs, image pairs, candidates
   uint32_t* pp_tile = nullptr;               // device [1]: next tile of the persistent short range
   int num_sms = 0;
   int* err_dev = nullptr;                    // device error bits
@@ -331,6 +331,9 @@ void launch_get_mesh(const p3m_ctx* c, int which, double* out);
 
 // short range (pp.cu)
 void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s);
+// (particle, record) distance tests of the FP32 short range on the current sorted records,
+// into *out (FP64 contexts: nothing; their short range counts as it runs)
+void launch_pp_count(const p3m_ctx* c, int64_t n, unsigned long long* out, cudaStream_t s);
 void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s);
 
 // particles (particles.cu)

@@ -240,6 +240,54 @@ __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restr
   j1 = starts[base + c1 + 1];
 }
 
+// The runs of the lane holding sorted particles a = ia and b = ia + 1 (b only if alive_b),
+// in walk order: emit(j0, j1) for each non-empty run. With a and b in one row (same) each run is
+// the hull of the two particles' runs in one neighbour row and is tested against both;
+// otherwise a's runs come first (split of them) and are tested against a only, then b's.
+template <typename Emit>
+__device__ __forceinline__ void pair_runs(const Geom& g, const uint32_t* __restrict__ starts,
+                                          const float4& pa, const float4& la, const float4& pb,
+                                          const float4& lb, uint32_t ia, bool alive_b, bool& same,
+                                          int& split, Emit&& emit) {
+  constexpr int kFirst = kRowSpan * kRowSpan / 2, kLast = kRowSpan * kRowSpan;  // half shell
+  const uint32_t ib = ia + 1;
+  const uint32_t row_a = __float_as_uint(la.w) & kRowMask;
+  const uint32_t row_b = __float_as_uint(lb.w) & kRowMask;
+  same = !alive_b || row_a == row_b;
+  const int cya = static_cast<int>(row_a % static_cast<uint32_t>(g.nc[1]));
+  const int cza = static_cast<int>(row_a / static_cast<uint32_t>(g.nc[1]));
+  int n = 0;
+  for (int r = kFirst; r < kLast; ++r) {
+    uint32_t j0, j1;
+    row_range(g, starts, pa.x, pa.y, pa.z, cya, cza, r, j0, j1);
+    j0 = max(j0, ia + 1);  // own row: only the particles after a (a no-op for later rows)
+    if (same && alive_b) {
+      uint32_t k0, k1;
+      row_range(g, starts, pb.x, pb.y, pb.z, cya, cza, r, k0, k1);
+      k0 = max(k0, ib + 1);
+      if (k0 < k1) {
+        j0 = j0 < j1 ? min(j0, k0) : k0;
+        j1 = max(j1, k1);
+      }
+    }
+    if (j0 < j1) {
+      emit(j0, j1);
+      ++n;
+    }
+  }
+  split = n;
+  if (!same) {
+    const int cyb = static_cast<int>(row_b % static_cast<uint32_t>(g.nc[1]));
+    const int czb = static_cast<int>(row_b / static_cast<uint32_t>(g.nc[1]));
+    for (int r = kFirst; r < kLast; ++r) {
+      uint32_t j0, j1;
+      row_range(g, starts, pb.x, pb.y, pb.z, cyb, czb, r, j0, j1);
+      j0 = max(j0, ib + 1);
+      if (j0 < j1) emit(j0, j1);
+    }
+  }
+}
+
 template <int kDeg>
 __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
@@ -247,7 +295,6 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
              float4* __restrict__ fpp, uint32_t* __restrict__ next_tile,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
   constexpr uint32_t kTile = 2 * kThreads;  // particles per tile
-  constexpr int kFirst = kRowSpan * kRowSpan / 2, kLast = kRowSpan * kRowSpan;  // half shell
   __shared__ uint32_t run_j0[kPairRuns][kThreads], run_j1[kPairRuns][kThreads];
   __shared__ uint32_t tile_s;
   const int tid = threadIdx.x;
@@ -274,47 +321,13 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     // against both); otherwise a's runs [0, split) and b's runs [split, cnt)
     int cnt = 0, split = 0;
     bool same = true;
-    if (alive_a) {
-      const uint32_t row_a = __float_as_uint(la.w) & kRowMask;
-      const uint32_t row_b = __float_as_uint(lb.w) & kRowMask;
-      same = !alive_b || row_a == row_b;
-      const int cya = static_cast<int>(row_a % static_cast<uint32_t>(g.nc[1]));
-      const int cza = static_cast<int>(row_a / static_cast<uint32_t>(g.nc[1]));
-      for (int r = kFirst; r < kLast; ++r) {
-        uint32_t j0, j1;
-        row_range(g, starts, pa.x, pa.y, pa.z, cya, cza, r, j0, j1);
-        j0 = max(j0, ia + 1);  // own row: only the particles after a (a no-op for later rows)
-        if (same && alive_b) {
-          uint32_t k0, k1;
-          row_range(g, starts, pb.x, pb.y, pb.z, cya, cza, r, k0, k1);
-          k0 = max(k0, ib + 1);
-          if (k0 < k1) {
-            j0 = j0 < j1 ? min(j0, k0) : k0;
-            j1 = max(j1, k1);
-          }
-        }
-        if (j0 < j1) {
-          run_j0[cnt][tid] = j0;
-          run_j1[cnt][tid] = j1;
-          ++cnt;
-        }
-      }
-      split = cnt;
-      if (!same) {
-        const int cyb = static_cast<int>(row_b % static_cast<uint32_t>(g.nc[1]));
-        const int czb = static_cast<int>(row_b / static_cast<uint32_t>(g.nc[1]));
-        for (int r = kFirst; r < kLast; ++r) {
-          uint32_t j0, j1;
-          row_range(g, starts, pb.x, pb.y, pb.z, cyb, czb, r, j0, j1);
-          j0 = max(j0, ib + 1);
-          if (j0 < j1) {
-            run_j0[cnt][tid] = j0;
-            run_j1[cnt][tid] = j1;
-            ++cnt;
-          }
-        }
-      }
-    }
+    if (alive_a)
+      pair_runs(g, starts, pa, la, pb, lb, ia, alive_b, same, split,
+                [&](uint32_t j0, uint32_t j1) {
+                  run_j0[cnt][tid] = j0;
+                  run_j1[cnt][tid] = j1;
+                  ++cnt;
+                });
     uint32_t ptr = 0, end = 0;
     int k = 0;
     if (cnt > 0) {
@@ -443,6 +456,31 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
   if (energy) block_reduce_add(e_acc, energy);
   warp_add_u64(2ull * np, pairs);
   warp_add_u64(ni, pairs + 1);
+}
+
+// (particle, record) distance tests k_pp_f32 makes on the current sorted records: the same
+// runs, summed instead of walked (a run shared by a and b counts twice). Run on request only,
+// so that the short range itself carries no counter.
+__global__ void k_pp_count_f32(Geom g, const uint32_t* __restrict__ total,
+                               const float4* __restrict__ rec,
+                               const uint32_t* __restrict__ starts,
+                               unsigned long long* __restrict__ out) {
+  const uint32_t N = *total;
+  const uint32_t lane_pair = blockIdx.x * static_cast<uint32_t>(blockDim.x) + threadIdx.x;
+  const uint32_t ia = 2 * lane_pair, ib = ia + 1;
+  unsigned long long n = 0;
+  if (ia < N) {
+    const bool alive_b = ib < N;
+    const uint32_t eb = alive_b ? ib : ia;
+    const float4 pa = rec[2 * ia], la = rec[2 * ia + 1];
+    const float4 pb = rec[2 * eb], lb = rec[2 * eb + 1];
+    bool same = true;
+    int split = 0;
+    pair_runs(g, starts, pa, la, pb, lb, ia, alive_b, same, split,
+              [&](uint32_t j0, uint32_t j1) { n += j1 - j0; });
+    if (same && alive_b) n *= 2;
+  }
+  warp_add_u64(n, out);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -662,7 +700,7 @@ __global__ void __launch_bounds__(kThreads)
   const int cy = min(max(static_cast<int>(floor(py * g.inv_cw[1])), 0), g.nc[1] - 1);
   const int cz = min(max(static_cast<int>(floor(pz * g.inv_cw[2])), 0), g.nc[2] - 1);
   double sum[4] = {0.0, 0.0, 0.0, 0.0};
-  unsigned int np = 0;
+  unsigned int np = 0, ncand = 0;  // pairs found, records tested
   int head = 0, cnt = 0;
   auto evaluate = [&]() {
     const bool has = cnt > 0;
@@ -694,6 +732,7 @@ __global__ void __launch_bounds__(kThreads)
       j1 = max(j1, j0);
     }
     const int len = static_cast<int>(j1 - j0);
+    ncand += static_cast<unsigned>(len);
     int maxlen = len;
     for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
     for (int t = 0; t < maxlen; ++t) {
@@ -740,6 +779,7 @@ __global__ void __launch_bounds__(kThreads)
   if (energy) block_reduce_add(alive ? sum[3] + pair_pot : 0.0, energy);
   warp_add_u64(2ull * np, pairs);
   warp_add_u64(ni, pairs + 1);
+  warp_add_u64(ncand, pairs + 2);
 }
 
 // Vector-Jacobian product of the short-range force map, into acc (sorted order):
@@ -857,6 +897,15 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
     k_pp_f64<<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const Rec64*>(c->recp), c->starts,
                                          static_cast<D4*>(c->fpp), c->energy_acc, c->pair_acc);
   }
+}
+
+void launch_pp_count(const p3m_ctx* c, int64_t n, unsigned long long* out, cudaStream_t s) {
+  if (n == 0 || !c->fp32) return;  // FP64: the short range counts as it walks
+  cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  const int64_t lane_pairs = (n + 1) / 2;
+  k_pp_count_f32<<<static_cast<unsigned>((lane_pairs + kThreads - 1) / kThreads), kThreads, 0,
+                   s>>>(c->g, c->starts + c->nkeys, static_cast<const float4*>(c->recp),
+                        c->starts, out);
 }
 
 void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s) {

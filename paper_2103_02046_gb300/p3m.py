@@ -77,6 +77,7 @@ def lib():
             "p3m_forces_ex": [P, P, I64, P, P, I32],
             "p3m_forces": [P, P, I64, P, P],
             "p3m_pair_count": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
+            "p3m_candidate_count": [P, ctypes.POINTER(I64)],
             "p3m_push": [P, P, P, I64, D, I32, P, I32],
             "p3m_force_vjp": [P, P, I64, P, P],
             "p3m_backward": [P, P, P, I64, D, I32, P, P, P, P],
@@ -235,6 +236,13 @@ class Context:
         self._check(lib().p3m_pair_count(self._h, ctypes.byref(a), ctypes.byref(b)),
                     "p3m_pair_count")
         return a.value, b.value
+
+    def candidate_count(self):
+        """(particle, record) distance tests of the last short range (p3m_candidate_count)."""
+        a = ctypes.c_int64()
+        self._bind()
+        self._check(lib().p3m_candidate_count(self._h, ctypes.byref(a)), "p3m_candidate_count")
+        return a.value
 
     def push(self, x, p, dt: float, nsteps: int, f=None):
         """In-place leapfrog; returns F(x_end) (p3m_push)."""

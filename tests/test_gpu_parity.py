@@ -79,6 +79,8 @@ def test_forces_parity(case, precision):
     xg = cuda(x)
     f_pp = ctx.forces(xg, parts=1)
     np_gpu, ni_gpu = ctx.pair_count()
+    # every unordered in-cutoff pair was among the candidates the search handed out
+    assert ref.pairs // 2 <= ctx.candidate_count() <= 2 * len(x) * len(x)
     f_pm = ctx.forces(xg, parts=2)
     f, e = ctx.forces(xg, energy=True)
     ctx.sync()
@@ -156,9 +158,12 @@ def test_lattice_pairs_at_cutoff(precision):
     ctx = p3m().Context(gpu_params(P, precision), len(x))
     f_pp = ctx.forces(cuda(x), parts=1)
     npairs, _ = ctx.pair_count()
+    ncand = ctx.candidate_count()
     ctx.sync()
     assert npairs == ref.pairs
     assert rel(f_pp, ref.F_pp) <= TOL[precision]
+    # the row search looks at about 8 r_c^3 per particle, the cutoff sphere is 4.19 r_c^3
+    assert npairs // 2 <= ncand <= 8 * npairs
 
 
 @pytest.mark.parametrize("layout", ["counts", "sparse_rows"])
