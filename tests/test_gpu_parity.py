@@ -457,15 +457,17 @@ def test_autograd_emittance_gradient():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("rc", [1.0, 2.0, 3.0])
 @pytest.mark.parametrize("precision", [1, 0])
-def test_full_size_sphere_sampled(precision):
-    """The benchmark workload at full size (16,777,216-particle uniform sphere, 256^3 mesh,
-    r_c = 2h, open boundaries) in the benchmark's launch configuration, checked against the oracle
-    on 2048 sampled particles (full deposit and solve, short range and interpolation per sample)."""
+def test_full_size_sphere_sampled(precision, rc):
+    """The precision workload at full size (16,777,216-particle uniform sphere, 256^3 mesh,
+    r_c = 1, 2 and 3 h, open boundaries) in the benchmark's launch configuration, checked against
+    the oracle on the 65,536-particle subsample (full deposit and solve, short range and
+    interpolation per sample)."""
     spec = dict(B.WORKLOADS["sphere16m"])
     x = B.positions(spec)
-    P = O.auto_mesh(x, 256, rc_over_h=2.0)
-    idx = B.subsample(len(x), 2048, seed=12345)
+    P = O.auto_mesh(x, 256, rc_over_h=rc)
+    idx = B.subsample(len(x), 65536, seed=12345)
     ref = O.forces(x, P, sample=idx)
     ctx = p3m().Context(gpu_params(P, precision), len(x))
     f = ctx.forces(cuda(x))
@@ -473,7 +475,8 @@ def test_full_size_sphere_sampled(precision):
     fs = f[torch.from_numpy(idx).cuda()]
     assert rel(fs, ref.F) <= TOL[precision]
     pairs, _ = ctx.pair_count()
-    assert pairs > 1.0e9
+    # about 67 neighbours per particle at r_c = 2h, scaling as r_c^3
+    assert pairs > 0.8 * 1.128e9 * (rc / 2.0) ** 3
     ctx.close()
 
 
