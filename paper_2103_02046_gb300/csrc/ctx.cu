@@ -77,11 +77,14 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   g.rc = p->rc_over_h * hmax;
   g.alpha = p->alpha > 0.0 ? p->alpha : p->kappa / g.rc;
   g.kappa_eff = g.alpha * g.rc;
-  // cells: y and z edges r_c (1 + 4 slack) / 2, x edges r_c / nsub (nsub = 4 unless that makes
-  // too many cells). A particle's row is computed in FP32 and may be off by one within rounding
-  // (< slack / 3) of a row boundary; with rows this wide, two particles closer than r_c still
-  // sit at most two rows apart, so the 5 x 5 row block around a particle's row holds all of its
-  // neighbours.
+  // cells: y and z edges r_c (1 + 4 slack) / rows, x edges r_c / nsub, at most
+  // max(4 n_max, 2^20) cells. rows = 2 (a tighter search) while the budget allows nsub = 4;
+  // otherwise rows = 1, which keeps x edges r_c / 4 with 4x fewer cells: at low density the
+  // per-particle row setup (13 neighbour rows of the half shell, or 5) and the x rounding of the
+  // runs outweigh the pairs. A particle's row is computed in FP32 and may be off by one within
+  // rounding (< slack / 3) of a row boundary; with rows (1 + 4 slack) r_c / rows wide, two
+  // particles closer than r_c still sit at most `rows` rows apart, so the (2 rows + 1)^2 row
+  // block around a particle's row holds all of its neighbours.
   double ext[3];
   double ext_max = 0.0;
   for (int d = 0; d < 3; ++d) {
@@ -90,20 +93,21 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
     ext_max = std::max(ext_max, ext[d]);
   }
   g.slack = std::max(1e-4, 1e-6 * ext_max);
-  int nsub = 4;
   const double cap = std::max<double>(4.0 * static_cast<double>(n_max), 1 << 20);
-  for (;;) {
+  auto layout = [&](int rows, int nsub) {
+    g.rows = rows;
     g.cw[0] = (1.0 + 1e-9) / nsub;
-    g.cw[1] = g.cw[2] = (1.0 + 4.0 * g.slack) / kRowsPerCutoff;
+    g.cw[1] = g.cw[2] = (1.0 + 4.0 * g.slack) / rows;
     double cells = 1.0;
     for (int d = 0; d < 3; ++d) {
       g.inv_cw[d] = 1.0 / g.cw[d];
       g.nc[d] = static_cast<int>(std::floor(ext[d] * g.inv_cw[d])) + 1;
       cells *= g.nc[d];
     }
-    if (cells <= cap || nsub == 1) break;
-    nsub /= 2;
-  }
+    return cells;
+  };
+  if (layout(2, 4) > cap)
+    for (int nsub = 4; layout(1, nsub) > cap && nsub > 1;) nsub /= 2;
   for (int d = 0; d < 3; ++d) {
     g.cw_f[d] = static_cast<float>(g.cw[d]);
     g.inv_cw_f[d] = static_cast<float>(g.inv_cw[d]);

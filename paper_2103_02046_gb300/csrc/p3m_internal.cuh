@@ -1,10 +1,11 @@
 // Internal declarations of the GB300 P3M library (not part of the C ABI).
 //
 // Data layout in HBM (one context, up to n_max particles, mesh n = (nx, ny, nz), n_d <= 1024):
-//   * Cells for the short-range search are rows along x: edge a hair above r_c / 2 in y and z,
-//     r_c / nsub in x, keys x-fastest, so the cells of one (y, z) row within any x-interval hold a
-//     contiguous run of sorted particles. Each of the 5 x 5 neighbour rows of a particle is then
-//     one index range, pruned by the particle's distance to the row.
+//   * Cells for the short-range search are rows along x: edge a hair above r_c / rows in y and z
+//     (rows = 2, or 1 at low density), r_c / nsub in x, keys x-fastest, so the cells of one (y, z)
+//     row within any x-interval hold a contiguous run of sorted particles. Each of the
+//     (2 rows + 1)^2 neighbour rows of a particle is then one index range, pruned by the
+//     particle's distance to the row.
 //   * Sorted records (counting sort by cell key):
 //       recp  positions in cutoff units from the mesh origin, (x - lo) / r_c, 32 B each:
 //             FP32 two float4 {hi_x, hi_y, hi_z, bits(original index)} {lo_x, lo_y, lo_z, 0},
@@ -29,7 +30,6 @@
 namespace p3m {
 
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
-constexpr int kRowsPerCutoff = 2;  // cell rows are r_c / 2 wide in y and z
 constexpr int kMaxMesh = 1024;
 
 enum ErrBits : int { kErrRange = 1, kErrNaN = 2, kErrTimeout = 4 };
@@ -39,6 +39,7 @@ struct Geom {
   int n[3];      // mesh nodes per axis
   int M[3];      // doubled mesh 2 n
   int nc[3];     // cells per axis
+  int rows;      // cell rows per cutoff length in y and z (1 or 2)
   int order;     // 1 CIC, 2 TSC
   int pm_bc, pp_bc;
   int force_diff;  // 1: long-range force from central differences of the mesh potential
@@ -46,7 +47,7 @@ struct Geom {
   double rc, alpha, zc;
   double q, mass, ke;
   double a[3];       // h_d / r_c
-  double cw[3];      // cell edges in cutoff units (y, z: (1 + 4 slack) / 2; x: 1 / nsub)
+  double cw[3];      // cell edges in cutoff units (y, z: (1 + 4 slack) / rows; x: 1 / nsub)
   double inv_cw[3];
   double inv_h[3];   // 1 / h_d
   float inv_h_f[3];  // 1 / h_d, FP32

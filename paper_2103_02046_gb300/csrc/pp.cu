@@ -27,8 +27,19 @@ namespace p3m {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kRowReach = kRowsPerCutoff;          // neighbour rows on each side (y and z)
-constexpr int kRowSpan = 2 * kRowReach + 1;
+
+// Row geometry for kRows cell rows per cutoff length in y and z (Geom::rows, 1 or 2): the
+// neighbour rows of a particle's row are the (2 kRows + 1)^2 rows around it, numbered y fastest;
+// the particle's own row is number `first`, and the half shell walked by the short range is
+// rows first .. last - 1 (13 of 25 rows, or 5 of 9).
+template <int kRows>
+struct Rows {
+  static constexpr int reach = kRows;
+  static constexpr int span = 2 * kRows + 1;
+  static constexpr int first = span * span / 2;
+  static constexpr int last = span * span;
+  static constexpr int half = last - first;
+};
 
 // two-float accumulator (hi + lo) with Knuth's TwoSum
 struct Acc2 {
@@ -145,8 +156,6 @@ struct PosD {
 // R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}; rsqrt and ex2 are the
 // hardware approximations (flush-to-zero: every argument here is a normal number).
 // ------------------------------------------------------------------------------------------
-constexpr int kHalfRows = kRowSpan * kRowSpan / 2 + 1;  // own row + the 12 after it
-constexpr int kPairRuns = 2 * kHalfRows;           // a's and b's runs across a row boundary
 constexpr int kPpBlocksPerSm = 6;    // resident blocks per SM of the short range (80 registers)
 constexpr int kVjpBlocksPerSm = 10;  // resident blocks per SM of its adjoint (48 registers)
 
@@ -214,14 +223,16 @@ __device__ __forceinline__ void pair_poly(const PairPoly& P, float r2, float& fc
   fco = fmaf(P.c2k, ex, pot) * (rinv * rinv);
 }
 
-// Sorted range [j0, j1) of neighbour row r (0..24, y fastest, 12 = the particle's own row
+// Sorted range [j0, j1) of neighbour row r (y fastest, Rows::first = the particle's own row
 // (cy, cz)) that can hold particles within distance 1 of (px, py, pz); empty if none can. The
 // rectangle distance and the x half-width carry the search slack, as in for_rows.
+template <int kRows>
 __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restrict__ starts,
                                           float px, float py, float pz, int cy, int cz, int r,
                                           uint32_t& j0, uint32_t& j1) {
+  using R = Rows<kRows>;
   j0 = j1 = 0;
-  const int ry = cy + (r % kRowSpan) - kRowReach, rz = cz + (r / kRowSpan) - kRowReach;
+  const int ry = cy + (r % R::span) - R::reach, rz = cz + (r / R::span) - R::reach;
   if (ry < 0 || ry >= g.nc[1] || rz < 0 || rz >= g.nc[2]) return;
   const float slack = g.slack_f;
   const float cwy = g.cw_f[1], cwz = g.cw_f[2];
@@ -244,12 +255,12 @@ __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restr
 // in walk order: emit(j0, j1) for each non-empty run. With a and b in one row (same) each run is
 // the hull of the two particles' runs in one neighbour row and is tested against both;
 // otherwise a's runs come first (split of them) and are tested against a only, then b's.
-template <typename Emit>
+template <int kRows, typename Emit>
 __device__ __forceinline__ void pair_runs(const Geom& g, const uint32_t* __restrict__ starts,
                                           const float4& pa, const float4& la, const float4& pb,
                                           const float4& lb, uint32_t ia, bool alive_b, bool& same,
                                           int& split, Emit&& emit) {
-  constexpr int kFirst = kRowSpan * kRowSpan / 2, kLast = kRowSpan * kRowSpan;  // half shell
+  constexpr int kFirst = Rows<kRows>::first, kLast = Rows<kRows>::last;  // half shell
   const uint32_t ib = ia + 1;
   const uint32_t row_a = __float_as_uint(la.w) & kRowMask;
   const uint32_t row_b = __float_as_uint(lb.w) & kRowMask;
@@ -257,13 +268,14 @@ __device__ __forceinline__ void pair_runs(const Geom& g, const uint32_t* __restr
   const int cya = static_cast<int>(row_a % static_cast<uint32_t>(g.nc[1]));
   const int cza = static_cast<int>(row_a / static_cast<uint32_t>(g.nc[1]));
   int n = 0;
+#pragma unroll 1
   for (int r = kFirst; r < kLast; ++r) {
     uint32_t j0, j1;
-    row_range(g, starts, pa.x, pa.y, pa.z, cya, cza, r, j0, j1);
+    row_range<kRows>(g, starts, pa.x, pa.y, pa.z, cya, cza, r, j0, j1);
     j0 = max(j0, ia + 1);  // own row: only the particles after a (a no-op for later rows)
     if (same && alive_b) {
       uint32_t k0, k1;
-      row_range(g, starts, pb.x, pb.y, pb.z, cya, cza, r, k0, k1);
+      row_range<kRows>(g, starts, pb.x, pb.y, pb.z, cya, cza, r, k0, k1);
       k0 = max(k0, ib + 1);
       if (k0 < k1) {
         j0 = j0 < j1 ? min(j0, k0) : k0;
@@ -279,22 +291,25 @@ __device__ __forceinline__ void pair_runs(const Geom& g, const uint32_t* __restr
   if (!same) {
     const int cyb = static_cast<int>(row_b % static_cast<uint32_t>(g.nc[1]));
     const int czb = static_cast<int>(row_b / static_cast<uint32_t>(g.nc[1]));
+#pragma unroll 1
     for (int r = kFirst; r < kLast; ++r) {
       uint32_t j0, j1;
-      row_range(g, starts, pb.x, pb.y, pb.z, cyb, czb, r, j0, j1);
+      row_range<kRows>(g, starts, pb.x, pb.y, pb.z, cyb, czb, r, j0, j1);
       j0 = max(j0, ib + 1);
       if (j0 < j1) emit(j0, j1);
     }
   }
 }
 
-template <int kDeg>
+template <int kDeg, int kRows>
 __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
              const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
              float4* __restrict__ fpp, uint32_t* __restrict__ next_tile,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
   constexpr uint32_t kTile = 2 * kThreads;  // particles per tile
+  // a's and b's runs: up to twice the half shell when their rows differ
+  constexpr int kPairRuns = 2 * Rows<kRows>::half;
   __shared__ uint32_t run_j0[kPairRuns][kThreads], run_j1[kPairRuns][kThreads];
   __shared__ uint32_t tile_s;
   const int tid = threadIdx.x;
@@ -322,8 +337,8 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     int cnt = 0, split = 0;
     bool same = true;
     if (alive_a)
-      pair_runs(g, starts, pa, la, pb, lb, ia, alive_b, same, split,
-                [&](uint32_t j0, uint32_t j1) {
+      pair_runs<kRows>(g, starts, pa, la, pb, lb, ia, alive_b, same, split,
+                       [&](uint32_t j0, uint32_t j1) {
                   run_j0[cnt][tid] = j0;
                   run_j1[cnt][tid] = j1;
                   ++cnt;
@@ -461,6 +476,7 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
 // (particle, record) distance tests k_pp_f32 makes on the current sorted records: the same
 // runs, summed instead of walked (a run shared by a and b counts twice). Run on request only,
 // so that the short range itself carries no counter.
+template <int kRows>
 __global__ void k_pp_count_f32(Geom g, const uint32_t* __restrict__ total,
                                const float4* __restrict__ rec,
                                const uint32_t* __restrict__ starts,
@@ -476,8 +492,8 @@ __global__ void k_pp_count_f32(Geom g, const uint32_t* __restrict__ total,
     const float4 pb = rec[2 * eb], lb = rec[2 * eb + 1];
     bool same = true;
     int split = 0;
-    pair_runs(g, starts, pa, la, pb, lb, ia, alive_b, same, split,
-              [&](uint32_t j0, uint32_t j1) { n += j1 - j0; });
+    pair_runs<kRows>(g, starts, pa, la, pb, lb, ia, alive_b, same, split,
+                     [&](uint32_t j0, uint32_t j1) { n += j1 - j0; });
     if (same && alive_b) n *= 2;
   }
   warp_add_u64(n, out);
@@ -511,13 +527,14 @@ __device__ __forceinline__ void pair_hess_poly(const PairPoly& P, float r2, floa
   dfr = (dA - 2.f * A * rinv) * rinv2 * rinv;
 }
 
-template <int kDeg>
+template <int kDeg, int kRows>
 __global__ void __launch_bounds__(kThreads, kVjpBlocksPerSm)
     k_pp_vjp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
                  const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
                  const float4* __restrict__ ws, float4* __restrict__ acc4,
                  uint32_t* __restrict__ next_tile) {
-  __shared__ uint32_t run_j0[kHalfRows][kThreads], run_j1[kHalfRows][kThreads];
+  using R = Rows<kRows>;
+  __shared__ uint32_t run_j0[R::half][kThreads], run_j1[R::half][kThreads];
   __shared__ uint32_t tile_s;
   const int tid = threadIdx.x;
   const uint32_t N = *total;
@@ -537,9 +554,9 @@ __global__ void __launch_bounds__(kThreads, kVjpBlocksPerSm)
       const uint32_t row = __float_as_uint(li.w) & kRowMask;
       const int cy = static_cast<int>(row % static_cast<uint32_t>(g.nc[1]));
       const int cz = static_cast<int>(row / static_cast<uint32_t>(g.nc[1]));
-      for (int r = kRowSpan * kRowSpan / 2; r < kRowSpan * kRowSpan; ++r) {
+      for (int r = R::first; r < R::last; ++r) {
         uint32_t j0, j1;
-        row_range(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
+        row_range<kRows>(g, starts, pi.x, pi.y, pi.z, cy, cz, r, j0, j1);
         j0 = max(j0, i + 1);
         if (j0 < j1) {
           run_j0[cnt][tid] = j0;
@@ -658,11 +675,13 @@ __global__ void k_gather_w(const uint32_t* __restrict__ total, const float4* __r
 // ------------------------------------------------------------------------------------------
 constexpr int kRing64 = 4;
 
+template <int kRows>
 __device__ __forceinline__ void row_range64(const Geom& g, const uint32_t* __restrict__ starts,
                                             double px, double py, double pz, int cy, int cz,
                                             int r, uint32_t& j0, uint32_t& j1) {
+  using R = Rows<kRows>;
   j0 = j1 = 0;
-  const int ry = cy + (r % kRowSpan) - kRowReach, rz = cz + (r / kRowSpan) - kRowReach;
+  const int ry = cy + (r % R::span) - R::reach, rz = cz + (r / R::span) - R::reach;
   if (ry < 0 || ry >= g.nc[1] || rz < 0 || rz >= g.nc[2]) return;
   const double slack = g.slack;
   const double yl = ry * g.cw[1], yh = yl + g.cw[1], zl = rz * g.cw[2], zh = zl + g.cw[2];
@@ -679,6 +698,7 @@ __device__ __forceinline__ void row_range64(const Geom& g, const uint32_t* __res
   j1 = starts[base + c1 + 1];
 }
 
+template <int kRows>
 __global__ void __launch_bounds__(kThreads)
     k_pp_f64(Geom g, const uint32_t* __restrict__ total, const Rec64* __restrict__ rec,
              const uint32_t* __restrict__ starts, D4* __restrict__ fpp,
@@ -724,10 +744,10 @@ __global__ void __launch_bounds__(kThreads)
     head += has;
     cnt -= has;
   };
-  for (int r = 0; r < kRowSpan * kRowSpan; ++r) {
+  for (int r = 0; r < Rows<kRows>::last; ++r) {
     uint32_t j0 = 0, j1 = 0;
     if (alive) {
-      row_range64(g, starts, px, py, pz, cy, cz, r, j0, j1);
+      row_range64<kRows>(g, starts, px, py, pz, cy, cz, r, j0, j1);
       j0 = max(j0, i + 1);
       j1 = max(j1, j0);
     }
@@ -875,27 +895,30 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
     const int64_t tiles = (n + 2 * kThreads - 1) / (2 * kThreads);  // two particles a thread
     const unsigned wblocks = static_cast<unsigned>(
         std::min<int64_t>(tiles, static_cast<int64_t>(kPpBlocksPerSm) * c->num_sms));
-    auto run = [&](auto kern) {
+    // the kernel for the context's row geometry (Geom::rows cell rows per cutoff)
+    auto run = [&](auto k_rows1, auto k_rows2) {
+      auto kern = c->g.rows == 1 ? k_rows1 : k_rows2;
       kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
                                        c->starts, static_cast<float4*>(c->fpp), c->pp_tile,
                                        c->energy_acc, c->pair_acc);
     };
     switch (c->poly.deg) {
-      case 6: run(k_pp_f32<6>); break;
-      case 7: run(k_pp_f32<7>); break;
-      case 8: run(k_pp_f32<8>); break;
-      case 9: run(k_pp_f32<9>); break;
-      case 10: run(k_pp_f32<10>); break;
-      case 11: run(k_pp_f32<11>); break;
-      case 12: run(k_pp_f32<12>); break;
-      case 13: run(k_pp_f32<13>); break;
-      case 14: run(k_pp_f32<14>); break;
-      default: run(k_pp_f32<15>); break;
+      case 6: run(k_pp_f32<6, 1>, k_pp_f32<6, 2>); break;
+      case 7: run(k_pp_f32<7, 1>, k_pp_f32<7, 2>); break;
+      case 8: run(k_pp_f32<8, 1>, k_pp_f32<8, 2>); break;
+      case 9: run(k_pp_f32<9, 1>, k_pp_f32<9, 2>); break;
+      case 10: run(k_pp_f32<10, 1>, k_pp_f32<10, 2>); break;
+      case 11: run(k_pp_f32<11, 1>, k_pp_f32<11, 2>); break;
+      case 12: run(k_pp_f32<12, 1>, k_pp_f32<12, 2>); break;
+      case 13: run(k_pp_f32<13, 1>, k_pp_f32<13, 2>); break;
+      case 14: run(k_pp_f32<14, 1>, k_pp_f32<14, 2>); break;
+      default: run(k_pp_f32<15, 1>, k_pp_f32<15, 2>); break;
     }
   } else {
     cudaMemsetAsync(c->fpp, 0, sizeof(D4) * static_cast<size_t>(n), s);
-    k_pp_f64<<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const Rec64*>(c->recp), c->starts,
-                                         static_cast<D4*>(c->fpp), c->energy_acc, c->pair_acc);
+    auto kern = c->g.rows == 1 ? k_pp_f64<1> : k_pp_f64<2>;
+    kern<<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const Rec64*>(c->recp), c->starts,
+                                     static_cast<D4*>(c->fpp), c->energy_acc, c->pair_acc);
   }
 }
 
@@ -903,9 +926,9 @@ void launch_pp_count(const p3m_ctx* c, int64_t n, unsigned long long* out, cudaS
   if (n == 0 || !c->fp32) return;  // FP64: the short range counts as it walks
   cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
   const int64_t lane_pairs = (n + 1) / 2;
-  k_pp_count_f32<<<static_cast<unsigned>((lane_pairs + kThreads - 1) / kThreads), kThreads, 0,
-                   s>>>(c->g, c->starts + c->nkeys, static_cast<const float4*>(c->recp),
-                        c->starts, out);
+  auto kern = c->g.rows == 1 ? k_pp_count_f32<1> : k_pp_count_f32<2>;
+  kern<<<static_cast<unsigned>((lane_pairs + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      c->g, c->starts + c->nkeys, static_cast<const float4*>(c->recp), c->starts, out);
 }
 
 void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s) {
@@ -921,22 +944,23 @@ void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s)
     cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
     const unsigned wblocks = static_cast<unsigned>(
         std::min<int64_t>(blocks, static_cast<int64_t>(kVjpBlocksPerSm) * c->num_sms));
-    auto run = [&](auto kern) {
+    auto run = [&](auto k_rows1, auto k_rows2) {
+      auto kern = c->g.rows == 1 ? k_rows1 : k_rows2;
       kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total,
                                         static_cast<const float4*>(c->recp), c->starts, ws,
                                         static_cast<float4*>(c->fpp), c->pp_tile);
     };
     switch (c->poly.deg) {
-      case 6: run(k_pp_vjp_f32<6>); break;
-      case 7: run(k_pp_vjp_f32<7>); break;
-      case 8: run(k_pp_vjp_f32<8>); break;
-      case 9: run(k_pp_vjp_f32<9>); break;
-      case 10: run(k_pp_vjp_f32<10>); break;
-      case 11: run(k_pp_vjp_f32<11>); break;
-      case 12: run(k_pp_vjp_f32<12>); break;
-      case 13: run(k_pp_vjp_f32<13>); break;
-      case 14: run(k_pp_vjp_f32<14>); break;
-      default: run(k_pp_vjp_f32<15>); break;
+      case 6: run(k_pp_vjp_f32<6, 1>, k_pp_vjp_f32<6, 2>); break;
+      case 7: run(k_pp_vjp_f32<7, 1>, k_pp_vjp_f32<7, 2>); break;
+      case 8: run(k_pp_vjp_f32<8, 1>, k_pp_vjp_f32<8, 2>); break;
+      case 9: run(k_pp_vjp_f32<9, 1>, k_pp_vjp_f32<9, 2>); break;
+      case 10: run(k_pp_vjp_f32<10, 1>, k_pp_vjp_f32<10, 2>); break;
+      case 11: run(k_pp_vjp_f32<11, 1>, k_pp_vjp_f32<11, 2>); break;
+      case 12: run(k_pp_vjp_f32<12, 1>, k_pp_vjp_f32<12, 2>); break;
+      case 13: run(k_pp_vjp_f32<13, 1>, k_pp_vjp_f32<13, 2>); break;
+      case 14: run(k_pp_vjp_f32<14, 1>, k_pp_vjp_f32<14, 2>); break;
+      default: run(k_pp_vjp_f32<15, 1>, k_pp_vjp_f32<15, 2>); break;
     }
   } else {
     // d/dxi of (k_e q^2 / r_c^2) f(rho): one more factor 1/r_c
