@@ -195,6 +195,40 @@ def test_fp32_short_range_lane_pairs(layout):
             assert ref.pairs > 0
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("bc", [(0, 0), (1, 1)])
+def test_short_range_wide_rows(precision, bc):
+    # 20,000 particles in a 32^3 mesh at r_c = 0.6h: about 52 cutoff lengths per axis, where the
+    # cell budget no longer allows rows r_c / 2 wide with x cells r_c / 4, so the search uses
+    # rows r_c wide (the 5 half-shell rows of a 3 x 3 block): forces, pair counts, images and
+    # the force VJP through that layout
+    pm_bc, pp_bc = bc
+    x = np.random.default_rng(31).uniform(-1e-3, 1e-3, size=(20000, 3))
+    if pm_bc:
+        x = B.lift_to_plane(x, 0.0, 0.005e-3)
+    P = O.auto_mesh(x, 32, rc_over_h=0.6, pm_bc=pm_bc, pp_bc=pp_bc, z_cathode=0.0)
+    ref = O.forces(x, P)
+    ctx = p3m().Context(gpu_params(P, precision), len(x))
+    xg = cuda(x)
+    f_pp = ctx.forces(xg, parts=1)
+    npairs, nimg = ctx.pair_count()
+    ncand = ctx.candidate_count()
+    f = ctx.forces(xg)
+    w = np.random.default_rng(32).standard_normal(x.shape)
+    g = ctx.force_vjp(xg, cuda(w))
+    ctx.sync()
+    tol = TOL[precision]
+    assert ref.pairs > 10000 and (pp_bc == 0 or ref.image_pairs > 0)
+    assert rel(f_pp, ref.F_pp) <= tol
+    assert rel(f, ref.F) <= tol
+    if precision == 0:
+        assert (npairs, nimg) == (ref.pairs, ref.image_pairs)
+    else:
+        assert abs(npairs - ref.pairs) <= 2 and abs(nimg - ref.image_pairs) <= 2
+    assert ref.pairs // 2 <= ncand
+    assert rel(g, O.force_vjp(x, w, P)) <= (1e-11 if precision == 0 else 2e-5)
+
+
 def _box_case():
     # a bunch inside a grounded box of 20 x 24 x 28 nodes (h = 0.1 mm), supports off the faces
     x = B.gaussian(3000, (0.2e-3, 0.25e-3, 0.3e-3), 51)
