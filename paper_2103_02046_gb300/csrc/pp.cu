@@ -923,8 +923,9 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
 }
 
 void launch_pp_count(const p3m_ctx* c, int64_t n, unsigned long long* out, cudaStream_t s) {
-  if (n == 0 || !c->fp32) return;  // FP64: the short range counts as it walks
+  if (!c->fp32) return;  // FP64: the short range counts as it walks
   cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (n == 0) return;
   const int64_t lane_pairs = (n + 1) / 2;
   auto kern = c->g.rows == 1 ? k_pp_count_f32<1> : k_pp_count_f32<2>;
   kern<<<static_cast<unsigned>((lane_pairs + kThreads - 1) / kThreads), kThreads, 0, s>>>(

@@ -193,6 +193,9 @@ def test_fp32_short_range_lane_pairs(layout):
         assert abs(npairs - ref.pairs) <= max(2, 1e-5 * ref.pairs)
         if layout == "counts" and len(x) >= 255:
             assert ref.pairs > 0
+    # an empty evaluation leaves nothing counted
+    ctx.forces(torch.zeros((0, 3), dtype=torch.float64, device="cuda"))
+    assert ctx.pair_count() == (0, 0) and ctx.candidate_count() == 0
 
 
 @pytest.mark.parametrize("precision", [0, 1])
