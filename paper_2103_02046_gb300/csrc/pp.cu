@@ -8,16 +8,17 @@
 // Work is in cutoff units (rho = r / r_c, kappa = a r_c): the force is
 // (k_e q^2 / r_c^2) [erfc(kappa rho)/rho + (2 kappa/sqrt(pi)) e^{-kappa^2 rho^2}] rho_vec / rho^2.
 //
-// Search: cells are rows along x (r_c / 2 wide in y and z, r_c / nsub in x, keys x-fastest).
-// For particle i and each of the 5 x 5 neighbour rows, the distance d from i to the row's (y, z)
-// rectangle bounds |dx| < sqrt(1 - d^2), which selects one contiguous run of sorted particles;
-// rows with d >= 1 are skipped. This visits about 8 r_c^3 of volume per particle (the cutoff
-// sphere is 4.19 r_c^3) instead of the 27 r_c^3 of a plain 27-cell stencil.
+// Search: cells are rows along x (r_c / R wide in y and z, R = Geom::rows = 2, or 1 at low
+// density; r_c / nsub in x; keys x-fastest). For particle i and each of the (2R + 1)^2
+// neighbour rows, the distance d from i to the row's (y, z) rectangle bounds |dx| < sqrt(1 - d^2),
+// which selects one contiguous run of sorted particles; rows with d >= 1 are skipped. With R = 2
+// this visits about 8 r_c^3 of volume per particle (the cutoff sphere is 4.19 r_c^3) instead of
+// the 27 r_c^3 of a plain 27-cell stencil.
 //
-// FP32: candidates are tested with the hi parts of the cutoff-unit positions; in-cutoff pairs
-// recompute the separation as (hi_i - hi_j) + (lo_i - lo_j), exact to FP32 relative rounding at
-// any distance. Partial sums are folded into a two-float (TwoSum) accumulator every few pairs,
-// so the per-particle sum is compensated at a small fraction of an addition per pair.
+// FP32: every candidate's separation is (hi_i - hi_j) + (lo_i - lo_j) of the cutoff-unit
+// positions, exact to FP32 relative rounding at any distance. Partial sums are folded into a
+// two-float (TwoSum) accumulator every few steps, so the per-particle sum is compensated at a
+// small fraction of an addition per pair.
 #include <algorithm>
 #include <cmath>
 
@@ -127,9 +128,10 @@ struct PosD {
 // particles and walking their candidate lists in lockstep with the other lanes.
 //
 // Pairs: particle i takes the pairs (i, j) with j > i in sorted order. Sorted order is row-major
-// over (z row, y row, x cell), so these are the later part of i's own row and the 12 neighbour
-// rows after it (dz > 0, or dz = 0 and dy > 0) -- 13 of the 25 rows. i's row is the one the sort
-// put it in (stored with the record), so every pair is taken by exactly one of its particles.
+// over (z row, y row, x cell), so these are the later part of i's own row and the neighbour
+// rows after it (dz > 0, or dz = 0 and dy > 0) -- 13 of 25 rows, or 5 of 9. i's row is the one
+// the sort put it in (stored with the record), so every pair is taken by exactly one of its
+// particles.
 //
 // Lanes: lane l of a tile holds the sorted particles a = 2l and b = 2l + 1 (adjacent in sorted
 // order, so nearly always in the same row and a quarter cutoff apart or less). Per neighbour row
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     np += np_part;
     const float pair_pot_a = sa[3].value(), pair_pot_b = sb[3].value();
     // images within r_c of particles less than r_c above the cathode (rare): plain loop over
-    // all 25 rows around the image point; image pairs act on the particle only
+    // all rows around the image point; image pairs act on the particle only
     auto images = [&](const float4 pi, const float4 li, Acc2* sum) {
       const double zi = static_cast<double>(pi.z) + static_cast<double>(li.z);
       if (zi - 0.5 * g.img_c >= 1.0) return;

@@ -1,9 +1,10 @@
 // Binning of particles into cutoff cells and a counting sort by cell.
 //
 // The short-range sum of eq. (summation_short) needs, for each particle, the particles
-// "close to" it (within r_c, Sec. 3.1.1, fig. ShortError). Cells at least r_c / 2 wide in y and
-// z turn that search into 5 x 5 rows of cells along x. The sort is a counting sort in three
-// passes: histogram with in-cell ranks (atomics), exclusive scan of the cell counts, scatter.
+// "close to" it (within r_c, Sec. 3.1.1, fig. ShortError). Cells at least r_c / R wide in y and
+// z (R = 2, or 1 at low density) turn that search into (2R + 1)^2 rows of cells along x. The
+// sort is a counting sort in three passes: histogram with in-cell ranks (atomics), exclusive
+// scan of the cell counts, scatter.
 // No pass waits on another block, so no inter-block spin is needed.
 #include "p3m_internal.cuh"
 
