@@ -37,11 +37,11 @@ METRIC = "P3M force evals/s and PP pair-interactions/s at N=16M, FP32 vs FP64 at
 FLOPS_PER_PAIR = 37.0  # algorithmic FP32 flops per in-cutoff pair (FFMA = 2, incl. 3 MUFU)
 KERNELS_PER_EVAL = 10  # bin, 3 scan passes, scatter, short range, deposit, Green multiply,
                        # interpolation + combination, unpermute (cuFFT's kernels not counted)
-# DRAM bytes (read + write) of one k_pp_f32<12> launch per particle, from an ncu capture of the
+# DRAM bytes (read + write) of one k_pp_f32<12, 2> launch per particle, from an ncu capture of the
 # 2,097,152-particle sphere on a 128^3 mesh (123.9 MB per launch, profiles/k_pp_f32_sphere2m_128.md).
 # The kernel reads each 32-B record about once from DRAM (the neighbour runs and the reduction
 # targets stay in L2), so its traffic scales with the particle count at fixed density.
-PP_DRAM_BYTES_PER_PARTICLE = (110.77248e6 + 13.134336e6) / 2097152
+PP_DRAM_BYTES_PER_PARTICLE = (110.694144e6 + 13.249280e6) / 2097152
 
 
 def parse():
