@@ -153,7 +153,7 @@ struct PosD {
 // lane and candidate and its results are selected by the hit predicate, since with 64 lane
 // candidates per step some lane nearly always holds a pair. Separations are exact to FP32
 // relative rounding ((hi_i - hi_j) + (lo_i - lo_j)). FP32 partial sums are folded into a
-// two-float (TwoSum) accumulator every 8 steps.
+// two-float (TwoSum) accumulator every 16 steps.
 // The pair function uses one ex2 for both e^{-kappa^2 rho^2} terms and the fitted polynomial
 // R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}; rsqrt and ex2 are the
 // hardware approximations (flush-to-zero: every argument here is a normal number).
@@ -402,13 +402,17 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
       cand(va, ja, h0, l0);
       cand(vb, jb, h1, l1);
       ptr += 2;
-      if (ptr >= end && ++k < cnt) {
-        ptr = run_j0[k][tid];
-        end = run_j1[k][tid];
+      {
+        // the next run without a branch: slot k stays in bounds (k < cnt, or k = 0)
+        const bool sw = ptr >= end && k + 1 < cnt;
+        k += sw ? 1 : 0;
+        const uint32_t nj0 = run_j0[k][tid], nj1 = run_j1[k][tid];
+        ptr = sw ? nj0 : ptr;
+        end = sw ? nj1 : end;
         ta = same || k < split;
         tb = alive_b && (same || k >= split);
       }
-      if ((++step & 7) == 0) {
+      if ((++step & 15) == 0) {
         for (int c = 0; c < 4; ++c) {
           sa[c].add(qa[c]);
           sb[c].add(qb[c]);
@@ -608,9 +612,13 @@ __global__ void __launch_bounds__(kThreads, kVjpBlocksPerSm)
       if (__any_sync(0xffffffffu, hita)) pair(hita, ra, ax, ay, az, ptr);
       if (__any_sync(0xffffffffu, hitb)) pair(hitb, rb, bx, by, bz, ptr + 1);
       ptr += 2;
-      if (ptr >= end && ++k < cnt) {
-        ptr = run_j0[k][tid];
-        end = run_j1[k][tid];
+      {
+        // the next run without a branch: slot k stays in bounds (k < cnt, or k = 0)
+        const bool sw = ptr >= end && k + 1 < cnt;
+        k += sw ? 1 : 0;
+        const uint32_t nj0 = run_j0[k][tid], nj1 = run_j1[k][tid];
+        ptr = sw ? nj0 : ptr;
+        end = sw ? nj1 : end;
       }
       if ((++step & 7) == 0) {
         for (int c = 0; c < 3; ++c) {
