@@ -41,7 +41,7 @@ KERNELS_PER_EVAL = 10  # bin, 3 scan passes, scatter, short range, deposit, Gree
 # 2,097,152-particle sphere on a 128^3 mesh (123.9 MB per launch, profiles/k_pp_f32_sphere2m_128.md).
 # The kernel reads each 32-B record about once from DRAM (the neighbour runs and the reduction
 # targets stay in L2), so its traffic scales with the particle count at fixed density.
-PP_DRAM_BYTES_PER_PARTICLE = (110.694144e6 + 13.249280e6) / 2097152
+PP_DRAM_BYTES_PER_PARTICLE = (110.694144e6 + 13.193984e6) / 2097152
 
 
 def parse():
@@ -322,7 +322,7 @@ def run_ours(a, rank, world, local_rank):
             ["bin_sort", "short_range", "deposit", "solve", "interp_combine", "total"], t64))},
         "error": {"fp32_vs_fp64_gpu_rel_l2": err32},
         "roofline": {"bound": "alu", "kernel": "k_pp_f32 (short range)",
-                     "limiter": "instruction issue ~77%, L1 data pipe ~61% (ncu, "
+                     "limiter": "instruction issue ~77%, L1 data pipe ~65% (ncu, "
                                 "profiles/k_pp_f32_sphere2m_128.md)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": PP_DRAM_BYTES_PER_PARTICLE * N,
