@@ -388,7 +388,9 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
       qb[2] += fbz;
       qb[3] += ub;
       np_part += static_cast<uint32_t>(ha) + static_cast<uint32_t>(hb);
-      red_add_v4_if(ha || hb, fpp + j, -(fax + fbx), -(fay + fby), -(faz + fbz), ua + ub);
+      // the reaction on j; the potential is summed on the owner's side only (each pair's is
+      // counted twice into the energy there), so j's fourth component stays unused
+      red_add_v4_if(ha || hb, fpp + j, -(fax + fbx), -(fay + fby), -(faz + fbz), 0.f);
     };
     int step = 0;
     while (__any_sync(0xffffffffu, ptr < end)) {
@@ -746,10 +748,10 @@ __global__ void __launch_bounds__(kThreads)
       sum[2] += fz;
       sum[3] += pot;
       double* fj = &fpp[j].x;
+      // the potential is summed on the owner's side only: j's fourth component stays unused
       atomicAdd(fj, -fx);
       atomicAdd(fj + 1, -fy);
       atomicAdd(fj + 2, -fz);
-      atomicAdd(fj + 3, pot);
     }
     head += has;
     cnt -= has;
@@ -803,7 +805,7 @@ __global__ void __launch_bounds__(kThreads)
   }
   if (alive) {
     double* fi = &fpp[i].x;
-    for (int c = 0; c < 4; ++c) atomicAdd(fi + c, sum[c]);
+    for (int c = 0; c < 3; ++c) atomicAdd(fi + c, sum[c]);  // the potential goes to the energy only
   }
   // sum_i phi_i over ordered pairs: each pair's potential was taken once here, plus the images
   if (energy) block_reduce_add(alive ? sum[3] + pair_pot : 0.0, energy);
