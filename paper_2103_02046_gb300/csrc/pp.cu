@@ -388,9 +388,7 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
       qb[2] += fbz;
       qb[3] += ub;
       np_part += static_cast<uint32_t>(ha) + static_cast<uint32_t>(hb);
-      // the reaction on j; the potential is summed on the owner's side only (each pair's is
-      // counted twice into the energy there), so j's fourth component stays unused
-      red_add_v4_if(ha || hb, fpp + j, -(fax + fbx), -(fay + fby), -(faz + fbz), 0.f);
+      red_add_v4_if(ha || hb, fpp + j, -(fax + fbx), -(fay + fby), -(faz + fbz), ua + ub);
     };
     int step = 0;
     while (__any_sync(0xffffffffu, ptr < end)) {
