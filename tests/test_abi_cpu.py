@@ -64,3 +64,13 @@ def test_create_refuses_bad_params_without_touching_the_device(lib):
     assert lib.p3m_create(None, 10, None, ctypes.byref(h)) == p3m.P3M_EINVAL
     assert lib.p3m_destroy(None) == p3m.P3M_OK
     assert lib.p3m_last_error(None) == b"null context"
+
+
+def test_counts_refuse_null_arguments(lib):
+    from paper_2103_02046_gb300 import p3m
+    v = ctypes.c_int64(-1)
+    lib.p3m_pair_count.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64)]
+    assert lib.p3m_pair_count(None, ctypes.byref(v), None) == p3m.P3M_EINVAL
+    assert lib.p3m_candidate_count(None, ctypes.byref(v)) == p3m.P3M_EINVAL
+    assert v.value == -1
