@@ -191,16 +191,26 @@ p3m_status p3m_emittance(p3m_ctx* ctx, const double* x, const double* p, int64_t
  *   gx, gp: nullable device [n][3] float64 for the gradient of eps_x + eps_y + eps_z;
  *   stream: cudaStream_t (may be NULL).
  * It needs no context and allocates nothing: its scratch is a fixed 512 KiB array in device
- * memory that every GPU loading the library holds until the process exits. Its first call on a
- * device looks up that array's address (once per device, with the device current); make that
- * first call before any stream capture. Every call shares the array; each call writes every
+ * memory that every GPU loading the library holds until the process exits. Its first call in a
+ * CUDA context (normally a device's primary context, with that device current) looks up the
+ * array's address and keeps it for that context; make that first call before any stream capture. Every call shares the array; each call writes every
  * slot it later reads, so no state carries over, but calls that overlap on the GPU (other
  * streams, no ordering between them) race and must not be issued. The sums are combined in a
  * fixed order, so results are reproducible run to run.
  * Errors: EINVAL for NULL x/p/eps3, n < 2, mass <= 0 or n > P3M_NOALLOC_MAX_N; ECUDA if the
- * scratch address cannot be obtained or a launch fails. Asynchronous on `stream`. */
+ * scratch address cannot be obtained or one of this call's launches fails (an error left
+ * pending by the caller's earlier work is neither reported nor cleared). Asynchronous on
+ * `stream`. */
 p3m_status p3m_emittance_noalloc(const double* x, const double* p, int64_t n, double mass,
                                  double* eps3, double* gx, double* gp, void* stream);
+
+/* Measurement utility (no counterpart in the paper): launches an FP32 fused-multiply-add chain
+ * kernel on the current device (8 blocks of 256 threads per SM, 8 independent chains of `iters`
+ * steps per thread; packed != 0 uses the two-wide FP32 instructions) on `stream` and writes the
+ * launch's flop count (FMA = 2 flops) to *flops (host). Time the launch with events on the same
+ * stream to measure the FP32 pipe's throughput, the denominator of the short range's roofline.
+ * Allocates nothing. EINVAL for NULL flops or iters < 1; ECUDA if the launch fails. */
+p3m_status p3m_fp32_probe(int32_t packed, int32_t iters, double* flops, void* stream);
 
 /* Waits for the context's stream and returns any latched device error (then clears it). */
 p3m_status p3m_sync(p3m_ctx* ctx);

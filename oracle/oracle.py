@@ -159,7 +159,7 @@ def _mesh_args(P: Params):
 # ------------------------------------------------------------------------------------------
 # mesh steps
 # ------------------------------------------------------------------------------------------
-def deposit(x, P: Params, weights=None):
+def deposit(x, P: Params):
     """Node charges Q[gz, gy, gx] = q sum_i W(x_g - xi_i) (eq. (rho_L)); returns (Q, n_bad)."""
     x = _f64(x)
     n, lo, h = _mesh_args(P)

@@ -6,6 +6,8 @@
 // array, then one block combining them), so every slot that a later step reads has been
 // written earlier in the same call: nothing has to be cleared between calls. Calls that run at
 // the same time on the GPU (different streams, no ordering) share the array and race.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "p3m_internal.cuh"
@@ -24,8 +26,17 @@ static_assert(static_cast<long long>(kNaPerBlock) * kNaMaxBlocks == P3M_NOALLOC_
 // [block][16] partial sums, then 16 totals; 4096 * 16 * 8 B + 128 B = 512.1 KiB per device.
 static __device__ __align__(256) double g_na_scratch[kNaMaxBlocks * kNaSums + kNaSums];
 
+// Scratch addresses already looked up, keyed by the CUDA context they belong to. A context ID
+// is never reused within a process, so an address cached for a context that was destroyed
+// (cudaDeviceReset, or a driver-API context that was popped and freed) is never handed out again.
+struct NaSlot {
+  unsigned long long ctx_id;
+  double* ptr;
+};
+constexpr int kNaMaxContexts = 64;
 std::mutex g_na_mutex;
-double* g_na_ptr[kNaMaxDevices] = {};
+NaSlot g_na_slots[kNaMaxContexts] = {};
+int g_na_used = 0;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -131,19 +142,74 @@ __global__ void k_na_finish(const double* __restrict__ x, const double* __restri
   if (gp) gp[t] = den > 0.0 ? (dp * a - du * c) / den : 0.0;
 }
 
-// Device address of the static scratch on the current device, looked up once per device.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// ID of the CUDA context current on this thread (0 if none is current yet). The two driver
+// functions are fetched through the runtime, so the library needs no link to the driver.
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the static scratch in the current context (the caller's device current),
+// looked up once per context with cudaGetSymbolAddress and cached under the context's ID.
 p3m_status scratch_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return P3M_ECUDA;
   std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_na_scratch);
-    if (e != cudaSuccess || !ptr) return P3M_ECUDA;
-    g_na_ptr[dev] = static_cast<double*>(ptr);
+  unsigned long long id = current_context_id();
+  if (id != 0)
+    for (int k = 0; k < g_na_used; ++k)
+      if (g_na_slots[k].ctx_id == id) {
+        *out = g_na_slots[k].ptr;
+        return P3M_OK;
+      }
+  // not seen yet in this context (or no context bound yet: the lookup binds the device's
+  // primary context, whose ID is taken afterwards)
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_na_scratch);
+  if (e != cudaSuccess || !ptr) return P3M_ECUDA;
+  if (id == 0) id = current_context_id();
+  if (id != 0) {
+    if (g_na_used < kNaMaxContexts) {
+      g_na_slots[g_na_used++] = NaSlot{id, static_cast<double*>(ptr)};
+    } else {  // many contexts over the process's life: reuse slots round-robin
+      static int next = 0;
+      g_na_slots[next] = NaSlot{id, static_cast<double*>(ptr)};
+      next = (next + 1) % kNaMaxContexts;
+    }
   }
-  *out = g_na_ptr[dev];
+  *out = static_cast<double*>(ptr);
   return P3M_OK;
+}
+
+// Launch status of the kernel just launched by this call. `before` is the runtime's pending
+// error from the caller's own earlier work (peeked, not cleared): it is left for the caller,
+// and only an error that this launch added is taken (and cleared) here.
+bool launch_failed(cudaError_t before) {
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e == cudaSuccess || e == before) return false;
+  (void)cudaGetLastError();
+  return true;
 }
 
 }  // namespace
@@ -159,12 +225,17 @@ extern "C" p3m_status p3m_emittance_noalloc(const double* x, const double* p, in
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int nb = static_cast<int>((n + kNaPerBlock - 1) / kNaPerBlock);
   const double mc = mass * 299792458.0;
+  const cudaError_t before = cudaPeekAtLastError();
   k_na_first<<<nb, kNaThreads, 0, st>>>(x, p, n, scratch);
+  if (launch_failed(before)) return P3M_ECUDA;
   k_na_combine<<<1, kNaThreads, 0, st>>>(scratch, nb, 0, 6);
+  if (launch_failed(before)) return P3M_ECUDA;
   k_na_second<<<nb, kNaThreads, 0, st>>>(x, p, n, scratch);
+  if (launch_failed(before)) return P3M_ECUDA;
   k_na_combine<<<1, kNaThreads, 0, st>>>(scratch, nb, 6, 15);
+  if (launch_failed(before)) return P3M_ECUDA;
   const int64_t work = (gx || gp) ? 3 * n : 3;
   k_na_finish<<<static_cast<unsigned>((work + 255) / 256), 256, 0, st>>>(x, p, n, scratch, mc,
                                                                         eps3, gx, gp);
-  return cudaGetLastError() == cudaSuccess ? P3M_OK : P3M_ECUDA;
+  return launch_failed(before) ? P3M_ECUDA : P3M_OK;
 }

@@ -162,6 +162,41 @@ __global__ void k_energy_out(const double* __restrict__ acc, double pp_scale, do
   }
 }
 
+// FP32 throughput probe: every thread runs 8 independent chains of fused multiply-adds
+// a <- a b + c (packed: two lanes of a float2 per instruction). Nothing depends on memory, so the
+// launch measures the FMA pipe alone. The chains' sum is written only in a case that cannot
+// occur (|a| stays below 2 for b < 1, c small), which keeps the compiler from dropping them.
+__device__ float g_probe_sink;
+
+template <bool kPacked>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters) {
+  const float b = 0.9999f, c = 1e-4f;
+  float s = 0.f;
+  if constexpr (kPacked) {
+    float2 a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = make_float2(1e-3f * u, 2e-3f * threadIdx.x);
+    const float2 b2 = make_float2(b, b), c2 = make_float2(c, c);
+#pragma unroll 4
+    for (int k = 0; k < iters; ++k)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = __ffma2_rn(a[u], b2, c2);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += a[u].x + a[u].y;
+  } else {
+    float a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = 1e-3f * u + 2e-3f * threadIdx.x;
+#pragma unroll 4
+    for (int k = 0; k < iters; ++k)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = fmaf(a[u], b, c);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += a[u];
+  }
+  if (s == 1234567.f) g_probe_sink = s;
+}
+
 }  // namespace
 
 void launch_bbox(const double* x, int64_t n, double* red, cudaStream_t s) {
@@ -208,3 +243,20 @@ void launch_energy_out(const p3m_ctx* c, double* energy) {
 }
 
 }  // namespace p3m
+
+extern "C" p3m_status p3m_fp32_probe(int32_t packed, int32_t iters, double* flops, void* stream) {
+  if (!flops || iters < 1) return P3M_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return P3M_ECUDA;
+  const unsigned blocks = static_cast<unsigned>(sms) * 8u;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (packed)
+    p3m::k_fma_probe<true><<<blocks, 256, 0, st>>>(iters);
+  else
+    p3m::k_fma_probe<false><<<blocks, 256, 0, st>>>(iters);
+  // 8 chains per thread, one FMA (2 flops) per chain and step, two lanes when packed
+  *flops = static_cast<double>(blocks) * 256.0 * iters * 8.0 * 2.0 * (packed ? 2.0 : 1.0);
+  return cudaGetLastError() == cudaSuccess ? P3M_OK : P3M_ECUDA;
+}

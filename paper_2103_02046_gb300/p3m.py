@@ -84,6 +84,7 @@ def lib():
             "p3m_emittance": [P, P, P, I64, P, P, P],
             "p3m_sync": [P],
             "p3m_get_timings": [P, ctypes.POINTER(D), I32, ctypes.POINTER(I32)],
+            "p3m_fp32_probe": [I32, I32, ctypes.POINTER(D), P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -336,3 +337,12 @@ class Emittance(torch.autograd.Function):
     def backward(ctx, g):
         gx, gp = ctx.saved_tensors
         return g * gx, g * gp, None
+
+
+def fp32_probe(packed: bool, iters: int) -> float:
+    """Launches the FP32 multiply-add chain probe on the current stream; returns its flops."""
+    flops = ctypes.c_double(0.0)
+    st = lib().p3m_fp32_probe(int(bool(packed)), int(iters), ctypes.byref(flops), _stream())
+    if st != P3M_OK:
+        raise P3MError(st, "p3m_fp32_probe")
+    return flops.value

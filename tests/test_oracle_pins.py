@@ -306,6 +306,60 @@ def test_uniform_sphere_radial_field():
 
 
 # ------------------------------------------------------------------------------------------
+# energies (eq. (pot_split): the split potential energy; the charge splitting of
+# eq. (charge_splitting) puts each particle's self term k_e q^2 a / sqrt(pi) into the mesh part)
+# ------------------------------------------------------------------------------------------
+def _mesh_in_box(n, alpha, rc):
+    L = 4e-3
+    h = 2 * L / (n - 1)
+    return O.Params(n=(n,) * 3, lo=(-L,) * 3, h=(h,) * 3, rc_over_h=rc / h, alpha=alpha)
+
+
+def test_self_energy_is_the_lone_particles_mesh_energy():
+    # A lone particle has no pairs: its long-range mesh energy (1/2) Q phi is the interaction of
+    # its screened charge with itself, k_e q^2 G^L(0) / 2 = k_e q^2 a / sqrt(pi) in the limit of
+    # a fine mesh. The total energy minus self_energy must therefore vanish as h -> 0, at the
+    # second order of the assignment's smoothing (a factor 2, or a instead of a / sqrt(pi), in
+    # self_energy would leave a finite remainder).
+    alpha, x = 2.0e3, np.array([[0.1e-3, -0.2e-3, 0.05e-3]])
+    rel = []
+    for n in (16, 32, 64):
+        P = _mesh_in_box(n, alpha, 1.5e-3)
+        E = O.total_energy(x, np.zeros_like(x), P)
+        rel.append(abs(E) / O.self_energy(1, P))
+        assert O.self_energy(1, P) == pytest.approx(KE * P.q ** 2 * alpha / math.sqrt(math.pi),
+                                                    rel=1e-15)
+    assert rel[-1] < 0.05
+    assert rel[0] / rel[1] > 2.5 and rel[1] / rel[2] > 3.0  # second order in h
+
+
+def test_total_energy_of_two_charges_tends_to_coulomb():
+    # Two charges closer than r_c: short range k_e q^2 erfc(a r)/r plus the mesh's cross term
+    # k_e q^2 erf(a r)/r, the self terms removed, is k_e q^2 / r as the mesh refines; the
+    # momenta add sum p^2 / 2M exactly.
+    alpha = 2.0e3
+    xa = np.array([[0.1e-3, -0.2e-3, 0.05e-3]])
+    xb = np.array([[0.5e-3, 0.2e-3, 0.3e-3]])
+    x = np.vstack([xa, xb])
+    r = float(np.linalg.norm(xa - xb))
+    exact = KE * 1e-15 ** 2 / r
+    errs = []
+    for n in (16, 32, 64):
+        P = _mesh_in_box(n, alpha, 1.5e-3)
+        z = lambda y: np.zeros_like(y)
+        inter = (O.total_energy(x, z(x), P) - O.total_energy(xa, z(xa), P)
+                 - O.total_energy(xb, z(xb), P))
+        errs.append(abs(inter - exact) / exact)
+        assert abs(O.total_energy(x, z(x), P) - exact) / exact < (0.7, 0.25, 0.07)[len(errs) - 1]
+    assert errs[-1] < 0.015
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0
+    p = np.array([[1e-22, 2e-22, -1e-22], [0.0, -3e-22, 1e-22]])
+    P = _mesh_in_box(16, alpha, 1.5e-3)
+    kin = O.total_energy(x, p, P) - O.total_energy(x, np.zeros_like(p), P)
+    assert kin == pytest.approx(float(np.sum(p * p)) / (2 * P.mass), rel=1e-9)
+
+
+# ------------------------------------------------------------------------------------------
 # leapfrog (eq. (leapfrog))
 # ------------------------------------------------------------------------------------------
 def test_kdk_harmonic_closed_form():

@@ -4,8 +4,9 @@ Some callers cannot allocate device memory (a host application that owns the dev
 own allocator or a fixed budget, or a monitoring hook inside a simulation loop that must not
 stall on an allocation). For them the library offers p3m_emittance_noalloc, whose scratch is a
 fixed static device array. This test calls it through the C ABI twice in a row, on two
-different bunches, and checks each result against the context-based entry point at the same
-tolerance as the other emittance tests. It lives in a file of its own that runs last.
+different bunches, and checks each result against the context-based entry point and against the
+FP64 oracle at the same tolerance as the other emittance tests. It lives in a file of its own
+that runs last.
 """
 import ctypes
 
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as O
 from paper_2103_02046_gb300 import bunches as B
 
 pytestmark = pytest.mark.gpu
@@ -49,6 +51,15 @@ def test_emittance_noalloc_matches_context_entry_point_twice():
         assert rel(eps, eps_ref) <= 1e-12, f"call {call}"
         assert rel(gx, gx_ref) <= 1e-11, f"call {call}"
         assert rel(gp, gp_ref) <= 1e-11, f"call {call}"
+        # and directly against the oracle's definition
+        Po = O.Params(mass=mass)
+        xo, po = x.cpu().numpy(), p.cpu().numpy()
+        e_or = O.emittance(xo, po, Po)
+        gx_or, gp_or = O.emittance_grad(xo, po, Po)
+        e_np = eps.cpu().numpy()
+        assert np.linalg.norm(e_np - e_or) <= 1e-12 * np.linalg.norm(e_or), f"call {call}"
+        assert np.linalg.norm(gx.cpu().numpy() - gx_or) <= 1e-11 * np.linalg.norm(gx_or)
+        assert np.linalg.norm(gp.cpu().numpy() - gp_or) <= 1e-11 * np.linalg.norm(gp_or)
     # sizes beyond the static scratch are refused, not truncated
     big = ctypes.c_int64(16_777_217)
     st = fn(P(x.data_ptr()), P(p.data_ptr()), big, mass, P(eps.data_ptr()), None, None, stream)
