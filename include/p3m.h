@@ -73,7 +73,11 @@ typedef struct p3m_params {
                             factor on the sampled kernels: 1 = principal alias only (1/U^2),
                             2 = alias sums over |m_d| <= 2 (computed once in p3m_create) */
   int32_t precision;     /* p3m_precision */
-  int32_t deterministic; /* reserved, must be 0 */
+  int32_t deterministic; /* 1 = run-to-run identical results (FP64 path, pm_bc 0 or 1): particles
+                            in a fixed order within each cell, every ordered pair evaluated by
+                            its own particle without reductions, node charges summed exactly in
+                            128-bit fixed point, energies and emittances in fixed-order
+                            reductions. 0 = the faster unordered reductions (default) */
   int32_t adj_slots;     /* checkpoint slots for p3m_backward (0 disables the reverse pass) */
   int32_t adj_segment;   /* steps per checkpoint segment in p3m_backward */
   double q;              /* macro-particle charge [C] (all particles equal) */
@@ -105,7 +109,8 @@ p3m_status p3m_auto_mesh(const double* x, int64_t n, p3m_params* inout, void* st
 /* Validates params, allocates every buffer for up to n_max particles, creates the FFT
  * plans and builds the Green's-function spectra (eq. (phi_L), eq. (GreenFunc_planar_cathode)).
  * `stream` (cudaStream_t, may be NULL) becomes the context's stream. *out is set on success.
- * EINVAL: bad params or n_max outside [1, 2^31 - 1]; ENOMEM / ECUFFT / ECUDA on failure
+ * EINVAL: bad params or n_max outside [1, 2^31 - 1] (FP32 mixed precision: [1, 2^30]);
+ * ENOMEM / ECUFFT / ECUDA on failure
  * (nothing is leaked). */
 p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m_ctx** out);
 

@@ -542,6 +542,19 @@ def total_energy(x, p, P: Params, res: ForceResult | None = None) -> float:
     return ke + res.U_pp + res.U_pm - self_energy(len(x), P)
 
 
+def discrete_action(X, dt, P: Params, kernels=None) -> float:
+    """Discrete action of eq. (full_p3m_lagrangian) with the left-point patch of eq. (leapfrog):
+    S_d = dt sum_n [ sum_i M |x^{n+1}_i - x^n_i|^2 / (2 dt^2) - U(x^n) ] over the states
+    X = [x^0, ..., x^K], with U = U_pp + U_pm the split P3M potential energy (eq. (pot_split)).
+    The self term is a constant of the motion and is left in U."""
+    tot = 0.0
+    for n in range(len(X) - 1):
+        R = forces(X[n], P, kernels=kernels)
+        kin = 0.5 * P.mass * float(((_f64(X[n + 1]) - _f64(X[n])) ** 2).sum()) / dt ** 2
+        tot += kin - (R.U_pp + R.U_pm)
+    return tot * dt
+
+
 # ------------------------------------------------------------------------------------------
 # leapfrog push (eq. (leapfrog); kick-drift-kick with an initial half kick)
 # ------------------------------------------------------------------------------------------

@@ -56,7 +56,15 @@ p3m_status validate(const p3m_params* p, std::string* why) {
   if (!std::isfinite(p->z_cathode)) { *why = "z_cathode must be finite"; return P3M_EINVAL; }
   if (p->influence < 0 || p->influence > 2) { *why = "influence must be 0, 1 or 2"; return P3M_EINVAL; }
   if (p->precision != P3M_FP64 && p->precision != P3M_FP32_MIXED) { *why = "precision must be 0 or 1"; return P3M_EINVAL; }
-  if (p->deterministic != 0) { *why = "deterministic must be 0"; return P3M_EINVAL; }
+  if (p->deterministic != 0 && p->deterministic != 1) { *why = "deterministic must be 0 or 1"; return P3M_EINVAL; }
+  if (p->deterministic && p->precision != P3M_FP64) {
+    *why = "deterministic = 1 runs on the FP64 path";
+    return P3M_EINVAL;
+  }
+  if (p->deterministic && p->pm_bc == 2) {
+    *why = "deterministic = 1 does not cover the grounded box";
+    return P3M_EINVAL;
+  }
   if (p->force_diff != 0 && p->force_diff != 1) { *why = "force_diff must be 0 or 1"; return P3M_EINVAL; }
   if (p->adj_slots < 0 || p->adj_segment < 0 || (p->adj_slots > 0 && p->adj_segment < 1)) { *why = "adj_slots/adj_segment invalid"; return P3M_EINVAL; }
   if (!std::isfinite(p->q) || p->q == 0.0) { *why = "q must be finite and nonzero"; return P3M_EINVAL; }
@@ -96,6 +104,7 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   const double cap = std::max<double>(4.0 * static_cast<double>(n_max), 1 << 20);
   auto layout = [&](int rows, int nsub) {
     g.rows = rows;
+    g.xunit = 1.0f / static_cast<float>(nsub);
     g.cw[0] = (1.0 + 1e-9) / nsub;
     g.cw[1] = g.cw[2] = (1.0 + 4.0 * g.slack) / rows;
     double cells = 1.0;
@@ -206,11 +215,12 @@ cudaError_t alloc(T** ptr, size_t count) {
 
 void free_all(p3m_ctx* c) {
   void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recm, c->fpp,
+                  c->recs, c->left,
                   c->acc, c->qpad, c->qhat, c->qhat2, c->khat_f, c->khat_i, c->fhat, c->freal,
                   c->phihat, c->phireal, c->dfac, c->ztw, c->box_real, c->box_spec, c->box_mult,
                   c->energy_acc, c->pair_acc,
                   c->pp_tile, c->err_dev, c->ckpt, c->seg, c->lam_x, c->lam_p, c->xw, c->pw,
-                  c->tmp3, c->tmp3b, c->f_work, c->red};
+                  c->tmp3, c->tmp3b, c->f_work, c->red, c->ered, c->q128, c->dbound, c->dred};
   for (void* b : bufs) cudaFree(b);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->have_xy_f) cufftDestroy(c->plan_xy_f);
@@ -332,11 +342,13 @@ p3m_status mesh_solve(p3m_ctx* c, bool want_phi, bool want_diff, bool want_energ
   p3m_status s = fft_r2c(c);
   if (s != P3M_OK) return s;
   if (!c->fp32) want_phi = true, want_diff = false;
-  launch_green_multiply(c, want_phi, want_diff, want_energy);
+  // deterministic contexts form the mesh energy from the potential, in a fixed order
+  launch_green_multiply(c, want_phi, want_diff, want_energy && !c->det);
   if (want_phi) {
     if (fft_c2r(c, c->phihat, c->phireal) != CUFFT_SUCCESS)
       return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
     c->phi_valid = true;
+    if (c->det && want_energy) launch_det_sum_mesh(c);
   }
   if (want_diff) {
     for (int d = 0; d < 3; ++d) {
@@ -490,12 +502,15 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     return P3M_EINVAL;
   }
   if (n_max < 1 || n_max > 2147483647LL) return P3M_EINVAL;
+  // the FP32 short range packs sorted indices into 30 bits
+  if (params->precision == P3M_FP32_MIXED && n_max > (1LL << 30)) return P3M_EINVAL;
   auto* c = new p3m_ctx();
   c->prm = *params;
   c->g = make_geom(params, n_max);
   c->poly = fit_pair_poly(c->g.kappa_eff);
   c->n_max = n_max;
   c->fp32 = params->precision == P3M_FP32_MIXED;
+  c->det = params->deterministic != 0;
   c->stream = static_cast<cudaStream_t>(stream);
   cudaGetDevice(&c->device);
   const Geom& g = c->g;
@@ -520,7 +535,12 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   A(alloc(&c->ranks, n_max));
   A(cudaMalloc(&c->recp, 32 * static_cast<size_t>(n_max)));
   if (!c->fp32) A(cudaMalloc(&c->recm, 32 * static_cast<size_t>(n_max)));  // FP32: in recp
+  // short-range result: FP64 {F, phi} (32 B); FP32 float4
   A(cudaMalloc(&c->fpp, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
+  if (c->fp32) {
+    A(alloc(&c->recs, n_max + 1));  // + a sentinel record far from every particle
+    A(alloc(&c->left, n_max / 2 + 2));
+  }
   A(alloc(&c->acc, 3 * n_max));
   A(cudaMalloc(&c->qpad, es * c->n_real));
   A(cudaMalloc(&c->qhat, 2 * es * c->n_cplx));
@@ -540,6 +560,13 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   A(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   A(alloc(&c->err_dev, 1));
   A(alloc(&c->red, 32));
+  A(alloc(&c->ered, static_cast<size_t>(kEmitBlocks) * 16));
+  if (params->deterministic) {
+    const size_t nn = static_cast<size_t>(g.n[0]) * g.n[1] * g.n[2];
+    A(alloc(&c->q128, 2 * nn));
+    A(alloc(&c->dbound, 1));
+    A(alloc(&c->dred, 2 * 1024));
+  }
   A(alloc(&c->f_work, 3 * n_max));
   if (params->adj_slots > 0) {
     A(alloc(&c->ckpt, static_cast<size_t>(params->adj_slots) * 6 * n_max));
@@ -571,6 +598,11 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   }
   *c->err_host = 0;
   cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->work);
+  if (c->fp32) {
+    // the short range's sentinel: every separation to it is about 1e18 cutoff lengths
+    static const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+    cudaMemcpyAsync(c->recs + n_max, &far, sizeof(float4), cudaMemcpyHostToDevice, c->work);
+  }
   cudaMemsetAsync(c->qpad, 0, es * c->n_real, c->work);
   cudaMemsetAsync(c->qhat, 0, 2 * es * c->n_cplx, c->work);  // planes z >= n_z stay zero
   if (c->fp32) {
@@ -839,7 +871,7 @@ p3m_status p3m_emittance(p3m_ctx* c, const double* x, const double* p, int64_t n
   if (!x || !p || !eps3 || n < 2) return fail(c, P3M_EINVAL, "bad argument");
   p3m_status s = take_deferred(c);
   if (s != P3M_OK) return s;
-  launch_emittance(x, p, n, c->g.mass * kSpeedOfLight, eps3, gx, gp, c->red, c->work);
+  launch_emittance(x, p, n, c->g.mass * kSpeedOfLight, eps3, gx, gp, c->ered, c->red, c->work);
   return finish(c);
 }
 

@@ -67,7 +67,18 @@ struct Geom {
   float inv_h_df[3][2];  // 1 / h_d
   float fscale_f[3];     // -q / h_d in FP32
   float rch_df[3][2];    // r_c / h_d: cutoff units -> mesh units
+  float xunit;           // 1 / nsub (a power of two): the x origin of a search record's cell
 };
+
+// FP32 search record of a sorted particle (16 B, float4): its position in cutoff units relative
+// to origins whose differences are exact in FP32, so that the short range gets every separation
+// to a few 1e-8 cutoff lengths from three subtractions:
+//   x: x_loc = x - ox, ox = cx * xunit (cx the particle's x cell); stored with ox in w.
+//      dx = (x_loc_i - x_loc_j) + (ox_i - ox_j), the second difference exact;
+//   y, z: y_loc = y - ry * cw_y (ry the particle's row); between rows ry and ry + k,
+//      dy = (y_loc_i - k cw_y) - y_loc_j, with k cw_y exact (|k| <= 2).
+// The 32-byte record (hi + lo) keeps the position to 2^-46 relative for the mesh kernels, the
+// images and the rare pairs closer than 1e-2 r_c.
 
 // FP32 records: the lo part's w packs the particle's row (rz nc_y + ry, below 2^26) and, in the
 // top 6 bits, a node correction of -1, 0 or +1 per axis (2 bits each, stored + 1) that turns the
@@ -230,6 +241,7 @@ struct p3m_ctx {
   int64_t n_max = 0;
   int device = 0;
   bool fp32 = false;
+  bool det = false;             // deterministic = 1 (FP64 path): run-to-run identical results
   cudaStream_t stream = nullptr;  // caller's stream (not owned)
   cudaStream_t work = nullptr;    // owned, low priority: sort, mesh chain, combination
   cudaStream_t s_pp = nullptr;    // owned, high priority: the short range (the longest stage),
@@ -246,7 +258,10 @@ struct p3m_ctx {
   uint32_t* ranks = nullptr;    // [n_max] rank within its cell
   void* recp = nullptr;         // [n_max] sorted positions, cutoff units (2 float4 / Rec64)
   void* recm = nullptr;         // [n_max] FP64 path: sorted assignment records (Rec64)
-  void* fpp = nullptr;          // [n_max] short-range force + potential, sorted (float4/double4)
+  void* fpp = nullptr;          // [n_max] short-range result, sorted (FP32 float4, FP64 D4)
+  float4* recs = nullptr;       // [n_max] FP32 path: search records (SearchRec layout)
+  uint32_t* left = nullptr;     // [n_max / 2 + 2] FP32 path: [0] count, then sorted indices of
+                                // particles the paired walk leaves to a second pass
   double* acc = nullptr;        // [3 n_max] adjoint accumulator, sorted order
 
   // mesh
@@ -297,6 +312,12 @@ struct p3m_ctx {
   double* tmp3b = nullptr;                  // [3 n_max] scratch product
   double* f_work = nullptr;                 // [3 n_max]
   double* red = nullptr;                    // device reduction scratch [32]
+  double* ered = nullptr;                   // emittance partial sums [blocks][16]
+  // deterministic = 1: 128-bit fixed-point node sums [n^3][2], the dipole scale bound, and the
+  // partial sums of the fixed-order energy reductions [2][1024]
+  unsigned long long* q128 = nullptr;
+  unsigned long long* dbound = nullptr;
+  double* dred = nullptr;
 
   // state
   bool deposited = false, solved = false, phi_valid = false;
@@ -327,6 +348,10 @@ void launch_zconv(const p3m_ctx* c, bool want_energy);
 p3m_status box_setup(p3m_ctx* c);
 p3m_status box_solve(p3m_ctx* c, bool want_energy);
 void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts);
+// deterministic = 1: fixed-order energies (short range from the per-particle potentials, mesh
+// from (1/2) sum_g Q_g phi_g) into energy_acc[0] and energy_acc[1]
+void launch_det_sum_pp(const p3m_ctx* c, int64_t n, cudaStream_t s);
+void launch_det_sum_mesh(const p3m_ctx* c);
 void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, double* out);
 void launch_get_mesh(const p3m_ctx* c, int which, double* out);
 
@@ -343,8 +368,11 @@ void launch_kick_drift(double* x, double* p, const double* f, int64_t n, double 
                        cudaStream_t s);
 void launch_axpy(double* y, const double* x, int64_t n3, double a, cudaStream_t s);
 void launch_scale(double* y, const double* x, int64_t n3, double a, cudaStream_t s);
+// fixed-order reductions (deterministic for every context): part holds kEmitBlocks x 16 partial
+// sums, red the 16 totals
+constexpr int kEmitBlocks = 1216;
 void launch_emittance(const double* x, const double* p, int64_t n, double mc, double* eps3,
-                      double* gx, double* gp, double* red, cudaStream_t s);
+                      double* gx, double* gp, double* part, double* red, cudaStream_t s);
 void launch_energy_out(const p3m_ctx* c, double* energy);
 
 }  // namespace p3m

@@ -76,9 +76,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// sums of k values per particle row into red[0..k)
+// Sums of K values per particle over the particles, in a fixed order: block b adds a fixed
+// stride of particles and reduces them in a fixed tree into part[b][0..K); k_part_combine then
+// adds the kEmitBlocks parts in order. No atomics: the emittance is reproducible run to run.
 template <int K, typename F>
-__device__ void block_sums(F get, int64_t n, double* __restrict__ red) {
+__device__ void block_sums(F get, int64_t n, double* __restrict__ part) {
   double s[K];
   for (int k = 0; k < K; ++k) s[k] = 0.0;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
@@ -90,17 +92,25 @@ __device__ void block_sums(F get, int64_t n, double* __restrict__ red) {
     if ((threadIdx.x & 31) == 0) ws[k][threadIdx.x >> 5] = v;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    for (int k = 0; k < K; ++k) {
-      double v = threadIdx.x < kThreads / 32 ? ws[k][threadIdx.x] : 0.0;
-      v = warp_sum(v);
-      if (threadIdx.x == 0) atomicAdd(red + k, v);
-    }
+  if (threadIdx.x < K) {
+    double v = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) v += ws[threadIdx.x][w];
+    part[blockIdx.x * 16 + threadIdx.x] = v;
   }
 }
 
+// red[k0 + k] = sum over blocks of part[b][k0 + k], k < K, in block order
+__global__ void k_part_combine(const double* __restrict__ part, int nb, int k0, int K,
+                               double* __restrict__ red) {
+  const int k = threadIdx.x;
+  if (k >= K) return;
+  double v = 0.0;
+  for (int b = 0; b < nb; ++b) v += part[b * 16 + k0 + k];
+  red[k0 + k] = v;
+}
+
 __global__ void k_mom_first(const double* __restrict__ x, const double* __restrict__ p, int64_t n,
-                            double* __restrict__ red) {
+                            double* __restrict__ part) {
   block_sums<6>(
       [&](int64_t i, double* s) {
         for (int d = 0; d < 3; ++d) {
@@ -108,12 +118,12 @@ __global__ void k_mom_first(const double* __restrict__ x, const double* __restri
           s[3 + d] += p[3 * i + d];
         }
       },
-      n, red);
+      n, part);
 }
 
-// centred second moments <du^2>, <dp^2>, <du dp> per axis into red[6..15)
+// centred second moments <du^2>, <dp^2>, <du dp> per axis into part[b][6..15)
 __global__ void k_mom_second(const double* __restrict__ x, const double* __restrict__ p, int64_t n,
-                             double* __restrict__ red) {
+                             const double* __restrict__ red, double* __restrict__ part) {
   const double inv = 1.0 / static_cast<double>(n);
   const double mx[3] = {red[0] * inv, red[1] * inv, red[2] * inv};
   const double mp[3] = {red[3] * inv, red[4] * inv, red[5] * inv};
@@ -126,7 +136,7 @@ __global__ void k_mom_second(const double* __restrict__ x, const double* __restr
           s[3 * d + 2] += du * dp;
         }
       },
-      n, red + 6);
+      n, part + 6);
 }
 
 __global__ void k_emit_finish(const double* __restrict__ red, int64_t n, double mc,
@@ -225,11 +235,12 @@ void launch_scale(double* y, const double* x, int64_t n3, double a, cudaStream_t
 }
 
 void launch_emittance(const double* x, const double* p, int64_t n, double mc, double* eps3,
-                      double* gx, double* gp, double* red, cudaStream_t s) {
-  cudaMemsetAsync(red, 0, 16 * sizeof(double), s);
-  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(blocks_for(n), 1216));
-  k_mom_first<<<blocks, kThreads, 0, s>>>(x, p, n, red);
-  k_mom_second<<<blocks, kThreads, 0, s>>>(x, p, n, red);
+                      double* gx, double* gp, double* part, double* red, cudaStream_t s) {
+  const int blocks = static_cast<int>(std::min<int64_t>(blocks_for(n), kEmitBlocks));
+  k_mom_first<<<blocks, kThreads, 0, s>>>(x, p, n, part);
+  k_part_combine<<<1, 32, 0, s>>>(part, blocks, 0, 6, red);
+  k_mom_second<<<blocks, kThreads, 0, s>>>(x, p, n, red, part);
+  k_part_combine<<<1, 32, 0, s>>>(part, blocks, 6, 9, red);
   if (eps3) k_emit_finish<<<1, 32, 0, s>>>(red, n, mc, eps3);
   if (gx || gp) k_emit_grad<<<blocks_for(3 * n), kThreads, 0, s>>>(x, p, n, red, mc, gx, gp);
 }

@@ -227,6 +227,8 @@ __device__ __forceinline__ long long orig_index(const Rec64* recp, uint32_t i) {
 constexpr int kDepThreads = 256;
 constexpr int kDepItems = 4;
 constexpr int kDepPerBlock = kDepThreads * kDepItems;
+static_assert(kDepPerBlock == 32 * 32 && kDepThreads / 32 * kDepItems == 32,
+              "the deposit's slot map covers a block's particles once");
 constexpr int kTileBytes = 32768;
 
 template <typename T, bool kDipole>
@@ -257,10 +259,15 @@ __global__ void __launch_bounds__(kDepThreads)
     bmax[threadIdx.x] = -1;
   }
   __syncthreads();
+  // particle slot of (thread, item): the lanes of a warp take particles 32 apart in sorted order
+  // (about 8 cutoff lengths along a row), so that one warp's shared-memory atomics rarely hit the
+  // same node; consecutive particles of a cell share all their nodes
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  auto slot = [&](int k) { return b0 + lane * 32u + warp * kDepItems + static_cast<uint32_t>(k); };
   int lmin[3] = {1 << 30, 1 << 30, 1 << 30}, lmax[3] = {-1, -1, -1};
 #pragma unroll
   for (int k = 0; k < kDepItems; ++k) {
-    const uint32_t i = b0 + k * kDepThreads + threadIdx.x;
+    const uint32_t i = slot(k);
     if (i < N) {
       Axis<T> ax[3];
       particle_axes(g, recm, i, ax);
@@ -288,7 +295,7 @@ __global__ void __launch_bounds__(kDepThreads)
     for (int t = threadIdx.x; t < ex * ey * ez; t += kDepThreads) tile[t] = Slot(0);
   __syncthreads();
   for (int k = 0; k < kDepItems; ++k) {
-    const uint32_t i = b0 + k * kDepThreads + threadIdx.x;
+    const uint32_t i = slot(k);
     if (i >= N) continue;
     Axis<T> A[3];
     particle_axes(g, recm, i, A);
@@ -331,6 +338,142 @@ __global__ void __launch_bounds__(kDepThreads)
       atomicAdd(qpad + real_index(g, gx, gy, gz), v);
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Deterministic charge assignment (deterministic = 1, FP64 path): every weight is added to its
+// node as a 128-bit fixed-point integer (two 64-bit words, the carry taken from the low word's
+// returned old value), so the node sums are exact and independent of the order of the adds.
+// The charge weights lie in [0, 1] and use 62 fractional bits; the dipole deposit of the adjoint
+// scales by 2^(61 - e), with 2^e above the largest |w_i|_1 / h of this call, found first by a
+// max reduction (an order-free operation). A node sum of up to 2^31 weights stays below 2^93.
+// ---------------------------------------------------------------------------------------------
+constexpr int kDetBlocks = 1024;  // fixed grid of the deterministic reductions
+
+__device__ __forceinline__ void add128(unsigned long long* acc, long long v) {
+  const unsigned long long lo = static_cast<unsigned long long>(v);
+  const unsigned long long old = atomicAdd(acc, lo);
+  const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  atomicAdd(acc + 1, (v < 0 ? ~0ull : 0ull) + carry);
+}
+
+// largest sum_d |w_d| / h_d over the particles (non-negative doubles order as their bits)
+__global__ void k_dipole_bound(Geom g, const uint32_t* __restrict__ total,
+                               const Rec64* __restrict__ recp, const double* __restrict__ w,
+                               unsigned long long* __restrict__ bound) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  double b = 0.0;
+  if (i < *total) {
+    const long long idx = recp[i].idx;
+    for (int d = 0; d < 3; ++d) b += fabs(w[3 * idx + d]) * g.inv_h[d];
+  }
+  for (int o = 16; o > 0; o >>= 1) b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  if ((threadIdx.x & 31) == 0 && b > 0.0)
+    atomicMax(bound, static_cast<unsigned long long>(__double_as_longlong(b)));
+}
+
+__device__ __forceinline__ double det_scale(bool dipole, const unsigned long long* bound) {
+  if (!dipole) return 4611686018427387904.0;  // 2^62
+  const double b = __longlong_as_double(static_cast<long long>(*bound));
+  if (!(b > 0.0)) return 1.0;
+  return ldexp(1.0, 61 - (ilogb(b) + 1));
+}
+
+template <bool kDipole>
+__global__ void k_deposit_det(Geom g, const uint32_t* __restrict__ total,
+                              const Rec64* __restrict__ recm, const Rec64* __restrict__ recp,
+                              const double* __restrict__ w,
+                              const unsigned long long* __restrict__ bound,
+                              unsigned long long* __restrict__ q128) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *total) return;
+  const int S = g.order == 2 ? 3 : 2;
+  const double scale = det_scale(kDipole, bound);
+  Axis<double> A[3];
+  particle_axes(g, recm, i, A);
+  double wv[3] = {0.0, 0.0, 0.0};
+  if (kDipole) {
+    const long long idx = recp[i].idx;
+    for (int d = 0; d < 3; ++d) wv[d] = w[3 * idx + d] * g.inv_h[d];
+  }
+  for (int c = 0; c < S; ++c)
+    for (int b = 0; b < S; ++b)
+      for (int a = 0; a < S; ++a) {
+        double v;
+        if (kDipole)
+          v = wv[0] * A[0].dw[a] * A[1].w[b] * A[2].w[c] +
+              wv[1] * A[0].w[a] * A[1].dw[b] * A[2].w[c] +
+              wv[2] * A[0].w[a] * A[1].w[b] * A[2].dw[c];
+        else
+          v = A[0].w[a] * A[1].w[b] * A[2].w[c];
+        const size_t node = (static_cast<size_t>(A[2].c + c) * g.n[1] + (A[1].c + b)) * g.n[0] +
+                            (A[0].c + a);
+        add128(q128 + 2 * node, __double2ll_rn(v * scale));
+      }
+}
+
+// the exact 128-bit node sums, rounded to FP64, into the doubled mesh's n^3 block
+template <bool kDipole>
+__global__ void k_q128_to_mesh(Geom g, const unsigned long long* __restrict__ q128,
+                               const unsigned long long* __restrict__ bound,
+                               double* __restrict__ qpad) {
+  const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  const size_t nn = static_cast<size_t>(g.n[0]) * g.n[1] * g.n[2];
+  if (t >= nn) return;
+  const unsigned long long lo = q128[2 * t];
+  const long long hi = static_cast<long long>(q128[2 * t + 1]);
+  const double v = static_cast<double>(hi) * 18446744073709551616.0 + static_cast<double>(lo);
+  const int gx = static_cast<int>(t % g.n[0]);
+  const int gy = static_cast<int>((t / g.n[0]) % g.n[1]);
+  const int gz = static_cast<int>(t / (static_cast<size_t>(g.n[0]) * g.n[1]));
+  qpad[real_index(g, gx, gy, gz)] = v / det_scale(kDipole, bound);
+}
+
+// Fixed-order sums for the deterministic energies: each block adds a fixed stride of the terms
+// and reduces them in a fixed tree into part[block]; one block then adds the parts in order.
+__device__ __forceinline__ double block_tree_sum(double v) {
+  __shared__ double ws[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kThreads / 32; ++k) r += ws[k];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_det_part_pp(const uint32_t* __restrict__ total, const D4* __restrict__ fpp,
+                              double* __restrict__ part) {
+  const uint32_t N = *total;
+  double s = 0.0;
+  for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < N; i += kDetBlocks * kThreads)
+    s += fpp[i].w;
+  const double r = block_tree_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+__global__ void k_det_part_mesh(Geom g, const double* __restrict__ qpad,
+                                const double* __restrict__ phi, double* __restrict__ part) {
+  const size_t nn = static_cast<size_t>(g.n[0]) * g.n[1] * g.n[2];
+  double s = 0.0;
+  for (size_t t = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; t < nn;
+       t += static_cast<size_t>(kDetBlocks) * kThreads) {
+    const int gx = static_cast<int>(t % g.n[0]);
+    const int gy = static_cast<int>((t / g.n[0]) % g.n[1]);
+    const int gz = static_cast<int>(t / (static_cast<size_t>(g.n[0]) * g.n[1]));
+    const size_t r = real_index(g, gx, gy, gz);
+    s += qpad[r] * phi[r];
+  }
+  const double r = block_tree_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+__global__ void k_det_combine(const double* __restrict__ part, double* __restrict__ out) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < kDetBlocks; k += kThreads) s += part[k];
+  const double r = block_tree_sum(s);
+  if (threadIdx.x == 0) *out = r;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -525,16 +668,20 @@ __device__ __forceinline__ void grad_central_phi(const Geom& g, const double* __
 template <typename T>
 __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
                          const typename RecT<T>::type* __restrict__ recm,
-                         const T* __restrict__ field, size_t nreal, void* __restrict__ fpp,
-                         int parts, float pp_scale_f, double pp_scale) {
-  // F = F^L + F^S for sorted particle i, written over its short-range entry (sorted order, so
-  // the writes are coalesced); k_unpermute then puts the forces in the caller's order
+                         const typename RecT<T>::type* __restrict__ recp,
+                         const T* __restrict__ field, size_t nreal,
+                         const void* __restrict__ fpp, int parts, float pp_scale_f,
+                         double pp_scale, double* __restrict__ f) {
+  // F = F^L + F^S for sorted particle i, written straight into the caller's order (f[idx]);
+  // particles the sort left out (outside the mesh) had their f zeroed by the binning
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
   Axis<T> ax[3];
   particle_axes(g, recm, i, ax);
+  const long long idx = orig_index(recp, i);
+  double* out = f + 3 * idx;
   if constexpr (sizeof(T) == 4) {
-    // FP32 path: long and short range combined in FP32
+    // FP32 path: long and short range combined in FP32, widened exactly to FP64
     float F[3] = {0.f, 0.f, 0.f};
     if (parts & 2) {
       float G[3];
@@ -544,14 +691,13 @@ __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
         grad_from_diff(g, field, nreal, ax, G);
       for (int d = 0; d < 3; ++d) F[d] = g.fscale_f[d] * G[d];
     }
-    float4* out = reinterpret_cast<float4*>(fpp) + i;
     if (parts & 1) {
-      const float4 s = *out;
-      F[0] = fmaf(pp_scale_f, s.x, F[0]);
-      F[1] = fmaf(pp_scale_f, s.y, F[1]);
-      F[2] = fmaf(pp_scale_f, s.z, F[2]);
+      const float4 sr = static_cast<const float4*>(fpp)[i];
+      F[0] = fmaf(pp_scale_f, sr.x, F[0]);
+      F[1] = fmaf(pp_scale_f, sr.y, F[1]);
+      F[2] = fmaf(pp_scale_f, sr.z, F[2]);
     }
-    *out = make_float4(F[0], F[1], F[2], 0.f);
+    for (int d = 0; d < 3; ++d) out[d] = float_to_double_exact(F[d]);
   } else {
     double F[3] = {0.0, 0.0, 0.0};
     if (parts & 2) {
@@ -562,42 +708,14 @@ __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
         grad_from_phi(g, field, ax, G);
       for (int d = 0; d < 3; ++d) F[d] = g.fscale[d] * static_cast<double>(G[d]);
     }
-    D4* out = reinterpret_cast<D4*>(fpp) + i;
     if (parts & 1) {
-      const D4 s = *out;
+      const D4 s = static_cast<const D4*>(fpp)[i];
       F[0] += pp_scale * s.x;
       F[1] += pp_scale * s.y;
       F[2] += pp_scale * s.z;
     }
-    *out = D4{F[0], F[1], F[2], 0.0};
+    for (int d = 0; d < 3; ++d) out[d] = F[d];
   }
-}
-
-// f[i] = the force of input particle i, gathered from sorted order through its sorted position
-// (keys[i] after the scatter); particles left out of the sort (outside the mesh) get zero.
-template <typename T>
-__global__ void k_unpermute(const uint32_t* __restrict__ pos, int64_t n,
-                            const void* __restrict__ fsorted, double* __restrict__ f) {
-  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t k = pos[i];
-  double F[3] = {0.0, 0.0, 0.0};
-  if (k != kInvalidKey) {
-    if constexpr (sizeof(T) == 4) {
-      const float4 s = reinterpret_cast<const float4*>(fsorted)[k];
-      F[0] = float_to_double_exact(s.x);
-      F[1] = float_to_double_exact(s.y);
-      F[2] = float_to_double_exact(s.z);
-    } else {
-      const D4 s = reinterpret_cast<const D4*>(fsorted)[k];
-      F[0] = s.x;
-      F[1] = s.y;
-      F[2] = s.z;
-    }
-  }
-  f[3 * i] = F[0];
-  f[3 * i + 1] = F[1];
-  f[3 * i + 2] = F[2];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -783,7 +901,49 @@ void launch_zero_block(const p3m_ctx* c) {
   cudaMemset3DAsync(pp, 0, make_cudaExtent(es * c->g.n[0], c->g.n[1], c->g.n[2]), c->work);
 }
 
+void launch_deposit_det(const p3m_ctx* c, int64_t n, const double* w) {
+  const uint32_t* total = c->starts + c->nkeys;
+  const size_t nn = static_cast<size_t>(c->g.n[0]) * c->g.n[1] * c->g.n[2];
+  cudaMemsetAsync(c->q128, 0, 2 * sizeof(unsigned long long) * nn, c->work);
+  const auto* recm = static_cast<const Rec64*>(c->recm);
+  const auto* recp = static_cast<const Rec64*>(c->recp);
+  if (w) {
+    cudaMemsetAsync(c->dbound, 0, sizeof(unsigned long long), c->work);
+    if (n > 0)
+      k_dipole_bound<<<blocks_for(n), kThreads, 0, c->work>>>(c->g, total, recp, w, c->dbound);
+    if (n > 0)
+      k_deposit_det<true><<<blocks_for(n), kThreads, 0, c->work>>>(c->g, total, recm, recp, w,
+                                                                     c->dbound, c->q128);
+    k_q128_to_mesh<true><<<blocks_for(nn), kThreads, 0, c->work>>>(
+        c->g, c->q128, c->dbound, static_cast<double*>(c->qpad));
+  } else {
+    if (n > 0)
+      k_deposit_det<false><<<blocks_for(n), kThreads, 0, c->work>>>(c->g, total, recm, recp,
+                                                                      nullptr, c->dbound, c->q128);
+    k_q128_to_mesh<false><<<blocks_for(nn), kThreads, 0, c->work>>>(
+        c->g, c->q128, c->dbound, static_cast<double*>(c->qpad));
+  }
+}
+
+void launch_det_sum_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
+  (void)n;
+  k_det_part_pp<<<kDetBlocks, kThreads, 0, s>>>(c->starts + c->nkeys,
+                                                 static_cast<const D4*>(c->fpp), c->dred);
+  k_det_combine<<<1, kThreads, 0, s>>>(c->dred, c->energy_acc);
+}
+
+void launch_det_sum_mesh(const p3m_ctx* c) {
+  k_det_part_mesh<<<kDetBlocks, kThreads, 0, c->work>>>(
+      c->g, static_cast<const double*>(c->qpad), static_cast<const double*>(c->phireal),
+      c->dred + kDetBlocks);
+  k_det_combine<<<1, kThreads, 0, c->work>>>(c->dred + kDetBlocks, c->energy_acc + 1);
+}
+
 void launch_deposit(const p3m_ctx* c, int64_t n) {
+  if (c->det) {
+    launch_deposit_det(c, n, nullptr);
+    return;
+  }
   if (n == 0) return;
   const uint32_t* total = c->starts + c->nkeys;
   const unsigned blocks = static_cast<unsigned>((n + kDepPerBlock - 1) / kDepPerBlock);
@@ -798,6 +958,10 @@ void launch_deposit(const p3m_ctx* c, int64_t n) {
 }
 
 void launch_dipole_deposit(const p3m_ctx* c, int64_t n, const double* w) {
+  if (c->det) {
+    launch_deposit_det(c, n, w);
+    return;
+  }
   if (n == 0) return;
   const uint32_t* total = c->starts + c->nkeys;
   const unsigned blocks = static_cast<unsigned>((n + kDepPerBlock - 1) / kDepPerBlock);
@@ -832,17 +996,16 @@ void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts) {
   if (n == 0) return;
   const uint32_t* total = c->starts + c->nkeys;
   const double pp_scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc);
-  if (c->fp32) {
+  if (c->fp32)
     k_interp<float><<<blocks_for(n), kThreads, 0, c->work>>>(
-        c->g, total, static_cast<const float4*>(c->recp), static_cast<const float*>(c->freal),
-        c->n_real, c->fpp, parts, static_cast<float>(pp_scale), pp_scale);
-    k_unpermute<float><<<blocks_for(n), kThreads, 0, c->work>>>(c->keys, n, c->fpp, f);
-  } else {
+        c->g, total, static_cast<const float4*>(c->recp), static_cast<const float4*>(c->recp),
+        static_cast<const float*>(c->freal), c->n_real, c->fpp, parts,
+        static_cast<float>(pp_scale), pp_scale, f);
+  else
     k_interp<double><<<blocks_for(n), kThreads, 0, c->work>>>(
-        c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const double*>(c->phireal),
-        c->n_real, c->fpp, parts, static_cast<float>(pp_scale), pp_scale);
-    k_unpermute<double><<<blocks_for(n), kThreads, 0, c->work>>>(c->keys, n, c->fpp, f);
-  }
+        c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp),
+        static_cast<const double*>(c->phireal), c->n_real, c->fpp, parts,
+        static_cast<float>(pp_scale), pp_scale, f);
 }
 
 void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, double* out) {

@@ -182,14 +182,17 @@ def gradient(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps:
 
 def gradient_coords(precision: int = m.FP64, n_particles: int = 16_384, steps: int = 200,
                     every: int = 20, coords: int = 64, dt: float = 2.5e-13, eps_rel: float = 1e-6,
-                    seed: int = 0):
+                    seed: int = 0, deterministic: int = 0, compare_fp32: bool = True):
     """Reverse-pass gradient of J against central finite differences on randomly chosen single
     coordinates (positions and momenta), step eps_rel times that component's rms spread; and the
-    FP32 mixed path's reverse pass against the FP64 one on every coordinate."""
+    FP32 mixed path's reverse pass against the FP64 one on every coordinate. deterministic = 1
+    (FP64) makes every trajectory bitwise reproducible, so the differences carry no summation
+    noise."""
     x, p = _grad_bunch(n_particles)
     base = dict(n=(64,) * 3, rc_over_h=2.0, adj_slots=(steps + every - 1) // every,
                 adj_segment=every)
-    prm = m.auto_mesh(_cuda(x * 1.05), m.Params(precision=precision, **base))
+    prm = m.auto_mesh(_cuda(x * 1.05), m.Params(precision=precision, deterministic=deterministic,
+                                                **base))
     ctx = m.Context(prm, n_particles)
     x0, p0 = _cuda(x), _cuda(p)
 
@@ -228,13 +231,16 @@ def gradient_coords(precision: int = m.FP64, n_particles: int = 16_384, steps: i
     fd, ad = np.array(fd), np.array(ad)
     rel = np.abs(fd - ad) / np.maximum(np.abs(fd), 1e-300)
     out = {"experiment": "gradient_coords", "n": n_particles, "steps": steps, "dt": dt,
-           "checkpoint_every": every, "precision": precision, "coords": coords,
+           "checkpoint_every": every, "precision": precision, "deterministic": deterministic,
+           "coords": coords,
            "eps_rel": eps_rel, "rel_l2_over_coords": float(np.linalg.norm(fd - ad)
                                                           / np.linalg.norm(fd)),
            "max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
            "coords_above_1e-4": int((rel > 1e-4).sum()),
            "seconds_gradient": t_grad, "seconds_fd": t_fd}
-    if precision == m.FP64:
+    out["fd"] = fd.tolist()
+    out["adjoint"] = ad.tolist()
+    if precision == m.FP64 and compare_fp32:
         ctx.close()
         c32 = m.Context(m.auto_mesh(_cuda(x * 1.05), m.Params(precision=m.FP32_MIXED, **base)),
                         n_particles)
@@ -498,6 +504,12 @@ def main(argv):
         kw["n_particles"] = int(argv[argv.index("--n") + 1])
     if "--save" in argv:
         kw["save"] = argv[argv.index("--save") + 1]
+    if "--det" in argv:
+        kw["deterministic"] = 1
+    if "--coords" in argv:
+        kw["coords"] = int(argv[argv.index("--coords") + 1])
+    if "--steps" in argv:
+        kw["steps"] = int(argv[argv.index("--steps") + 1])
     fn = {"boundary": boundary, "energy": energy, "gradient": gradient,
           "gradient_coords": gradient_coords,
           "influence": influence, "error_measure": error_measure, "action": action,

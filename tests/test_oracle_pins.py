@@ -526,11 +526,7 @@ def test_discrete_action_is_stationary_on_the_trajectory():
     P, dt, X = _leapfrog_trajectory()
 
     def S(Xs):
-        tot = 0.0
-        for n in range(len(Xs) - 1):
-            R = O.forces(Xs[n], P)
-            tot += 0.5 * P.mass * ((Xs[n + 1] - Xs[n]) ** 2).sum() / dt ** 2 - (R.U_pp + R.U_pm)
-        return tot * dt
+        return O.discrete_action(Xs, dt, P)
 
     rng = np.random.default_rng(3)
     V = [np.zeros_like(X[0])] + [rng.standard_normal(X[0].shape) for _ in X[1:-1]] + \
