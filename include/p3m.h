@@ -109,8 +109,7 @@ p3m_status p3m_auto_mesh(const double* x, int64_t n, p3m_params* inout, void* st
 /* Validates params, allocates every buffer for up to n_max particles, creates the FFT
  * plans and builds the Green's-function spectra (eq. (phi_L), eq. (GreenFunc_planar_cathode)).
  * `stream` (cudaStream_t, may be NULL) becomes the context's stream. *out is set on success.
- * EINVAL: bad params or n_max outside [1, 2^31 - 1] (FP32 mixed precision: [1, 2^30]);
- * ENOMEM / ECUFFT / ECUDA on failure
+ * EINVAL: bad params or n_max outside [1, 2^31 - 1]; ENOMEM / ECUFFT / ECUDA on failure
  * (nothing is leaked). */
 p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m_ctx** out);
 

@@ -104,7 +104,6 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   const double cap = std::max<double>(4.0 * static_cast<double>(n_max), 1 << 20);
   auto layout = [&](int rows, int nsub) {
     g.rows = rows;
-    g.xunit = 1.0f / static_cast<float>(nsub);
     g.cw[0] = (1.0 + 1e-9) / nsub;
     g.cw[1] = g.cw[2] = (1.0 + 4.0 * g.slack) / rows;
     double cells = 1.0;
@@ -215,7 +214,6 @@ cudaError_t alloc(T** ptr, size_t count) {
 
 void free_all(p3m_ctx* c) {
   void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recm, c->fpp,
-                  c->recs, c->left,
                   c->acc, c->qpad, c->qhat, c->qhat2, c->khat_f, c->khat_i, c->fhat, c->freal,
                   c->phihat, c->phireal, c->dfac, c->ztw, c->box_real, c->box_spec, c->box_mult,
                   c->energy_acc, c->pair_acc,
@@ -502,8 +500,6 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     return P3M_EINVAL;
   }
   if (n_max < 1 || n_max > 2147483647LL) return P3M_EINVAL;
-  // the FP32 short range packs sorted indices into 30 bits
-  if (params->precision == P3M_FP32_MIXED && n_max > (1LL << 30)) return P3M_EINVAL;
   auto* c = new p3m_ctx();
   c->prm = *params;
   c->g = make_geom(params, n_max);
@@ -537,10 +533,6 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   if (!c->fp32) A(cudaMalloc(&c->recm, 32 * static_cast<size_t>(n_max)));  // FP32: in recp
   // short-range result: FP64 {F, phi} (32 B); FP32 float4
   A(cudaMalloc(&c->fpp, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
-  if (c->fp32) {
-    A(alloc(&c->recs, n_max + 1));  // + a sentinel record far from every particle
-    A(alloc(&c->left, n_max / 2 + 2));
-  }
   A(alloc(&c->acc, 3 * n_max));
   A(cudaMalloc(&c->qpad, es * c->n_real));
   A(cudaMalloc(&c->qhat, 2 * es * c->n_cplx));
@@ -598,11 +590,6 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   }
   *c->err_host = 0;
   cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->work);
-  if (c->fp32) {
-    // the short range's sentinel: every separation to it is about 1e18 cutoff lengths
-    static const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.f);
-    cudaMemcpyAsync(c->recs + n_max, &far, sizeof(float4), cudaMemcpyHostToDevice, c->work);
-  }
   cudaMemsetAsync(c->qpad, 0, es * c->n_real, c->work);
   cudaMemsetAsync(c->qhat, 0, 2 * es * c->n_cplx, c->work);  // planes z >= n_z stay zero
   if (c->fp32) {

@@ -67,18 +67,7 @@ struct Geom {
   float inv_h_df[3][2];  // 1 / h_d
   float fscale_f[3];     // -q / h_d in FP32
   float rch_df[3][2];    // r_c / h_d: cutoff units -> mesh units
-  float xunit;           // 1 / nsub (a power of two): the x origin of a search record's cell
 };
-
-// FP32 search record of a sorted particle (16 B, float4): its position in cutoff units relative
-// to origins whose differences are exact in FP32, so that the short range gets every separation
-// to a few 1e-8 cutoff lengths from three subtractions:
-//   x: x_loc = x - ox, ox = cx * xunit (cx the particle's x cell); stored with ox in w.
-//      dx = (x_loc_i - x_loc_j) + (ox_i - ox_j), the second difference exact;
-//   y, z: y_loc = y - ry * cw_y (ry the particle's row); between rows ry and ry + k,
-//      dy = (y_loc_i - k cw_y) - y_loc_j, with k cw_y exact (|k| <= 2).
-// The 32-byte record (hi + lo) keeps the position to 2^-46 relative for the mesh kernels, the
-// images and the rare pairs closer than 1e-2 r_c.
 
 // FP32 records: the lo part's w packs the particle's row (rz nc_y + ry, below 2^26) and, in the
 // top 6 bits, a node correction of -1, 0 or +1 per axis (2 bits each, stored + 1) that turns the
@@ -259,9 +248,6 @@ struct p3m_ctx {
   void* recp = nullptr;         // [n_max] sorted positions, cutoff units (2 float4 / Rec64)
   void* recm = nullptr;         // [n_max] FP64 path: sorted assignment records (Rec64)
   void* fpp = nullptr;          // [n_max] short-range result, sorted (FP32 float4, FP64 D4)
-  float4* recs = nullptr;       // [n_max] FP32 path: search records (SearchRec layout)
-  uint32_t* left = nullptr;     // [n_max / 2 + 2] FP32 path: [0] count, then sorted indices of
-                                // particles the paired walk leaves to a second pass
   double* acc = nullptr;        // [3 n_max] adjoint accumulator, sorted order
 
   // mesh

@@ -303,377 +303,134 @@ __device__ __forceinline__ void pair_runs(const Geom& g, const uint32_t* __restr
   }
 }
 
-// ------------------------------------------------------------------------------------------
-// FP32 short range with the candidate tests separated from the pair evaluations.
-//
-// Pairs: as above, particle i takes the pairs (i, j) with j > i in sorted order. Lane l of a
-// tile holds the adjacent sorted particles a = 2l and b = a + 1 when they share a cell row;
-// otherwise b goes to a list that a second launch works through, one particle per lane (so no
-// lane of the first launch carries two run lists). Per neighbour row the lane walks the hull of
-// a's and b's runs (13 rows of the half shell, or 5 with rows r_c wide), one candidate record
-// per step, and tests it against both particles.
-//
-// Tests read the 16-byte search records (SearchRec): a separation is three subtractions from
-// cell-local coordinates, accurate to a few 1e-8 cutoff lengths. A record within the cutoff of
-// a or b is pushed, with a's separation and the two hit flags, into the lane's ring of pending
-// pairs in shared memory. When some lane's ring is full the warp evaluates one pending entry per
-// lane: the pair function for a and b side by side in the two-wide FP32 instructions, the force
-// on a and b added to their sums in registers and the reaction on j (both particles' share)
-// added to j's result by one vector reduction. The pair function thus runs on pairs only (a ring
-// entry holds at least one), instead of on every lane's candidate as a lockstep walk would.
-//
-// Accumulation: the sums of a and b are folded into two-float (TwoSum) accumulators every 16
-// evaluations. Reactions are FP32 reductions: a particle with m reactions gets at most m
-// roundings of half an ulp of its running sum (FP64 reductions would need FP64 conversions and
-// additions in every evaluation, which this part runs at a small fraction of the FP32 rate).
-// Pairs closer than 1e-2 r_c (about one in a million) take their separation from the 32-byte
-// hi + lo records instead, exact to FP32 relative rounding.
-// ------------------------------------------------------------------------------------------
-// resident blocks per SM of the FP32 short range (its register budget: 65536 / (128 x blocks));
-// a build-time tuning value
-#ifndef P3M_PP32_BLOCKS
-#define P3M_PP32_BLOCKS 5
-#endif
-constexpr int kPp32BlocksPerSm = P3M_PP32_BLOCKS;
-
-__device__ __forceinline__ float4 ldg_nc(const float4* p) {
-  float4 v;
-  asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
-      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-      : "l"(p));
-  return v;
-}
-
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-
-// packed squared distance of (a, b): the same operations in the tests and in the evaluations,
-// so that an evaluation sees the r^2 its test saw
-__device__ __forceinline__ float2 dist2(float2 dx, float2 dy, float2 dz) {
-  float2 r2 = __fmul2_rn(dx, dx);
-  r2 = __ffma2_rn(dy, dy, r2);
-  return __ffma2_rn(dz, dz, r2);
-}
-
-// the pair function of pair_poly_hw for two pairs at once (r2 in (0, 1] in both lanes)
-template <int kDeg>
-__device__ __forceinline__ void pair_poly_hw2(const PairPoly& P, float2 r2, float2& fco,
-                                              float2& pot) {
-  const float2 rinv = f2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-  const float2 rho = __fmul2_rn(r2, rinv);
-  const float2 t = __ffma2_rn(f2(2.f, 2.f), rho, f2(-1.f, -1.f));
-  float2 R = f2(P.c[kDeg], P.c[kDeg]);
-#pragma unroll
-  for (int m = kDeg - 1; m >= 0; --m) R = __ffma2_rn(R, t, f2(P.c[m], P.c[m]));
-  const float2 arg = __fmul2_rn(f2(-P.kappa2_log2e, -P.kappa2_log2e), r2);
-  const float2 ex = f2(ex2_ftz(arg.x), ex2_ftz(arg.y));
-  pot = __fmul2_rn(__fmul2_rn(R, ex), rinv);
-  fco = __fmul2_rn(__ffma2_rn(f2(P.c2k, P.c2k), ex, pot), __fmul2_rn(rinv, rinv));
-}
-
-// exact separation of sorted particles i and j from the 32-byte records (hi + lo)
-__device__ __forceinline__ void exact_sep(const float4* __restrict__ rec, uint32_t i, uint32_t j,
-                                          float& dx, float& dy, float& dz) {
-  const float4 hi = rec[2 * static_cast<size_t>(i)], li = rec[2 * static_cast<size_t>(i) + 1];
-  const float4 hj = rec[2 * static_cast<size_t>(j)], lj = rec[2 * static_cast<size_t>(j) + 1];
-  dx = (hi.x - hj.x) + (li.x - lj.x);
-  dy = (hi.y - hj.y) + (li.y - lj.y);
-  dz = (hi.z - hj.z) + (li.z - lj.z);
-}
-
-template <int kDeg, int kRows, bool kLeft>
-__global__ void __launch_bounds__(kThreads, kPp32BlocksPerSm)
+template <int kDeg, int kRows>
+__global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
-             const float4* __restrict__ recs, const float4* __restrict__ rec,
-             const uint32_t* __restrict__ starts, float4* __restrict__ fs,
-             uint32_t* __restrict__ next_tile, uint32_t* __restrict__ left,
-             double* __restrict__ energy, unsigned long long* __restrict__ pairs,
-             uint32_t sentinel) {
-  using RW = Rows<kRows>;
-  constexpr int kW = kThreads / 32;
-  constexpr int kR = RW::half;
-  constexpr uint32_t kTile = kLeft ? 32u : 64u;  // particles per warp tile
-  // per warp: the owners' runs, the owners' particle data and the owners' sums (each owner's
-  // particles a and b: x, y, z, phi)
-  __shared__ uint2 run_s[kW][kR][32];      // {j0, length}
-  __shared__ uint8_t rrow_s[kW][kR][32];   // the run's row in the half shell
-  __shared__ uint8_t nrun_s[kW][32];       // runs per owner
-  __shared__ float4 own_s[kW][2][32];      // {x_loc, y_loc, z_loc, x_org}, {b - a, b alive}
-  // the owners' sums, gathered without atomics: a lane's chunk covers its first owner's
-  // candidates in part (sum in first_s[lane]), owners in the middle in full (mid_s[owner]) and
-  // its last owner in part (last_s[lane]); fo_s / lo_s name the first and last owner
-  __shared__ float mid_s[kW][8][32];
-  __shared__ float first_s[kW][8][32];
-  __shared__ float last_s[kW][8][32];
-  __shared__ uint8_t fo_s[kW][32], lo_s[kW][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t N = kLeft ? left[0] : *total;
-  const uint32_t nc1 = static_cast<uint32_t>(g.nc[1]);
-  float e_hi = 0.f, e_lo = 0.f;  // sum of the particles' potentials (compensated)
+             const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
+             float4* __restrict__ fpp, uint32_t* __restrict__ next_tile,
+             double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
+  constexpr uint32_t kTile = 2 * kThreads;  // particles per tile
+  // a's and b's runs: up to twice the half shell when their rows differ
+  constexpr int kPairRuns = 2 * Rows<kRows>::half;
+  __shared__ uint32_t run_j0[kPairRuns][kThreads], run_j1[kPairRuns][kThreads];
+  __shared__ uint32_t tile_s;
+  const int tid = threadIdx.x;
+  const uint32_t N = *total;
+  double e_acc = 0.0;
   unsigned long long np = 0, ni = 0;
+  // persistent blocks: each takes the next tile of kTile sorted particles until none is left
+  // (the block's four warps work on adjacent particles, which share most of their neighbours
+  // in L1)
   for (;;) {
-    uint32_t tile = 0;
-    if (lane == 0) tile = atomicAdd(next_tile, 1u);
-    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tid == 0) tile_s = atomicAdd(next_tile, 1u);
+    __syncthreads();
+    const uint32_t tile = tile_s;
+    __syncthreads();
     if (static_cast<uint64_t>(tile) * kTile >= N) break;
-    // ---- the owner: particles a and b of this lane ----
-    uint32_t a, b;
-    bool alive_a, alive_b;
-    if (kLeft) {
-      const uint32_t t = tile * kTile + lane;
-      alive_a = t < N;
-      a = alive_a ? left[1 + t] : 0u;
-      b = a;
-      alive_b = false;
-    } else {
-      a = tile * kTile + 2 * lane;
-      b = a + 1;
-      alive_a = a < N;
-      alive_b = b < N;
-    }
-    const uint32_t ea = alive_a ? a : 0u;
-    const uint32_t rowa = __float_as_uint(rec[2 * static_cast<size_t>(ea) + 1].w) & kRowMask;
-    if (alive_b) {
-      const uint32_t rowb = __float_as_uint(rec[2 * static_cast<size_t>(b) + 1].w) & kRowMask;
-      if (rowb != rowa) {  // a row boundary between a and b: b to the second pass
-        left[1 + atomicAdd(left, 1u)] = b;
-        alive_b = false;
-      }
-    }
-    const uint32_t eb = alive_b ? b : ea;
-    const float4 sa = recs[ea], sb = recs[eb];
-    const int cya = static_cast<int>(rowa % nc1), cza = static_cast<int>(rowa / nc1);
-    // runs: per neighbour row of the half shell, the hull of a's and b's runs
-    uint32_t L = 0;  // this owner's candidates
-    int nr = 0;
-    if (alive_a) {
-      // positions for the row search (FP32 in cutoff units; the search slack covers rounding)
-      const float ry0 = static_cast<float>(cya) * g.cw_f[1];
-      const float rz0 = static_cast<float>(cza) * g.cw_f[2];
-      const float pax = sa.w + sa.x, pay = ry0 + sa.y, paz = rz0 + sa.z;
-      const float pbx = sb.w + sb.x, pby = ry0 + sb.y, pbz = rz0 + sb.z;
-#pragma unroll 1
-      for (int r = RW::first; r < RW::last; ++r) {
-        uint32_t j0, j1;
-        row_range<kRows>(g, starts, pax, pay, paz, cya, cza, r, j0, j1);
-        j0 = max(j0, a + 1);
-        if (alive_b) {
-          uint32_t k0, k1;
-          row_range<kRows>(g, starts, pbx, pby, pbz, cya, cza, r, k0, k1);
-          k0 = max(k0, b + 1);
-          if (k0 < k1) {
-            j0 = j0 < j1 ? min(j0, k0) : k0;
-            j1 = max(j1, k1);
-          }
-        }
-        if (j0 < j1) {
-          run_s[w][nr][lane] = make_uint2(j0, j1 - j0);
-          rrow_s[w][nr][lane] = static_cast<uint8_t>(r);
-          L += j1 - j0;
-          ++nr;
-        }
-      }
-    }
-    nrun_s[w][lane] = static_cast<uint8_t>(nr);
-    own_s[w][0][lane] = sa;
-    own_s[w][1][lane] = make_float4(
-        __fadd_rn(__fsub_rn(sb.x, sa.x), __fsub_rn(sb.w, sa.w)), __fsub_rn(sb.y, sa.y),
-        __fsub_rn(sb.z, sa.z), alive_b ? 1.f : 0.f);
-    for (int c = 0; c < 8; ++c) mid_s[w][c][lane] = 0.f;
-    fo_s[w][lane] = lo_s[w][lane] = 0xff;
-    __syncwarp();
-    // ---- balanced chunks: the warp's candidates, owner by owner, cut into 32 equal parts ----
-    uint32_t incl = L;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
-    const uint32_t c0 = static_cast<uint32_t>((static_cast<uint64_t>(lane) * T) >> 5);
-    const uint32_t c1 = static_cast<uint32_t>((static_cast<uint64_t>(lane + 1) * T) >> 5);
-    uint32_t rem = c1 - c0;  // candidates left in this lane's chunk
-    // owner of candidate c0: the first lane whose inclusive prefix exceeds c0
-    int o = 0;
-    {
-      int lo = 0, hi = 31;
-#pragma unroll
-      for (int it = 0; it < 5; ++it) {
-        const int mid = (lo + hi) >> 1;
-        const uint32_t pm = __shfl_sync(0xffffffffu, incl, mid);
-        if (pm > c0) hi = mid; else lo = mid + 1;
-      }
-      o = lo;
-    }
-    const uint32_t before = __shfl_sync(0xffffffffu, incl - L, o);  // exclusive prefix of o
-    // run and offset of c0 within owner o (only lanes with work read the owner's runs)
+    const uint32_t ia = tile * kTile + 2 * tid, ib = ia + 1;
+    const bool alive_a = ia < N, alive_b = ib < N;
+    // lanes past the last particle read record 0 (in bounds) and take part in the lockstep
+    // loop with every result masked out
+    const uint32_t ea = alive_a ? ia : 0u, eb = alive_b ? ib : ea;
+    const float4 pa = rec[2 * ea], la = rec[2 * ea + 1];
+    const float4 pb = rec[2 * eb], lb = rec[2 * eb + 1];
+    // runs: with a and b in one row, the hull of their two runs per neighbour row (tested
+    // against both); otherwise a's runs [0, split) and b's runs [split, cnt)
+    int cnt = 0, split = 0;
+    bool same = true;
+    if (alive_a)
+      pair_runs<kRows>(g, starts, pa, la, pb, lb, ia, alive_b, same, split,
+                       [&](uint32_t j0, uint32_t j1) {
+                  run_j0[cnt][tid] = j0;
+                  run_j1[cnt][tid] = j1;
+                  ++cnt;
+                });
+    uint32_t ptr = 0, end = 0;
     int k = 0;
-    uint32_t ptr = 0, rrem = 0;
-    float4 oa = make_float4(0.f, 0.f, 0.f, 0.f), od = oa;
-    float yo = 0.f, zo = 0.f;
-    auto load_run = [&]() {
-      const uint2 q = run_s[w][k][o];
-      const int r = rrow_s[w][k][o];
-      // offsets toward row (cya + dy, cza + dz) of the owner: k cw is exact for |k| <= 2
-      yo = __fsub_rn(oa.y, static_cast<float>((r % RW::span) - RW::reach) * g.cw_f[1]);
-      zo = __fsub_rn(oa.z, static_cast<float>((r / RW::span) - RW::reach) * g.cw_f[2]);
-      return q;
-    };
-    if (rem > 0) {
-      oa = own_s[w][0][o];
-      od = own_s[w][1][o];
-      uint32_t off = c0 - before;
-      uint2 q = load_run();
-      while (off >= q.y) {
-        off -= q.y;
-        ++k;
-        q = load_run();
-      }
-      ptr = q.x + off;
-      rrem = q.y - off;
+    if (cnt > 0) {
+      ptr = run_j0[0][tid];
+      end = run_j1[0][tid];
     }
-    // ---- candidate tests and pair evaluations, one candidate record per lane and step ----
-    float2 qx = f2(0.f, 0.f), qy = qx, qz = qx, qp = qx;  // (a, b) partial sums
-    Acc2 sum[8];                                          // a: x y z phi, b: x y z phi
-    for (int c = 0; c < 8; ++c) sum[c].hi = sum[c].lo = 0.f;
-    float nhit = 0.f;  // pairs evaluated by this lane (exact as a float below 2^24 per tile)
-    auto fold = [&]() {
-      sum[0].add(qx.x);
-      sum[1].add(qy.x);
-      sum[2].add(qz.x);
-      sum[3].add(qp.x);
-      sum[4].add(qx.y);
-      sum[5].add(qy.y);
-      sum[6].add(qz.y);
-      sum[7].add(qp.y);
-      qx = qy = qz = qp = f2(0.f, 0.f);
+    bool ta = same || split > 0;                  // the current run is tested against a
+    bool tb = alive_b && (same || split == 0);    // ... and against b
+    Acc2 sa[4], sb[4];
+    for (int c = 0; c < 4; ++c) sa[c].hi = sa[c].lo = sb[c].hi = sb[c].lo = 0.f;
+    float qa[4] = {0.f, 0.f, 0.f, 0.f}, qb[4] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t np_part = 0;
+    // one candidate record j (hj, lj) against a and b
+    auto cand = [&](bool v, uint32_t j, const float4& hj, const float4& lj) {
+      const float ax = (pa.x - hj.x) + (la.x - lj.x);
+      const float ay = (pa.y - hj.y) + (la.y - lj.y);
+      const float az = (pa.z - hj.z) + (la.z - lj.z);
+      const float bx = (pb.x - hj.x) + (lb.x - lj.x);
+      const float by = (pb.y - hj.y) + (lb.y - lj.y);
+      const float bz = (pb.z - hj.z) + (lb.z - lj.z);
+      const float r2a = ax * ax + ay * ay + az * az;
+      const float r2b = bx * bx + by * by + bz * bz;
+      // coincident particles (r2 == 0) are skipped
+      const bool ha = v && ta && r2a < 1.f && r2a > 0.f;
+      const bool hb = v && tb && r2b < 1.f && r2b > 0.f;
+      float fa, ua, fb, ub;
+      pair_poly_hw<kDeg>(P, ha ? r2a : 0.5f, fa, ua);
+      pair_poly_hw<kDeg>(P, hb ? r2b : 0.5f, fb, ub);
+      fa = ha ? fa : 0.f;
+      ua = ha ? ua : 0.f;
+      fb = hb ? fb : 0.f;
+      ub = hb ? ub : 0.f;
+      const float fax = fa * ax, fay = fa * ay, faz = fa * az;
+      const float fbx = fb * bx, fby = fb * by, fbz = fb * bz;
+      qa[0] += fax;
+      qa[1] += fay;
+      qa[2] += faz;
+      qa[3] += ua;
+      qb[0] += fbx;
+      qb[1] += fby;
+      qb[2] += fbz;
+      qb[3] += ub;
+      np_part += static_cast<uint32_t>(ha) + static_cast<uint32_t>(hb);
+      red_add_v4_if(ha || hb, fpp + j, -(fax + fbx), -(fay + fby), -(faz + fbz), ua + ub);
     };
-    // a finished owner segment: the lane's first one to first_s, a middle one (the owner's
-    // candidates all in this chunk) to mid_s, the last one to last_s
-    int seg = 0;
-    auto store_segment = [&](int owner, bool last) {
-      fold();
-      float* dst;
-      if (seg == 0) {
-        dst = &first_s[w][0][lane];
-        fo_s[w][lane] = static_cast<uint8_t>(owner);
-      } else if (last) {
-        dst = &last_s[w][0][lane];
-        lo_s[w][lane] = static_cast<uint8_t>(owner);
-      } else {
-        dst = &mid_s[w][0][owner];
-      }
-      for (int c = 0; c < 8; ++c) {
-        dst[32 * c] = sum[c].value();
-        sum[c].hi = sum[c].lo = 0.f;
-      }
-      ++seg;
-    };
-    // the next candidate's record is loaded one step ahead
-    float4 rj = ldg_nc(recs + (rem > 0 ? ptr : sentinel));
     int step = 0;
-    while (__any_sync(0xffffffffu, rem > 0)) {
-      const bool v = rem > 0;
-      const float4 cur = rj;
-      const uint32_t jc = ptr;
-      const int oc = o;
-      const float xo = oa.x, xw = oa.w, yc = yo, zc = zo;
-      const float4 dc = od;
-      // advance: the next candidate of this run, of the owner's next run, or of the next owner
-      // (lanes whose chunk is done keep their counters at zero)
-      if (v) {
-        --rem;
-        --rrem;
-        ++ptr;
+    while (__any_sync(0xffffffffu, ptr < end)) {
+      // a lane without a candidate reads record 0, as every such lane does, so that the load
+      // costs the warp one extra sector at most; its results are masked out
+      const bool va = ptr < end, vb = ptr + 1 < end;
+      const uint32_t ja = va ? ptr : 0u, jb = vb ? ptr + 1 : 0u;
+      float4 h0, l0, h1, l1;  // both loads in flight before either record is used
+      load_rec32(rec + 2 * static_cast<size_t>(ja), h0, l0);
+      load_rec32(rec + 2 * static_cast<size_t>(jb), h1, l1);
+      cand(va, ja, h0, l0);
+      cand(vb, jb, h1, l1);
+      ptr += 2;
+      {
+        // the next run without a branch: slot k stays in bounds (k < cnt, or k = 0)
+        const bool sw = ptr >= end && k + 1 < cnt;
+        k += sw ? 1 : 0;
+        const uint32_t nj0 = run_j0[k][tid], nj1 = run_j1[k][tid];
+        ptr = sw ? nj0 : ptr;
+        end = sw ? nj1 : end;
+        ta = same || k < split;
+        tb = alive_b && (same || k >= split);
       }
-      if (v && rem > 0 && rrem == 0) {
-        ++k;
-        while (k >= nrun_s[w][o]) {
-          ++o;
-          k = 0;
-          oa = own_s[w][0][o];
-          od = own_s[w][1][o];
+      if ((++step & 15) == 0) {
+        for (int c = 0; c < 4; ++c) {
+          sa[c].add(qa[c]);
+          sb[c].add(qb[c]);
+          qa[c] = qb[c] = 0.f;
         }
-        const uint2 q = load_run();
-        ptr = q.x;
-        rrem = q.y;
-      }
-      rj = ldg_nc(recs + (rem > 0 ? ptr : sentinel));
-      // the current candidate against the owner's a and b (b's separation is a's plus b - a)
-      const float dxa = __fadd_rn(__fsub_rn(xo, cur.x), __fsub_rn(xw, cur.w));
-      const float dya = __fsub_rn(yc, cur.y), dza = __fsub_rn(zc, cur.z);
-      float2 DX = f2(dxa, __fadd_rn(dxa, dc.x)), DY = f2(dya, __fadd_rn(dya, dc.y)),
-             DZ = f2(dza, __fadd_rn(dza, dc.z));
-      float2 R2 = dist2(DX, DY, DZ);
-      // hit masks in FP32 (1 or 0): 0 < r2 < 1  <=>  r2 (1 - r2) > 0, saturated; a lane with
-      // nothing left reads the sentinel record far away (r2 ~ 1e36), b only if alive
-      const float2 t = __ffma2_rn(f2(-R2.x, -R2.y), R2, R2);
-      float2 m = f2(__saturatef(t.x * 1e38f), __saturatef(t.y * 1e38f) * dc.w);
-      // masked lanes evaluate the pair function at r2 = 1/2
-      float2 R2m = __ffma2_rn(__fadd2_rn(R2, f2(-0.5f, -0.5f)), m, f2(0.5f, 0.5f));
-      if (fminf(R2m.x, R2m.y) < 1e-4f) {
-        bool fa = m.x != 0.f, fb = m.y != 0.f;
-        // very close pair: the exact separation from the hi + lo records
-        const uint32_t ia = kLeft ? left[1 + tile * kTile + oc] : tile * kTile + 2 * oc;
-        float x0, y0, z0;
-        if (fa) {
-          exact_sep(rec, ia, jc, x0, y0, z0);
-          DX.x = x0, DY.x = y0, DZ.x = z0;
-        }
-        if (fb) {
-          exact_sep(rec, ia + 1, jc, x0, y0, z0);
-          DX.y = x0, DY.y = y0, DZ.y = z0;
-        }
-        R2 = dist2(DX, DY, DZ);
-        fa = fa && R2.x > 0.f && R2.x < 1.f;
-        fb = fb && R2.y > 0.f && R2.y < 1.f;
-        m = f2(fa ? 1.f : 0.f, fb ? 1.f : 0.f);
-        R2m = f2(fa ? R2.x : 0.5f, fb ? R2.y : 0.5f);
-      }
-      float2 FCO, POT;
-      pair_poly_hw2<kDeg>(P, R2m, FCO, POT);
-      FCO = __fmul2_rn(FCO, m);
-      POT = __fmul2_rn(POT, m);
-      const float2 FX = __fmul2_rn(FCO, DX), FY = __fmul2_rn(FCO, DY), FZ = __fmul2_rn(FCO, DZ);
-      qx = __fadd2_rn(qx, FX);
-      qy = __fadd2_rn(qy, FY);
-      qz = __fadd2_rn(qz, FZ);
-      qp = __fadd2_rn(qp, POT);
-      const float hits = m.x + m.y;
-      red_add_v4_if(hits != 0.f, fs + jc, -__fadd_rn(FX.x, FX.y), -__fadd_rn(FY.x, FY.y),
-                    -__fadd_rn(FZ.x, FZ.y), 0.f);
-      nhit += hits;
-      if (oc != o) store_segment(oc, false);  // the owner's last candidate of this chunk
-      if ((++step & 15) == 0) fold();
-    }
-    if (c1 > c0) store_segment(o, true);
-    np += static_cast<unsigned long long>(nhit);
-    __syncwarp();
-    // the owner's sums: its segments from the lanes whose chunks cover its candidates
-    Acc2 own[8];
-    for (int c = 0; c < 8; ++c) own[c].hi = own[c].lo = 0.f;
-    if (L > 0) {
-      const uint32_t pf = incl - L, pl = incl - 1;  // the owner's first and last candidate
-      // lane whose chunk holds candidate c: the largest l with l T < 32 (c + 1)
-      const int l0 = static_cast<int>((32ull * (pf + 1) - 1) / T);
-      const int l1 = static_cast<int>((32ull * (pl + 1) - 1) / T);
-      for (int l = l0; l <= l1; ++l) {
-        const float* src;
-        if (fo_s[w][l] == lane)
-          src = &first_s[w][0][l];
-        else if (lo_s[w][l] == lane)
-          src = &last_s[w][0][l];
-        else
-          src = &mid_s[w][0][lane];  // one lane's chunk holds all of the owner's candidates
-        for (int c = 0; c < 8; ++c) own[c].add(src[32 * c]);
+        np += np_part;
+        np_part = 0;
       }
     }
-    __syncwarp();  // the segment arrays are reused by the next tile
-    // ---- the owner's images and its own sums, energy ----
-    const float pair_pot_a = own[3].value(), pair_pot_b = own[7].value();
+    for (int c = 0; c < 4; ++c) {
+      sa[c].add(qa[c]);
+      sb[c].add(qb[c]);
+    }
+    np += np_part;
+    const float pair_pot_a = sa[3].value(), pair_pot_b = sb[3].value();
     // images within r_c of particles less than r_c above the cathode (rare): plain loop over
     // all rows around the image point; image pairs act on the particle only
-    auto images = [&](uint32_t i, Acc2* acc) {
-      const float4 pi = rec[2 * static_cast<size_t>(i)], li = rec[2 * static_cast<size_t>(i) + 1];
+    auto images = [&](const float4 pi, const float4 li, Acc2* sum) {
       const double zi = static_cast<double>(pi.z) + static_cast<double>(li.z);
       if (zi - 0.5 * g.img_c >= 1.0) return;
       const float mz = static_cast<float>(g.img_c - zi);
@@ -700,31 +457,24 @@ __global__ void __launch_bounds__(kThreads, kPp32BlocksPerSm)
             ++ni;
           }
         }
-        for (int c = 0; c < 4; ++c) acc[c].add(rowv[c]);
+        for (int c = 0; c < 4; ++c) sum[c].add(rowv[c]);
       });
     };
     if (g.pp_bc) {
-      if (alive_a) images(a, own);
-      if (alive_b) images(b, own + 4);
+      if (alive_a) images(pa, la, sa);
+      if (alive_b) images(pb, lb, sb);
     }
-    // own sums (reactions from other lanes arrive concurrently, by the same reduction)
-    auto add_energy = [&](float v) {
-      const DF t = df_two_sum(e_hi, v);
-      e_hi = t.hi;
-      e_lo += t.lo;
-    };
+    // sum_i phi_i over ordered pairs: each pair's potential was taken once here, plus images
     if (alive_a) {
-      red_add_v4(fs + a, own[0].value(), own[1].value(), own[2].value(), 0.f);
-      add_energy(own[3].value());
-      add_energy(pair_pot_a);
+      red_add_v4(fpp + ia, sa[0].value(), sa[1].value(), sa[2].value(), sa[3].value());
+      e_acc += static_cast<double>(sa[3].value()) + pair_pot_a;
     }
     if (alive_b) {
-      red_add_v4(fs + b, own[4].value(), own[5].value(), own[6].value(), 0.f);
-      add_energy(own[7].value());
-      add_energy(pair_pot_b);
+      red_add_v4(fpp + ib, sb[0].value(), sb[1].value(), sb[2].value(), sb[3].value());
+      e_acc += static_cast<double>(sb[3].value()) + pair_pot_b;
     }
   }
-  if (energy) block_reduce_add(static_cast<double>(e_hi) + static_cast<double>(e_lo), energy);
+  if (energy) block_reduce_add(e_acc, energy);
   warp_add_u64(2ull * np, pairs);
   warp_add_u64(ni, pairs + 1);
 }
@@ -1165,52 +915,30 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
     // the kernel adds each pair's force to both particles: the result starts at zero
     cudaMemsetAsync(c->fpp, 0, sizeof(float4) * static_cast<size_t>(n), s);
     cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
-    cudaMemsetAsync(c->left, 0, sizeof(uint32_t), s);
-    // persistent grids of a few blocks per SM; the second launch takes the particles the first
-    // left over (those whose sorted neighbour starts a new cell row)
+    // persistent grid of a few blocks per SM: the SM resources it leaves free let the mesh
+    // chain, on the other stream, run at the same time
     const int64_t tiles = (n + 2 * kThreads - 1) / (2 * kThreads);  // two particles a thread
-    const int64_t cap = static_cast<int64_t>(kPp32BlocksPerSm) * c->num_sms;
-    const unsigned wblocks = static_cast<unsigned>(std::min<int64_t>(tiles, cap));
-    const int64_t ltiles = (n / 2 + kThreads) / kThreads;
-    const unsigned lblocks = static_cast<unsigned>(std::min<int64_t>(ltiles, cap));
-    auto run = [&](auto k_rows1, auto k_rows2, auto l_rows1, auto l_rows2) {
-      const bool one = c->g.rows == 1;
-      auto kern = one ? k_rows1 : k_rows2;
-      auto lern = one ? l_rows1 : l_rows2;
-      const auto* recs = c->recs;
-      const auto* rec = static_cast<const float4*>(c->recp);
-      float4* fs = static_cast<float4*>(c->fpp);
-      // recs[n_max] holds a record far from every particle: lanes with nothing to test read it
-      const uint32_t sentinel = static_cast<uint32_t>(c->n_max);
-      kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, recs, rec, c->starts, fs,
-                                        c->pp_tile, c->left, c->energy_acc, c->pair_acc,
-                                        sentinel);
-      cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
-      lern<<<lblocks, kThreads, 0, s>>>(c->g, c->poly, total, recs, rec, c->starts, fs,
-                                        c->pp_tile, c->left, c->energy_acc, c->pair_acc,
-                                        sentinel);
+    const unsigned wblocks = static_cast<unsigned>(
+        std::min<int64_t>(tiles, static_cast<int64_t>(kPpBlocksPerSm) * c->num_sms));
+    // the kernel for the context's row geometry (Geom::rows cell rows per cutoff)
+    auto run = [&](auto k_rows1, auto k_rows2) {
+      auto kern = c->g.rows == 1 ? k_rows1 : k_rows2;
+      kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
+                                       c->starts, static_cast<float4*>(c->fpp), c->pp_tile,
+                                       c->energy_acc, c->pair_acc);
     };
-#define P3M_PP_CASE(D)                                                                   \
-  case D:                                                                               \
-    run(k_pp_f32<D, 1, false>, k_pp_f32<D, 2, false>, k_pp_f32<D, 1, true>,             \
-        k_pp_f32<D, 2, true>);                                                          \
-    break;
     switch (c->poly.deg) {
-      P3M_PP_CASE(6)
-      P3M_PP_CASE(7)
-      P3M_PP_CASE(8)
-      P3M_PP_CASE(9)
-      P3M_PP_CASE(10)
-      P3M_PP_CASE(11)
-      P3M_PP_CASE(12)
-      P3M_PP_CASE(13)
-      P3M_PP_CASE(14)
-      default:
-        run(k_pp_f32<15, 1, false>, k_pp_f32<15, 2, false>, k_pp_f32<15, 1, true>,
-            k_pp_f32<15, 2, true>);
-        break;
+      case 6: run(k_pp_f32<6, 1>, k_pp_f32<6, 2>); break;
+      case 7: run(k_pp_f32<7, 1>, k_pp_f32<7, 2>); break;
+      case 8: run(k_pp_f32<8, 1>, k_pp_f32<8, 2>); break;
+      case 9: run(k_pp_f32<9, 1>, k_pp_f32<9, 2>); break;
+      case 10: run(k_pp_f32<10, 1>, k_pp_f32<10, 2>); break;
+      case 11: run(k_pp_f32<11, 1>, k_pp_f32<11, 2>); break;
+      case 12: run(k_pp_f32<12, 1>, k_pp_f32<12, 2>); break;
+      case 13: run(k_pp_f32<13, 1>, k_pp_f32<13, 2>); break;
+      case 14: run(k_pp_f32<14, 1>, k_pp_f32<14, 2>); break;
+      default: run(k_pp_f32<15, 1>, k_pp_f32<15, 2>); break;
     }
-#undef P3M_PP_CASE
   } else {
     auto kern = c->det ? (c->g.rows == 1 ? k_pp_f64<1, true> : k_pp_f64<2, true>)
                        : (c->g.rows == 1 ? k_pp_f64<1, false> : k_pp_f64<2, false>);

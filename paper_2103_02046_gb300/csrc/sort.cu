@@ -184,7 +184,7 @@ template <bool kFP32>
 __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
                           uint32_t* __restrict__ keys, const uint32_t* __restrict__ ranks,
                           const uint32_t* __restrict__ starts, void* __restrict__ recp,
-                          void* __restrict__ recm, float4* __restrict__ recs) {
+                          void* __restrict__ recm) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n) return;
   const uint32_t key = keys[i];
@@ -221,23 +221,6 @@ __global__ void k_scatter(Geom g, const double* __restrict__ x, int64_t n,
     float4* r = reinterpret_cast<float4*>(recp) + 2 * static_cast<size_t>(pos);
     r[0] = make_float4(hi[0], hi[1], hi[2], __int_as_float(static_cast<int>(i)));
     r[1] = make_float4(lo[0], lo[1], lo[2], __uint_as_float(row | (code << kRowBits)));
-    // search record: the position relative to origins the short range can difference exactly
-    // (see SearchRec): x from cx * xunit (a power of two times an integer), y and z from the
-    // row corner ry * cw_y, rz * cw_z (their differences are small multiples of one float)
-    const int cxi = static_cast<int>(key % static_cast<uint32_t>(g.nc[0]));
-    const int ryi = static_cast<int>(row % static_cast<uint32_t>(g.nc[1]));
-    const int rzi = static_cast<int>(row / static_cast<uint32_t>(g.nc[1]));
-    const float ox = static_cast<float>(cxi) * g.xunit;  // exact
-    const float org[3] = {ox, static_cast<float>(ryi), static_cast<float>(rzi)};
-    float loc[3];
-    loc[0] = __fadd_rn(__fsub_rn(hi[0], ox), lo[0]);  // hi - ox is exact (same binade or 0)
-    for (int d = 1; d < 3; ++d) {
-      // origin k cw as an exact double-float (k < 2^24): p + e with e from an FMA
-      const float p = __fmul_rn(org[d], g.cw_f[d]);
-      const float e = __fmaf_rn(org[d], g.cw_f[d], -p);
-      loc[d] = df_sub(DF{hi[d], lo[d]}, DF{p, e}).hi;
-    }
-    recs[pos] = make_float4(loc[0], loc[1], loc[2], ox);
     return;
   }
   double xr[3], u[3];
@@ -333,10 +316,10 @@ void launch_scatter(const p3m_ctx* c, const double* x, int64_t n) {
   if (n == 0) return;
   if (c->fp32)
     k_scatter<true><<<grid_for(n, kBinThreads), kBinThreads, 0, c->work>>>(
-        c->g, x, n, c->keys, c->ranks, c->starts, c->recp, c->recm, c->recs);
+        c->g, x, n, c->keys, c->ranks, c->starts, c->recp, c->recm);
   else {
     k_scatter<false><<<grid_for(n, kBinThreads), kBinThreads, 0, c->work>>>(
-        c->g, x, n, c->keys, c->ranks, c->starts, c->recp, c->recm, nullptr);
+        c->g, x, n, c->keys, c->ranks, c->starts, c->recp, c->recm);
     if (c->det)
       k_cell_order<<<static_cast<unsigned>((c->nkeys + kBinThreads - 1) / kBinThreads),
                      kBinThreads, 0, c->work>>>(c->nkeys, c->starts, static_cast<Rec64*>(c->recp),

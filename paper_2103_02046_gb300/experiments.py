@@ -125,6 +125,9 @@ def energy(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps: i
 
     E0, f = total_energy()
     P0 = pg.sum(dim=0).clone()
+    # the short range conserves momentum pair by pair: sum_i F^S_i against sum_i |F^S_i|
+    fs = ctx.forces(xg, parts=1)
+    sum_fs_rel = float(torch.linalg.norm(fs.sum(dim=0))) / float(torch.linalg.norm(fs, dim=1).sum())
     t0 = time.time()
     energies = [E0]
     for _ in range(steps // 10):
@@ -138,7 +141,7 @@ def energy(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps: i
             "E0": E0, "rel_drift_final": (energies[-1] - E0) / abs(E0),
             "rel_drift_max": max(abs(e - E0) for e in energies) / abs(E0),
             "momentum_change_rel": float(torch.linalg.norm(P1 - P0)) / scale,
-            "seconds": elapsed}
+            "short_range_force_sum_rel": sum_fs_rel, "seconds": elapsed}
 
 
 def gradient(precision: int = m.FP32_MIXED, n_particles: int = 1_048_576, steps: int = 200,
