@@ -35,9 +35,9 @@ from paper_2103_02046_gb300 import bunches as B  # noqa: E402
 
 METRIC = "P3M force evals/s and PP pair-interactions/s at N=16M, FP32 vs FP64 at stated error"
 FLOPS_PER_PAIR = 37.0  # algorithmic FP32 flops per in-cutoff pair (FFMA = 2, incl. 3 MUFU)
-KERNELS_PER_EVAL = 10  # bin, 3 scan passes, scatter, short range (paired pass + second pass),
-                       # deposit, fused z solve, interpolation + combination in the caller's
-                       # order (cuFFT's kernels not counted)
+KERNELS_PER_EVAL = 10  # bin, 3 scan passes, scatter, short range, deposit, fused z solve,
+                       # interpolation, combination in the caller's order (cuFFT's kernels
+                       # not counted)
 # DRAM bytes (read + write) of one k_pp_f32<12, 2> launch per particle, from an ncu capture of the
 # 2,097,152-particle sphere on a 128^3 mesh (123.9 MB per launch, profiles/k_pp_f32_sphere2m_128.md).
 # The kernel reads each 32-B record about once from DRAM (the neighbour runs and the reduction

@@ -214,6 +214,7 @@ cudaError_t alloc(T** ptr, size_t count) {
 
 void free_all(p3m_ctx* c) {
   void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recm, c->fpp,
+                  c->fplo,
                   c->acc, c->qpad, c->qhat, c->qhat2, c->khat_f, c->khat_i, c->fhat, c->freal,
                   c->phihat, c->phireal, c->dfac, c->ztw, c->box_real, c->box_spec, c->box_mult,
                   c->energy_acc, c->pair_acc,
@@ -533,6 +534,7 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   if (!c->fp32) A(cudaMalloc(&c->recm, 32 * static_cast<size_t>(n_max)));  // FP32: in recp
   // short-range result: FP64 {F, phi} (32 B); FP32 float4
   A(cudaMalloc(&c->fpp, (c->fp32 ? 16 : 32) * static_cast<size_t>(n_max)));
+  if (c->fp32) A(alloc(&c->fplo, 2 * n_max));  // fine parts, then big terms
   A(alloc(&c->acc, 3 * n_max));
   A(cudaMalloc(&c->qpad, es * c->n_real));
   A(cudaMalloc(&c->qhat, 2 * es * c->n_cplx));

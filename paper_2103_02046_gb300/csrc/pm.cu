@@ -227,8 +227,6 @@ __device__ __forceinline__ long long orig_index(const Rec64* recp, uint32_t i) {
 constexpr int kDepThreads = 256;
 constexpr int kDepItems = 4;
 constexpr int kDepPerBlock = kDepThreads * kDepItems;
-static_assert(kDepPerBlock == 32 * 32 && kDepThreads / 32 * kDepItems == 32,
-              "the deposit's slot map covers a block's particles once");
 constexpr int kTileBytes = 32768;
 
 template <typename T, bool kDipole>
@@ -259,15 +257,10 @@ __global__ void __launch_bounds__(kDepThreads)
     bmax[threadIdx.x] = -1;
   }
   __syncthreads();
-  // particle slot of (thread, item): the lanes of a warp take particles 32 apart in sorted order
-  // (about 8 cutoff lengths along a row), so that one warp's shared-memory atomics rarely hit the
-  // same node; consecutive particles of a cell share all their nodes
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  auto slot = [&](int k) { return b0 + lane * 32u + warp * kDepItems + static_cast<uint32_t>(k); };
   int lmin[3] = {1 << 30, 1 << 30, 1 << 30}, lmax[3] = {-1, -1, -1};
 #pragma unroll
   for (int k = 0; k < kDepItems; ++k) {
-    const uint32_t i = slot(k);
+    const uint32_t i = b0 + k * kDepThreads + threadIdx.x;
     if (i < N) {
       Axis<T> ax[3];
       particle_axes(g, recm, i, ax);
@@ -295,7 +288,7 @@ __global__ void __launch_bounds__(kDepThreads)
     for (int t = threadIdx.x; t < ex * ey * ez; t += kDepThreads) tile[t] = Slot(0);
   __syncthreads();
   for (int k = 0; k < kDepItems; ++k) {
-    const uint32_t i = slot(k);
+    const uint32_t i = b0 + k * kDepThreads + threadIdx.x;
     if (i >= N) continue;
     Axis<T> A[3];
     particle_axes(g, recm, i, A);
@@ -668,20 +661,17 @@ __device__ __forceinline__ void grad_central_phi(const Geom& g, const double* __
 template <typename T>
 __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
                          const typename RecT<T>::type* __restrict__ recm,
-                         const typename RecT<T>::type* __restrict__ recp,
-                         const T* __restrict__ field, size_t nreal,
-                         const void* __restrict__ fpp, int parts, float pp_scale_f,
-                         double pp_scale, double* __restrict__ f) {
-  // F = F^L + F^S for sorted particle i, written straight into the caller's order (f[idx]);
-  // particles the sort left out (outside the mesh) had their f zeroed by the binning
+                         const T* __restrict__ field, size_t nreal, void* __restrict__ fpp,
+                         const float4* __restrict__ fplo, const float4* __restrict__ fbig,
+                         int parts, float pp_scale_f, double pp_scale) {
+  // F = F^L + F^S for sorted particle i, written over its short-range entry (sorted order, so
+  // the writes are coalesced); k_unpermute then puts the forces in the caller's order
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
   Axis<T> ax[3];
   particle_axes(g, recm, i, ax);
-  const long long idx = orig_index(recp, i);
-  double* out = f + 3 * idx;
   if constexpr (sizeof(T) == 4) {
-    // FP32 path: long and short range combined in FP32, widened exactly to FP64
+    // FP32 path: long and short range combined in FP32
     float F[3] = {0.f, 0.f, 0.f};
     if (parts & 2) {
       float G[3];
@@ -691,13 +681,15 @@ __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
         grad_from_diff(g, field, nreal, ax, G);
       for (int d = 0; d < 3; ++d) F[d] = g.fscale_f[d] * G[d];
     }
+    float4* out = reinterpret_cast<float4*>(fpp) + i;
     if (parts & 1) {
-      const float4 sr = static_cast<const float4*>(fpp)[i];
-      F[0] = fmaf(pp_scale_f, sr.x, F[0]);
-      F[1] = fmaf(pp_scale_f, sr.y, F[1]);
-      F[2] = fmaf(pp_scale_f, sr.z, F[2]);
+      // the short range: its coarse, fine and big parts
+      const float4 s = *out, l = fplo[i], b = fbig[i];
+      F[0] = fmaf(pp_scale_f, (s.x + l.x) + b.x, F[0]);
+      F[1] = fmaf(pp_scale_f, (s.y + l.y) + b.y, F[1]);
+      F[2] = fmaf(pp_scale_f, (s.z + l.z) + b.z, F[2]);
     }
-    for (int d = 0; d < 3; ++d) out[d] = float_to_double_exact(F[d]);
+    *out = make_float4(F[0], F[1], F[2], 0.f);
   } else {
     double F[3] = {0.0, 0.0, 0.0};
     if (parts & 2) {
@@ -708,14 +700,42 @@ __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
         grad_from_phi(g, field, ax, G);
       for (int d = 0; d < 3; ++d) F[d] = g.fscale[d] * static_cast<double>(G[d]);
     }
+    D4* out = reinterpret_cast<D4*>(fpp) + i;
     if (parts & 1) {
-      const D4 s = static_cast<const D4*>(fpp)[i];
+      const D4 s = *out;
       F[0] += pp_scale * s.x;
       F[1] += pp_scale * s.y;
       F[2] += pp_scale * s.z;
     }
-    for (int d = 0; d < 3; ++d) out[d] = F[d];
+    *out = D4{F[0], F[1], F[2], 0.0};
   }
+}
+
+// f[i] = the force of input particle i, gathered from sorted order through its sorted position
+// (keys[i] after the scatter); particles left out of the sort (outside the mesh) get zero.
+template <typename T>
+__global__ void k_unpermute(const uint32_t* __restrict__ pos, int64_t n,
+                            const void* __restrict__ fsorted, double* __restrict__ f) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = pos[i];
+  double F[3] = {0.0, 0.0, 0.0};
+  if (k != kInvalidKey) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 s = reinterpret_cast<const float4*>(fsorted)[k];
+      F[0] = float_to_double_exact(s.x);
+      F[1] = float_to_double_exact(s.y);
+      F[2] = float_to_double_exact(s.z);
+    } else {
+      const D4 s = reinterpret_cast<const D4*>(fsorted)[k];
+      F[0] = s.x;
+      F[1] = s.y;
+      F[2] = s.z;
+    }
+  }
+  f[3 * i] = F[0];
+  f[3 * i + 1] = F[1];
+  f[3 * i + 2] = F[2];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -996,16 +1016,18 @@ void launch_interp(const p3m_ctx* c, int64_t n, double* f, int parts) {
   if (n == 0) return;
   const uint32_t* total = c->starts + c->nkeys;
   const double pp_scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc);
-  if (c->fp32)
+  if (c->fp32) {
     k_interp<float><<<blocks_for(n), kThreads, 0, c->work>>>(
-        c->g, total, static_cast<const float4*>(c->recp), static_cast<const float4*>(c->recp),
-        static_cast<const float*>(c->freal), c->n_real, c->fpp, parts,
-        static_cast<float>(pp_scale), pp_scale, f);
-  else
+        c->g, total, static_cast<const float4*>(c->recp), static_cast<const float*>(c->freal),
+        c->n_real, c->fpp, c->fplo, c->fplo + c->n_max, parts, static_cast<float>(pp_scale),
+        pp_scale);
+    k_unpermute<float><<<blocks_for(n), kThreads, 0, c->work>>>(c->keys, n, c->fpp, f);
+  } else {
     k_interp<double><<<blocks_for(n), kThreads, 0, c->work>>>(
-        c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const Rec64*>(c->recp),
-        static_cast<const double*>(c->phireal), c->n_real, c->fpp, parts,
-        static_cast<float>(pp_scale), pp_scale, f);
+        c->g, total, static_cast<const Rec64*>(c->recm), static_cast<const double*>(c->phireal),
+        c->n_real, c->fpp, nullptr, nullptr, parts, static_cast<float>(pp_scale), pp_scale);
+    k_unpermute<double><<<blocks_for(n), kThreads, 0, c->work>>>(c->keys, n, c->fpp, f);
+  }
 }
 
 void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, double* out) {

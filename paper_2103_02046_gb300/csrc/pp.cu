@@ -185,6 +185,64 @@ __device__ __forceinline__ void red_add_v4_if(bool p, float4* dst, float a, floa
       : "memory");
 }
 
+// Error-free split of a short-range force component about the grid of multiples of
+// kSplitQ = 2^-6 (the kernel's force unit is the pair force at a cutoff length's scale, so the
+// terms are O(1) and a particle's sums stay far below 2^24 kSplitQ even with tens of thousands
+// of neighbours): v = c + f exactly, with c a multiple of kSplitQ and |f| <= kSplitQ / 2.
+// Adding kSplitC = 1.5 * 2^23 * kSplitQ rounds v to that grid (the sum's last mantissa bit is
+// worth kSplitQ); subtracting it again is exact (Sterbenz), and so is v - c. The coarse parts c
+// of one particle's terms are multiples of kSplitQ, so their FP32 atomic sum is exact, and
+// independent of the order, while it stays below 2^24 kSplitQ in magnitude; only the small
+// parts f are rounded when summed.
+constexpr float kSplitQ = 0.015625f;
+constexpr float kSplitC = 1.5f * 8388608.f * kSplitQ;
+// A term of magnitude 2^21 kSplitQ or more (a pair closer than about 0.006 cutoff lengths)
+// would take the coarse sum out of its exact range: it goes whole to a third array (big), where
+// a particle rarely has more than one term.
+constexpr float kBigTerm = 2097152.f * kSplitQ;
+// (in PTX, so that no compiler pass folds (v + C) - C into v)
+__device__ __forceinline__ void split_q(float v, float& c, float& f) {
+  float t;
+  asm("add.rn.f32 %0, %1, %2;" : "=f"(t) : "f"(v), "f"(kSplitC));
+  asm("sub.rn.f32 %0, %1, %2;" : "=f"(c) : "f"(t), "f"(kSplitC));
+  asm("sub.rn.f32 %0, %1, %2;" : "=f"(f) : "f"(v), "f"(c));
+}
+
+__device__ __forceinline__ bool big_term(float a, float b, float c) {
+  return fmaf(a, a, fmaf(b, b, c * c)) >= kBigTerm * kBigTerm;
+}
+
+// One particle's short-range force held as three float4 arrays: coarse (co) + fine (fi) + big
+// (bg). Each added term is split, its coarse part reduced into co and its fine part into fi, or,
+// if it is big, reduced whole into bg. The result is the exact sum up to the rounding of the
+// fine sums, whose terms are at most kSplitQ / 2, and of the (rare) big terms. `big` may be
+// set for terms below kBigTerm too (a cheaper test that never misses a big term).
+__device__ __forceinline__ void split_add_v4_if(bool p, bool big, float4* co, float4* fi,
+                                                float4* bg, float a, float b, float c) {
+  float ac, af, bc, bf, cc, cf;
+  split_q(a, ac, af);
+  split_q(b, bc, bf);
+  split_q(c, cc, cf);
+  red_add_v4_if(p && !big, co, ac, bc, cc, 0.f);
+  red_add_v4_if(p && !big, fi, af, bf, cf, 0.f);
+  if (p && big) red_add_v4(bg, ac + af, bc + bf, cc + cf, 0.f);  // = (a, b, c) exactly; rare
+}
+// the same for a compensated sum hi + lo (lo far below hi): hi is split, lo joins the fine part
+__device__ __forceinline__ void split_add_v4(float4* co, float4* fi, float4* bg, float a, float b,
+                                             float c, float la, float lb, float lc) {
+  if (big_term(a, b, c)) {
+    red_add_v4(bg, a, b, c, 0.f);
+    red_add_v4(fi, la, lb, lc, 0.f);
+    return;
+  }
+  float ac, af, bc, bf, cc, cf;
+  split_q(a, ac, af);
+  split_q(b, bc, bf);
+  split_q(c, cc, cf);
+  red_add_v4(co, ac, bc, cc, 0.f);
+  red_add_v4(fi, __fadd_rn(af, la), __fadd_rn(bf, lb), __fadd_rn(cf, lc), 0.f);
+}
+
 __device__ __forceinline__ float rsqrt_ftz(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -307,7 +365,8 @@ template <int kDeg, int kRows>
 __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
              const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
-             float4* __restrict__ fpp, uint32_t* __restrict__ next_tile,
+             float4* __restrict__ fpp, float4* __restrict__ flo, float4* __restrict__ fbig,
+             uint32_t* __restrict__ next_tile,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
   constexpr uint32_t kTile = 2 * kThreads;  // particles per tile
   // a's and b's runs: up to twice the half shell when their rows differ
@@ -388,7 +447,10 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
       qb[2] += fbz;
       qb[3] += ub;
       np_part += static_cast<uint32_t>(ha) + static_cast<uint32_t>(hb);
-      red_add_v4_if(ha || hb, fpp + j, -(fax + fbx), -(fay + fby), -(faz + fbz), ua + ub);
+      // the reaction on j, split into coarse and fine parts (j's potential is summed on the
+      // owner side only); it is big only if fa + fb is, as separations are below 1
+      split_add_v4_if(ha || hb, fa + fb >= kBigTerm, fpp + j, flo + j, fbig + j, -(fax + fbx),
+                      -(fay + fby), -(faz + fbz));
     };
     int step = 0;
     while (__any_sync(0xffffffffu, ptr < end)) {
@@ -465,12 +527,15 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
       if (alive_b) images(pb, lb, sb);
     }
     // sum_i phi_i over ordered pairs: each pair's potential was taken once here, plus images
+    // the own sums (hi + lo of the compensated accumulators), split like the reactions
     if (alive_a) {
-      red_add_v4(fpp + ia, sa[0].value(), sa[1].value(), sa[2].value(), sa[3].value());
+      split_add_v4(fpp + ia, flo + ia, fbig + ia, sa[0].hi, sa[1].hi, sa[2].hi, sa[0].lo,
+                   sa[1].lo, sa[2].lo);
       e_acc += static_cast<double>(sa[3].value()) + pair_pot_a;
     }
     if (alive_b) {
-      red_add_v4(fpp + ib, sb[0].value(), sb[1].value(), sb[2].value(), sb[3].value());
+      split_add_v4(fpp + ib, flo + ib, fbig + ib, sb[0].hi, sb[1].hi, sb[2].hi, sb[0].lo,
+                   sb[1].lo, sb[2].lo);
       e_acc += static_cast<double>(sb[3].value()) + pair_pot_b;
     }
   }
@@ -912,8 +977,12 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   const uint32_t* total = c->starts + c->nkeys;
   if (c->fp32) {
-    // the kernel adds each pair's force to both particles: the result starts at zero
+    // the kernel adds each pair's force to both particles: the result (coarse, fine and big
+    // parts) starts at zero
+    float4* fbig = c->fplo + c->n_max;
     cudaMemsetAsync(c->fpp, 0, sizeof(float4) * static_cast<size_t>(n), s);
+    cudaMemsetAsync(c->fplo, 0, sizeof(float4) * static_cast<size_t>(n), s);
+    cudaMemsetAsync(fbig, 0, sizeof(float4) * static_cast<size_t>(n), s);
     cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
     // persistent grid of a few blocks per SM: the SM resources it leaves free let the mesh
     // chain, on the other stream, run at the same time
@@ -924,8 +993,8 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
     auto run = [&](auto k_rows1, auto k_rows2) {
       auto kern = c->g.rows == 1 ? k_rows1 : k_rows2;
       kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
-                                       c->starts, static_cast<float4*>(c->fpp), c->pp_tile,
-                                       c->energy_acc, c->pair_acc);
+                                       c->starts, static_cast<float4*>(c->fpp), c->fplo, fbig,
+                                       c->pp_tile, c->energy_acc, c->pair_acc);
     };
     switch (c->poly.deg) {
       case 6: run(k_pp_f32<6, 1>, k_pp_f32<6, 2>); break;
