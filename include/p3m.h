@@ -89,6 +89,17 @@ typedef struct p3m_params {
                             variational, so p3m_force_vjp and p3m_backward refuse it with
                             P3M_ESTATE); every particle's assignment support must then keep one
                             node off the mesh edge (else P3M_ERANGE) */
+  int32_t search_rows;   /* short-range search cells (Sec. 2.4, the cell list that finds the pairs
+                            of eq. (summation_short)): rows per cutoff length in y and z, 1, 2 or
+                            3; 0 (default) chooses from the mesh and n_max: 3 when the estimated
+                            neighbour count (n_max particles over the mesh volume, per cutoff
+                            sphere) is 200 or more, else 2, or 1 where the cell budget
+                            (max(4 n_max, 2^20) cells) leaves no room for rows r_c/2 wide with
+                            x cells r_c/4. Results do not depend on it beyond rounding order */
+  int32_t search_xcells; /* x cells per cutoff length, 1, 2, 4, 8, 16 or 32; 0 (default) chooses
+                            (4, or 16 with 3 rows, fewer where the cell budget requires). A
+                            layout with an explicit search_rows or search_xcells over the cell
+                            budget gives P3M_EINVAL */
 } p3m_params;
 
 typedef struct p3m_ctx p3m_ctx; /* opaque; owns all scratch memory */
@@ -154,6 +165,12 @@ p3m_status p3m_pair_count(p3m_ctx* ctx, int64_t* pairs, int64_t* image_pairs);
  * *candidates is written on success; synchronises the context's stream. P3M_EINVAL for a NULL
  * argument. */
 p3m_status p3m_candidate_count(p3m_ctx* ctx, int64_t* candidates);
+
+/* The short-range search layout the context uses (Sec. 2.4, the cell list behind
+ * eq. (summation_short)): cell rows per cutoff length in y and z (1, 2 or 3) and x cells per
+ * cutoff length, as chosen at p3m_create from search_rows / search_xcells. Host only, no device
+ * work. P3M_EINVAL for a NULL argument. */
+p3m_status p3m_search_layout(const p3m_ctx* ctx, int32_t* rows, int32_t* xcells);
 
 /* Leapfrog, eq. (leapfrog) with the Stoermer form of eq. (eom_p3m_coord), as kick-drift-kick
  * (a reading: the paper leaves the start-up open):

@@ -66,6 +66,12 @@ p3m_status validate(const p3m_params* p, std::string* why) {
     return P3M_EINVAL;
   }
   if (p->force_diff != 0 && p->force_diff != 1) { *why = "force_diff must be 0 or 1"; return P3M_EINVAL; }
+  if (p->search_rows < 0 || p->search_rows > 3) { *why = "search_rows must be 0, 1, 2 or 3"; return P3M_EINVAL; }
+  if (p->search_xcells < 0 || p->search_xcells > 32 ||
+      (p->search_xcells & (p->search_xcells - 1)) != 0) {
+    *why = "search_xcells must be 0, 1, 2, 4, 8, 16 or 32";
+    return P3M_EINVAL;
+  }
   if (p->adj_slots < 0 || p->adj_segment < 0 || (p->adj_slots > 0 && p->adj_segment < 1)) { *why = "adj_slots/adj_segment invalid"; return P3M_EINVAL; }
   if (!std::isfinite(p->q) || p->q == 0.0) { *why = "q must be finite and nonzero"; return P3M_EINVAL; }
   if (!finite_pos(p->mass)) { *why = "mass must be > 0"; return P3M_EINVAL; }
@@ -114,8 +120,34 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
     }
     return cells;
   };
-  if (layout(2, 4) > cap)
-    for (int nsub = 4; layout(1, nsub) > cap && nsub > 1;) nsub /= 2;
+  // Dense bunches: with hundreds of neighbours per particle the per-particle setup of more rows
+  // is cheap next to the pairs, and narrower rows with shorter x cells cut the records tested
+  // that are not pairs (in a uniform-density model, 46% of the records a particle tests are
+  // pairs with rows r_c/2 and x cells r_c/4, 61% with rows r_c/3 and x cells r_c/16). The
+  // neighbour estimate takes n_max particles over the mesh volume (a Gaussian bunch's core is
+  // denser still).
+  const double vol = std::max(ext[0], 1e-3) * std::max(ext[1], 1e-3) * std::max(ext[2], 1e-3);
+  const double neighbours = static_cast<double>(n_max) * 4.18879020478639 / vol;
+  if (p->search_rows > 0) {
+    int nsub = p->search_xcells > 0 ? p->search_xcells : (p->search_rows == 3 ? 16 : 4);
+    while (layout(p->search_rows, nsub) > cap && p->search_xcells == 0 && nsub > 1) nsub /= 2;
+    if (layout(p->search_rows, nsub) > cap) g.rows = 0;  // refused by p3m_create
+  } else {
+    bool dense = false;
+    if (neighbours >= 200.0)
+      for (int nsub = p->search_xcells > 0 ? p->search_xcells : 16; nsub >= 4 && !dense; nsub /= 2)
+        dense = layout(3, nsub) <= cap;
+    if (!dense) {
+      const int nsub0 = p->search_xcells > 0 ? p->search_xcells : 4;
+      if (layout(2, nsub0) > cap) {
+        // (with nsub = 1 the layout stands even over the budget; p3m_create still refuses
+        // 2^32 cells or more)
+        int nsub = nsub0;
+        while (layout(1, nsub) > cap && nsub > 1 && p->search_xcells == 0) nsub /= 2;
+        if (p->search_xcells > 0 && layout(1, nsub) > cap) g.rows = 0;
+      }
+    }
+  }
   for (int d = 0; d < 3; ++d) {
     g.cw_f[d] = static_cast<float>(g.cw[d]);
     g.inv_cw_f[d] = static_cast<float>(g.inv_cw[d]);
@@ -451,6 +483,8 @@ p3m_status p3m_default_params(p3m_params* p) {
   p->z_cathode = 0.0;
   p->influence = 0;
   p->force_diff = 0;
+  p->search_rows = 0;
+  p->search_xcells = 0;
   p->precision = P3M_FP64;
   p->deterministic = 0;
   p->adj_slots = 0;
@@ -504,6 +538,11 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   auto* c = new p3m_ctx();
   c->prm = *params;
   c->g = make_geom(params, n_max);
+  if (c->g.rows == 0) {
+    std::fprintf(stderr, "p3m_create: the short-range search layout exceeds the cell budget\n");
+    delete c;
+    return P3M_EINVAL;
+  }
   c->poly = fit_pair_poly(c->g.kappa_eff);
   c->n_max = n_max;
   c->fp32 = params->precision == P3M_FP32_MIXED;
@@ -755,6 +794,13 @@ p3m_status p3m_candidate_count(p3m_ctx* c, int64_t* candidates) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
   if (e != cudaSuccess) return cuda_fail(c, e, "p3m_candidate_count");
   *candidates = static_cast<int64_t>(v);
+  return P3M_OK;
+}
+
+p3m_status p3m_search_layout(const p3m_ctx* c, int32_t* rows, int32_t* xcells) {
+  if (!c || !rows || !xcells) return P3M_EINVAL;
+  *rows = c->g.rows;
+  *xcells = static_cast<int32_t>(std::lround(1.0 / c->g.cw[0]));
   return P3M_OK;
 }
 

@@ -39,7 +39,7 @@ struct Geom {
   int n[3];      // mesh nodes per axis
   int M[3];      // doubled mesh 2 n
   int nc[3];     // cells per axis
-  int rows;      // cell rows per cutoff length in y and z (1 or 2)
+  int rows;      // cell rows per cutoff length in y and z (1, 2 or 3)
   int order;     // 1 CIC, 2 TSC
   int pm_bc, pp_bc;
   int force_diff;  // 1: long-range force from central differences of the mesh potential

@@ -29,10 +29,10 @@ namespace {
 
 constexpr int kThreads = 128;
 
-// Row geometry for kRows cell rows per cutoff length in y and z (Geom::rows, 1 or 2): the
+// Row geometry for kRows cell rows per cutoff length in y and z (Geom::rows, 1, 2 or 3): the
 // neighbour rows of a particle's row are the (2 kRows + 1)^2 rows around it, numbered y fastest;
 // the particle's own row is number `first`, and the half shell walked by the short range is
-// rows first .. last - 1 (13 of 25 rows, or 5 of 9).
+// rows first .. last - 1 (5 of 9, 13 of 25 or 25 of 49 rows).
 template <int kRows>
 struct Rows {
   static constexpr int reach = kRows;
@@ -311,11 +311,30 @@ __device__ __forceinline__ void row_range(const Geom& g, const uint32_t* __restr
   j1 = starts[base + c1 + 1];
 }
 
+// b's own runs (particle ib in row row_b), for a lane whose two particles sit in different rows
+template <int kRows, typename Emit>
+__device__ __forceinline__ void b_runs(const Geom& g, const uint32_t* __restrict__ starts,
+                                       const float4& pb, const float4& lb, uint32_t ib,
+                                       Emit&& emit) {
+  constexpr int kFirst = Rows<kRows>::first, kLast = Rows<kRows>::last;  // half shell
+  const uint32_t row_b = __float_as_uint(lb.w) & kRowMask;
+  const int cyb = static_cast<int>(row_b % static_cast<uint32_t>(g.nc[1]));
+  const int czb = static_cast<int>(row_b / static_cast<uint32_t>(g.nc[1]));
+#pragma unroll 1
+  for (int r = kFirst; r < kLast; ++r) {
+    uint32_t j0, j1;
+    row_range<kRows>(g, starts, pb.x, pb.y, pb.z, cyb, czb, r, j0, j1);
+    j0 = max(j0, ib + 1);
+    if (j0 < j1) emit(j0, j1);
+  }
+}
+
 // The runs of the lane holding sorted particles a = ia and b = ia + 1 (b only if alive_b),
 // in walk order: emit(j0, j1) for each non-empty run. With a and b in one row (same) each run is
 // the hull of the two particles' runs in one neighbour row and is tested against both;
-// otherwise a's runs come first (split of them) and are tested against a only, then b's.
-template <int kRows, typename Emit>
+// otherwise a's runs come first (split of them) and are tested against a only, then b's
+// (unless kOnlyA: the caller then takes b's runs later, from b_runs).
+template <int kRows, bool kOnlyA = false, typename Emit>
 __device__ __forceinline__ void pair_runs(const Geom& g, const uint32_t* __restrict__ starts,
                                           const float4& pa, const float4& la, const float4& pb,
                                           const float4& lb, uint32_t ia, bool alive_b, bool& same,
@@ -348,17 +367,7 @@ __device__ __forceinline__ void pair_runs(const Geom& g, const uint32_t* __restr
     }
   }
   split = n;
-  if (!same) {
-    const int cyb = static_cast<int>(row_b % static_cast<uint32_t>(g.nc[1]));
-    const int czb = static_cast<int>(row_b / static_cast<uint32_t>(g.nc[1]));
-#pragma unroll 1
-    for (int r = kFirst; r < kLast; ++r) {
-      uint32_t j0, j1;
-      row_range<kRows>(g, starts, pb.x, pb.y, pb.z, cyb, czb, r, j0, j1);
-      j0 = max(j0, ib + 1);
-      if (j0 < j1) emit(j0, j1);
-    }
-  }
+  if (!kOnlyA && !same) b_runs<kRows>(g, starts, pb, lb, ib, emit);
 }
 
 template <int kDeg, int kRows>
@@ -369,8 +378,11 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
              uint32_t* __restrict__ next_tile,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
   constexpr uint32_t kTile = 2 * kThreads;  // particles per tile
-  // a's and b's runs: up to twice the half shell when their rows differ
-  constexpr int kPairRuns = 2 * Rows<kRows>::half;
+  // a's and b's runs: up to twice the half shell when their rows differ. With 3 rows per cutoff
+  // (25 half-shell rows) that would not fit beside 6 blocks per SM: a lane whose particles sit
+  // in different rows then walks a's runs first and b's after them, in the same slots (kPhased)
+  constexpr bool kPhased = kRows >= 3;
+  constexpr int kPairRuns = (kPhased ? 1 : 2) * Rows<kRows>::half;
   __shared__ uint32_t run_j0[kPairRuns][kThreads], run_j1[kPairRuns][kThreads];
   __shared__ uint32_t tile_s;
   const int tid = threadIdx.x;
@@ -394,24 +406,26 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     const float4 pa = rec[2 * ea], la = rec[2 * ea + 1];
     const float4 pb = rec[2 * eb], lb = rec[2 * eb + 1];
     // runs: with a and b in one row, the hull of their two runs per neighbour row (tested
-    // against both); otherwise a's runs [0, split) and b's runs [split, cnt)
+    // against both); otherwise a's runs [0, split) and b's runs [split, cnt) (kPhased: a's
+    // runs, then b's in their place once they are walked, while pending_b)
     int cnt = 0, split = 0;
     bool same = true;
+    auto emit = [&](uint32_t j0, uint32_t j1) {
+      run_j0[cnt][tid] = j0;
+      run_j1[cnt][tid] = j1;
+      ++cnt;
+    };
     if (alive_a)
-      pair_runs<kRows>(g, starts, pa, la, pb, lb, ia, alive_b, same, split,
-                       [&](uint32_t j0, uint32_t j1) {
-                  run_j0[cnt][tid] = j0;
-                  run_j1[cnt][tid] = j1;
-                  ++cnt;
-                });
+      pair_runs<kRows, kPhased>(g, starts, pa, la, pb, lb, ia, alive_b, same, split, emit);
+    bool pending_b = kPhased && alive_a && !same;
     uint32_t ptr = 0, end = 0;
     int k = 0;
     if (cnt > 0) {
       ptr = run_j0[0][tid];
       end = run_j1[0][tid];
     }
-    bool ta = same || split > 0;                  // the current run is tested against a
-    bool tb = alive_b && (same || split == 0);    // ... and against b
+    bool ta = same || split > 0;                               // the current run is tested against a
+    bool tb = alive_b && (same || (!kPhased && split == 0));   // ... and against b
     Acc2 sa[4], sb[4];
     for (int c = 0; c < 4; ++c) sa[c].hi = sa[c].lo = sb[c].hi = sb[c].lo = 0.f;
     float qa[4] = {0.f, 0.f, 0.f, 0.f}, qb[4] = {0.f, 0.f, 0.f, 0.f};
@@ -453,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
                       -(fay + fby), -(faz + fbz));
     };
     int step = 0;
-    while (__any_sync(0xffffffffu, ptr < end)) {
+    while (__any_sync(0xffffffffu, ptr < end || pending_b)) {
       // a lane without a candidate reads record 0, as every such lane does, so that the load
       // costs the warp one extra sector at most; its results are masked out
       const bool va = ptr < end, vb = ptr + 1 < end;
@@ -471,8 +485,26 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
         const uint32_t nj0 = run_j0[k][tid], nj1 = run_j1[k][tid];
         ptr = sw ? nj0 : ptr;
         end = sw ? nj1 : end;
-        ta = same || k < split;
-        tb = alive_b && (same || k >= split);
+        if constexpr (!kPhased) {
+          ta = same || k < split;
+          tb = alive_b && (same || k >= split);
+        }
+      }
+      if constexpr (kPhased) {
+        // a's runs walked (rare: a and b in different rows): b's runs take their slots
+        const bool go = pending_b && ptr >= end;
+        if (__any_sync(0xffffffffu, go)) {
+          if (go) {
+            cnt = 0;
+            b_runs<kRows>(g, starts, pb, lb, ib, emit);
+            k = 0;
+            pending_b = false;
+            ta = false;
+            tb = true;
+            ptr = cnt > 0 ? run_j0[0][tid] : 0u;
+            end = cnt > 0 ? run_j1[0][tid] : 0u;
+          }
+        }
       }
       if ((++step & 15) == 0) {
         for (int c = 0; c < 4; ++c) {
@@ -990,27 +1022,31 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
     const unsigned wblocks = static_cast<unsigned>(
         std::min<int64_t>(tiles, static_cast<int64_t>(kPpBlocksPerSm) * c->num_sms));
     // the kernel for the context's row geometry (Geom::rows cell rows per cutoff)
-    auto run = [&](auto k_rows1, auto k_rows2) {
-      auto kern = c->g.rows == 1 ? k_rows1 : k_rows2;
+    auto run = [&](auto k_rows1, auto k_rows2, auto k_rows3) {
+      auto kern = c->g.rows == 1 ? k_rows1 : (c->g.rows == 2 ? k_rows2 : k_rows3);
       kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
                                        c->starts, static_cast<float4*>(c->fpp), c->fplo, fbig,
                                        c->pp_tile, c->energy_acc, c->pair_acc);
     };
     switch (c->poly.deg) {
-      case 6: run(k_pp_f32<6, 1>, k_pp_f32<6, 2>); break;
-      case 7: run(k_pp_f32<7, 1>, k_pp_f32<7, 2>); break;
-      case 8: run(k_pp_f32<8, 1>, k_pp_f32<8, 2>); break;
-      case 9: run(k_pp_f32<9, 1>, k_pp_f32<9, 2>); break;
-      case 10: run(k_pp_f32<10, 1>, k_pp_f32<10, 2>); break;
-      case 11: run(k_pp_f32<11, 1>, k_pp_f32<11, 2>); break;
-      case 12: run(k_pp_f32<12, 1>, k_pp_f32<12, 2>); break;
-      case 13: run(k_pp_f32<13, 1>, k_pp_f32<13, 2>); break;
-      case 14: run(k_pp_f32<14, 1>, k_pp_f32<14, 2>); break;
-      default: run(k_pp_f32<15, 1>, k_pp_f32<15, 2>); break;
+      case 6: run(k_pp_f32<6, 1>, k_pp_f32<6, 2>, k_pp_f32<6, 3>); break;
+      case 7: run(k_pp_f32<7, 1>, k_pp_f32<7, 2>, k_pp_f32<7, 3>); break;
+      case 8: run(k_pp_f32<8, 1>, k_pp_f32<8, 2>, k_pp_f32<8, 3>); break;
+      case 9: run(k_pp_f32<9, 1>, k_pp_f32<9, 2>, k_pp_f32<9, 3>); break;
+      case 10: run(k_pp_f32<10, 1>, k_pp_f32<10, 2>, k_pp_f32<10, 3>); break;
+      case 11: run(k_pp_f32<11, 1>, k_pp_f32<11, 2>, k_pp_f32<11, 3>); break;
+      case 12: run(k_pp_f32<12, 1>, k_pp_f32<12, 2>, k_pp_f32<12, 3>); break;
+      case 13: run(k_pp_f32<13, 1>, k_pp_f32<13, 2>, k_pp_f32<13, 3>); break;
+      case 14: run(k_pp_f32<14, 1>, k_pp_f32<14, 2>, k_pp_f32<14, 3>); break;
+      default: run(k_pp_f32<15, 1>, k_pp_f32<15, 2>, k_pp_f32<15, 3>); break;
     }
   } else {
-    auto kern = c->det ? (c->g.rows == 1 ? k_pp_f64<1, true> : k_pp_f64<2, true>)
-                       : (c->g.rows == 1 ? k_pp_f64<1, false> : k_pp_f64<2, false>);
+    auto kern = c->det ? (c->g.rows == 1   ? k_pp_f64<1, true>
+                          : c->g.rows == 2 ? k_pp_f64<2, true>
+                                           : k_pp_f64<3, true>)
+                       : (c->g.rows == 1   ? k_pp_f64<1, false>
+                          : c->g.rows == 2 ? k_pp_f64<2, false>
+                                           : k_pp_f64<3, false>);
     if (!c->det) cudaMemsetAsync(c->fpp, 0, sizeof(D4) * static_cast<size_t>(n), s);
     kern<<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const Rec64*>(c->recp),
                                      static_cast<const Rec64*>(c->recm), c->starts,
@@ -1024,7 +1060,9 @@ void launch_pp_count(const p3m_ctx* c, int64_t n, unsigned long long* out, cudaS
   cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
   if (n == 0) return;
   const int64_t lane_pairs = (n + 1) / 2;
-  auto kern = c->g.rows == 1 ? k_pp_count_f32<1> : k_pp_count_f32<2>;
+  auto kern = c->g.rows == 1   ? k_pp_count_f32<1>
+              : c->g.rows == 2 ? k_pp_count_f32<2>
+                               : k_pp_count_f32<3>;
   kern<<<static_cast<unsigned>((lane_pairs + kThreads - 1) / kThreads), kThreads, 0, s>>>(
       c->g, c->starts + c->nkeys, static_cast<const float4*>(c->recp), c->starts, out);
 }
@@ -1042,23 +1080,23 @@ void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s)
     cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
     const unsigned wblocks = static_cast<unsigned>(
         std::min<int64_t>(blocks, static_cast<int64_t>(kVjpBlocksPerSm) * c->num_sms));
-    auto run = [&](auto k_rows1, auto k_rows2) {
-      auto kern = c->g.rows == 1 ? k_rows1 : k_rows2;
+    auto run = [&](auto k_rows1, auto k_rows2, auto k_rows3) {
+      auto kern = c->g.rows == 1 ? k_rows1 : (c->g.rows == 2 ? k_rows2 : k_rows3);
       kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total,
                                         static_cast<const float4*>(c->recp), c->starts, ws,
                                         static_cast<float4*>(c->fpp), c->pp_tile);
     };
     switch (c->poly.deg) {
-      case 6: run(k_pp_vjp_f32<6, 1>, k_pp_vjp_f32<6, 2>); break;
-      case 7: run(k_pp_vjp_f32<7, 1>, k_pp_vjp_f32<7, 2>); break;
-      case 8: run(k_pp_vjp_f32<8, 1>, k_pp_vjp_f32<8, 2>); break;
-      case 9: run(k_pp_vjp_f32<9, 1>, k_pp_vjp_f32<9, 2>); break;
-      case 10: run(k_pp_vjp_f32<10, 1>, k_pp_vjp_f32<10, 2>); break;
-      case 11: run(k_pp_vjp_f32<11, 1>, k_pp_vjp_f32<11, 2>); break;
-      case 12: run(k_pp_vjp_f32<12, 1>, k_pp_vjp_f32<12, 2>); break;
-      case 13: run(k_pp_vjp_f32<13, 1>, k_pp_vjp_f32<13, 2>); break;
-      case 14: run(k_pp_vjp_f32<14, 1>, k_pp_vjp_f32<14, 2>); break;
-      default: run(k_pp_vjp_f32<15, 1>, k_pp_vjp_f32<15, 2>); break;
+      case 6: run(k_pp_vjp_f32<6, 1>, k_pp_vjp_f32<6, 2>, k_pp_vjp_f32<6, 3>); break;
+      case 7: run(k_pp_vjp_f32<7, 1>, k_pp_vjp_f32<7, 2>, k_pp_vjp_f32<7, 3>); break;
+      case 8: run(k_pp_vjp_f32<8, 1>, k_pp_vjp_f32<8, 2>, k_pp_vjp_f32<8, 3>); break;
+      case 9: run(k_pp_vjp_f32<9, 1>, k_pp_vjp_f32<9, 2>, k_pp_vjp_f32<9, 3>); break;
+      case 10: run(k_pp_vjp_f32<10, 1>, k_pp_vjp_f32<10, 2>, k_pp_vjp_f32<10, 3>); break;
+      case 11: run(k_pp_vjp_f32<11, 1>, k_pp_vjp_f32<11, 2>, k_pp_vjp_f32<11, 3>); break;
+      case 12: run(k_pp_vjp_f32<12, 1>, k_pp_vjp_f32<12, 2>, k_pp_vjp_f32<12, 3>); break;
+      case 13: run(k_pp_vjp_f32<13, 1>, k_pp_vjp_f32<13, 2>, k_pp_vjp_f32<13, 3>); break;
+      case 14: run(k_pp_vjp_f32<14, 1>, k_pp_vjp_f32<14, 2>, k_pp_vjp_f32<14, 3>); break;
+      default: run(k_pp_vjp_f32<15, 1>, k_pp_vjp_f32<15, 2>, k_pp_vjp_f32<15, 3>); break;
     }
   } else {
     // d/dxi of (k_e q^2 / r_c^2) f(rho): one more factor 1/r_c

@@ -49,6 +49,8 @@ class CParams(ctypes.Structure):
         ("q", ctypes.c_double),
         ("mass", ctypes.c_double),
         ("force_diff", ctypes.c_int32),
+        ("search_rows", ctypes.c_int32),
+        ("search_xcells", ctypes.c_int32),
     ]
 
 
@@ -78,6 +80,7 @@ def lib():
             "p3m_forces": [P, P, I64, P, P],
             "p3m_pair_count": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
             "p3m_candidate_count": [P, ctypes.POINTER(I64)],
+            "p3m_search_layout": [P, ctypes.POINTER(I32), ctypes.POINTER(I32)],
             "p3m_push": [P, P, P, I64, D, I32, P, I32],
             "p3m_force_vjp": [P, P, I64, P, P],
             "p3m_backward": [P, P, P, I64, D, I32, P, P, P, P],
@@ -132,6 +135,8 @@ class Params:
     q: float = 1e-15
     mass: float = 1e-15 / 1.602176634e-19 * 9.1093837015e-31
     force_diff: int = 0  # 1 = central-difference mesh gradient (not the variational force)
+    search_rows: int = 0  # short-range cell rows per cutoff (1, 2, 3); 0 = chosen by the library
+    search_xcells: int = 0  # x cells per cutoff (1 .. 32, powers of 2); 0 = chosen
 
     def to_c(self) -> CParams:
         c = CParams()
@@ -244,6 +249,13 @@ class Context:
         self._bind()
         self._check(lib().p3m_candidate_count(self._h, ctypes.byref(a)), "p3m_candidate_count")
         return a.value
+
+    def search_layout(self):
+        """(cell rows per cutoff in y and z, x cells per cutoff) of the short-range search."""
+        r, c = ctypes.c_int32(), ctypes.c_int32()
+        self._check(lib().p3m_search_layout(self._h, ctypes.byref(r), ctypes.byref(c)),
+                    "p3m_search_layout")
+        return r.value, c.value
 
     def push(self, x, p, dt: float, nsteps: int, f=None):
         """In-place leapfrog; returns F(x_end) (p3m_push)."""

@@ -56,7 +56,12 @@ def test_create_refuses_bad_params_without_touching_the_device(lib):
     for bad in (dict(n=(4, 16, 16)), dict(assign_order=0), dict(h=(1e-5, -1.0, 1e-5)),
                 dict(precision=2), dict(q=0.0), dict(mass=0.0), dict(deterministic=2),
                 dict(deterministic=1, precision=p3m.FP32_MIXED),
-                dict(deterministic=1, pm_bc=2), dict(adj_slots=2, adj_segment=0)):
+                dict(deterministic=1, pm_bc=2), dict(adj_slots=2, adj_segment=0),
+                dict(search_rows=4), dict(search_rows=-1), dict(search_xcells=3),
+                dict(search_xcells=64),
+                # an explicit search layout over the cell budget (max(4 n_max, 2^20) cells)
+                dict(n=(512, 512, 512), search_rows=3, search_xcells=32),
+                dict(n=(512, 512, 512), search_xcells=32)):
         cp = p3m.Params(**bad).to_c()
         assert lib.p3m_create(ctypes.byref(cp), 10, None, ctypes.byref(h)) == p3m.P3M_EINVAL
         assert not h.value

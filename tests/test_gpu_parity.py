@@ -265,6 +265,76 @@ def test_short_range_wide_rows(precision, bc):
     assert rel(g, O.force_vjp(x, w, P)) <= (1e-11 if precision == 0 else 2e-5)
 
 
+LAYOUTS = [(1, 4), (2, 4), (2, 16), (3, 4), (3, 16), (3, 32)]
+
+
+@pytest.mark.parametrize("layout", LAYOUTS, ids=[f"rows{r}_x{c}" for r, c in LAYOUTS])
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("bc", [(0, 0), (1, 1)])
+def test_short_range_search_layouts(layout, precision, bc):
+    # every search layout (cell rows per cutoff in y and z, x cells per cutoff) gives the same
+    # pairs: a Gaussian bunch (open, or above the cathode with images), forces, pair counts,
+    # images and the force VJP against the oracle; and (FP32) a sparse set where most lanes'
+    # two particles sit in different cell rows, which with 3 rows walks b's runs after a's
+    rows, xcells = layout
+    pm_bc, pp_bc = bc
+    x = B.gaussian(3000, (0.4e-3, 0.5e-3, 0.6e-3), 71)
+    if pm_bc:
+        x = B.lift_to_plane(x, 0.0, 0.02e-3)
+    P = O.auto_mesh(x, 16, rc_over_h=2.0, pm_bc=pm_bc, pp_bc=pp_bc, z_cathode=0.0)
+    ref = O.forces(x, P)
+    ctx = p3m().Context(gpu_params(P, precision, search_rows=rows, search_xcells=xcells), len(x))
+    xg = cuda(x)
+    f = ctx.forces(xg)
+    npairs, nimg = ctx.pair_count()
+    ncand = ctx.candidate_count() if precision == 1 else None
+    w = np.random.default_rng(72).standard_normal(x.shape)
+    g = ctx.force_vjp(xg, cuda(w))
+    ctx.sync()
+    tol = TOL[precision]
+    assert ref.pairs > 100000 and (pp_bc == 0 or ref.image_pairs > 0)
+    assert rel(f, ref.F) <= tol
+    if precision == 0:
+        assert (npairs, nimg) == (ref.pairs, ref.image_pairs)
+    else:
+        assert abs(npairs - ref.pairs) <= 2 and abs(nimg - ref.image_pairs) <= 2
+        assert ref.pairs // 2 <= ncand
+    assert rel(g, O.force_vjp(x, w, P)) <= (1e-11 if precision == 0 else 2e-5)
+    ctx.close()
+    if precision == 1 and pm_bc == 0:
+        xs = np.random.default_rng(73).uniform(-1e-3, 1e-3, size=(301, 3))
+        Ps = O.auto_mesh(xs, 16, rc_over_h=1.0)
+        ctx = p3m().Context(gpu_params(Ps, 1, search_rows=rows, search_xcells=xcells), len(xs))
+        for xx in (xs, xs[:300]):
+            r = O.forces(xx, Ps)
+            f_pp = ctx.forces(cuda(xx), parts=1).cpu().numpy()
+            n_pp, _ = ctx.pair_count()
+            ctx.sync()
+            assert r.pairs > 0
+            assert np.linalg.norm(f_pp - r.F_pp) <= TOL[1] * np.linalg.norm(r.F_pp)
+            assert abs(n_pp - r.pairs) <= 2
+        ctx.close()
+
+
+def test_dense_bunch_picks_three_rows():
+    # the 1,048,576-particle Gaussian's context chooses the dense search layout by itself, and
+    # an explicit layout reproduces its pair count
+    m = p3m()
+    spec = dict(B.WORKLOADS["gauss1m"])
+    x = B.positions(spec)
+    P = O.auto_mesh(x, 64, rc_over_h=2.0)
+    xg = cuda(x)
+    counts = {}
+    for rows in (0, 2, 3):
+        ctx = m.Context(gpu_params(P, 0, search_rows=rows), len(x))
+        ctx.forces(xg, parts=1)
+        counts[rows] = ctx.pair_count()
+        if rows == 0:
+            assert ctx.search_layout()[0] == 3
+        ctx.close()
+    assert counts[0] == counts[2] == counts[3]
+
+
 def _box_case():
     # a bunch inside a grounded box of 20 x 24 x 28 nodes (h = 0.1 mm), supports off the faces
     x = B.gaussian(3000, (0.2e-3, 0.25e-3, 0.3e-3), 51)

@@ -1,6 +1,6 @@
 """The short-range search's cell geometry, checked on the host with the binning arithmetic the
 sort uses (FP32): particles closer than r_c must land in rows at most R apart (R = cell rows per
-cutoff, 1 or 2, rows (1 + 4 slack) r_c / R wide) and in an x-cell inside the run window the walk
+cutoff, 1, 2 or 3, rows (1 + 4 slack) r_c / R wide) and in an x-cell inside the run window the walk
 derives from the other particle's FP32 position. This is the argument that lets the walk visit
 only the (2R + 1)^2 row block around a particle's row (eq. (summation_short): the particles
 "close to" it), including at the largest extent the parameters allow (4092 cutoff lengths) and
@@ -46,7 +46,7 @@ def pairs_near_boundaries(rng, cw, ext, n):
     return xa, xa + d * RC
 
 
-@pytest.mark.parametrize("rows", [1, 2])
+@pytest.mark.parametrize("rows", [1, 2, 3])
 @pytest.mark.parametrize("ext", [10.0, 500.0, 4092.0])
 def test_close_particles_sit_at_most_rows_apart(rows, ext):
     rng = np.random.default_rng(int(ext) + rows)
@@ -61,7 +61,7 @@ def test_close_particles_sit_at_most_rows_apart(rows, ext):
     assert np.all(np.abs(sort_cell(xa, cw) - sort_cell(xb, cw)) <= rows)
 
 
-@pytest.mark.parametrize("nsub", [1, 2, 4])
+@pytest.mark.parametrize("nsub", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("ext", [10.0, 500.0, 4092.0])
 def test_partner_cell_inside_the_run_window(nsub, ext):
     rng = np.random.default_rng(int(ext) * 7 + nsub)
