@@ -219,13 +219,16 @@ __device__ __forceinline__ bool big_term(float a, float b, float c) {
 // set for terms below kBigTerm too (a cheaper test that never misses a big term).
 __device__ __forceinline__ void split_add_v4_if(bool p, bool big, float4* co, float4* fi,
                                                 float4* bg, float a, float b, float c) {
-  float ac, af, bc, bf, cc, cf;
-  split_q(a, ac, af);
-  split_q(b, bc, bf);
+  // x and y split on the two-wide FP32 instructions, z on the scalar ones (the same steps)
+  const float2 ab = make_float2(a, b);
+  const float2 abc = __fadd2_rn(__fadd2_rn(ab, make_float2(kSplitC, kSplitC)),
+                                make_float2(-kSplitC, -kSplitC));
+  const float2 abf = __fadd2_rn(ab, make_float2(-abc.x, -abc.y));
+  float cc, cf;
   split_q(c, cc, cf);
-  red_add_v4_if(p && !big, co, ac, bc, cc, 0.f);
-  red_add_v4_if(p && !big, fi, af, bf, cf, 0.f);
-  if (p && big) red_add_v4(bg, ac + af, bc + bf, cc + cf, 0.f);  // = (a, b, c) exactly; rare
+  red_add_v4_if(p && !big, co, abc.x, abc.y, cc, 0.f);
+  red_add_v4_if(p && !big, fi, abf.x, abf.y, cf, 0.f);
+  if (p && big) red_add_v4(bg, abc.x + abf.x, abc.y + abf.y, cc + cf, 0.f);  // (a, b, c); rare
 }
 // the same for a compensated sum hi + lo (lo far below hi): hi is split, lo joins the fine part
 __device__ __forceinline__ void split_add_v4(float4* co, float4* fi, float4* bg, float a, float b,
