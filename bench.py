@@ -38,11 +38,24 @@ FLOPS_PER_PAIR = 37.0  # algorithmic FP32 flops per in-cutoff pair (FFMA = 2, in
 KERNELS_PER_EVAL = 10  # bin, 3 scan passes, scatter, short range, deposit, fused z solve,
                        # interpolation, combination in the caller's order (cuFFT's kernels
                        # not counted)
-# DRAM bytes (read + write) of one k_pp_f32<12, 2> launch per particle, from an ncu capture of the
-# 2,097,152-particle sphere on a 128^3 mesh (123.9 MB per launch, profiles/k_pp_f32_sphere2m_128.md).
-# The kernel reads each 32-B record about once from DRAM (the neighbour runs and the reduction
-# targets stay in L2), so its traffic scales with the particle count at fixed density.
-PP_DRAM_BYTES_PER_PARTICLE = (110.694144e6 + 13.193984e6) / 2097152
+# DRAM bytes (read + write) of one k_pp_f32 launch, from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum), with the particle count captured and the limiter the capture showed:
+# the 2,097,152-particle sphere on a 128^3 mesh stands in for the 16M sphere (same density; the
+# kernel reads each 32-B record about once from DRAM and its reductions into the coarse, fine
+# and big result arrays miss L2 about once per particle, so its traffic scales with the
+# particle count); the 1M Gaussian is captured at full size. Workloads without a capture of the
+# current kernel report traffic null.
+PP_DRAM = {
+    "sphere16m": dict(bytes=144.48896e6 + 30.167808e6, particles=2097152,
+                      source="k_pp_f32<12, 2> on the 2,097,152-particle sphere (128^3), scaled "
+                             "by particle count",
+                      limiter="instruction issue 76%, L1 data pipe 71% (ncu, "
+                              "profiles/k_pp_f32_sphere2m_128.md)"),
+    "gauss1m": dict(bytes=80.014848e6 + 2.086656e6, particles=1048576,
+                    source="k_pp_f32<12, 3> on this workload (1,048,576 particles)",
+                    limiter="L1 data pipe 78%, L2 72% (vector reductions), issue 53% "
+                            "(ncu, profiles/k_pp_f32_gauss1m_64.md)"),
+}
 
 
 def parse():
@@ -377,6 +390,11 @@ def run_ours(a, rank, world, local_rank):
             "tflops": fl / (p0.elapsed_time(p1) / 1e3) / 1e12, "clocks": pclk.summary()}
     fp32_peak = max(v["tflops"] for v in probe.values())
     achieved = FLOPS_PER_PAIR * pairs / (pp_avg_ms / 1e3) / 1e12
+    # the capture stands for this launch only at the captured workload's default cutoff and layout
+    spec = B.WORKLOADS[a.workload]
+    cap = PP_DRAM.get(a.workload) if (a.rc == spec["rc_over_h"] and a.n == spec["n"]
+                                      and a.mesh == spec["mesh"] and a.rows == 0
+                                      and a.xcells == 0) else None
     result = {
         "metric": METRIC,
         "value": evals_per_s,
@@ -411,13 +429,10 @@ def run_ours(a, rank, world, local_rank):
             ["bin_sort", "short_range", "deposit", "solve", "interp_combine", "total"], t64))},
         "error": {"fp32_vs_fp64_gpu_rel_l2": err32},
         "roofline": {"bound": "alu", "kernel": "k_pp_f32 (short range)",
-                     "limiter": "instruction issue ~77%, L1 data pipe ~65% (ncu, "
-                                "profiles/k_pp_f32_sphere2m_128.md)", "achieved": achieved,
+                     "limiter": cap["limiter"] if cap else None, "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": PP_DRAM_BYTES_PER_PARTICLE * N,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
-                                       "k_pp_f32 on the 2,097,152-particle sphere (128^3), "
-                                       "scaled by particle count",
+                     "traffic": cap["bytes"] / cap["particles"] * N if cap else None,
+                     "traffic_source": cap["source"] if cap else "no capture of this workload",
                      "peak_source": "measured: FP32 multiply-add chain probe (p3m_fp32_probe), "
                                     "16 launches timed with CUDA events, the larger of scalar "
                                     "and packed",

@@ -139,7 +139,12 @@ p3m_status p3m_deposit(p3m_ctx* ctx, const double* x, int64_t n);
 p3m_status p3m_solve(p3m_ctx* ctx);
 
 /* Copies a mesh quantity to caller device memory `out` (float64, n_z*n_y*n_x, x fastest):
- * which = 0 node charges Q [C], which = 1 mesh potential phi [V]. ESTATE if not computed. */
+ * which = 0 node charges Q [C], which = 1 mesh potential phi [V]; which = 2, 3, 4 (FP32 path,
+ * after a p3m_forces call that included the long range) the forward differences of the mesh
+ * potential along x, y, z, D_d phi(g) = phi(g + e_d) - phi(g) [V], which the FP32 path convolves
+ * directly (difference kernels, eq. (phi_L)) and interpolates with the assignment function
+ * (eq. (eom_p3m_coord) by summation by parts); at g_d = n_d - 1 phi(g + e_d) is the open-boundary
+ * potential one node outside the mesh. ESTATE if not computed. */
 p3m_status p3m_get_mesh(p3m_ctx* ctx, int32_t which, double* out);
 
 /* One P3M force evaluation, eq. (eom_p3m_coord) right-hand side: f = F^S + F^L for the n

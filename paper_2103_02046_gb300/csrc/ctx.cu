@@ -368,6 +368,7 @@ p3m_status mesh_solve(p3m_ctx* c, bool want_phi, bool want_diff, bool want_energ
       if (cufftExecC2R(c->plan_xy_i, spec, real) != CUFFT_SUCCESS)
         return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
     }
+    c->diff_valid = true;
     return P3M_OK;
   }
   p3m_status s = fft_r2c(c);
@@ -388,6 +389,7 @@ p3m_status mesh_solve(p3m_ctx* c, bool want_phi, bool want_diff, bool want_energ
       if (fft_c2r(c, spec, real) != CUFFT_SUCCESS)
         return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
     }
+    c->diff_valid = true;
   }
   return P3M_OK;
 }
@@ -444,6 +446,7 @@ p3m_status vjp_impl(p3m_ctx* c, const double* x, int64_t n, const double* w, dou
   launch_vjp_gather(c, n, 1, w, out);
   c->deposited = false;  // the mesh now holds the dipole deposit
   c->phi_valid = false;
+  c->diff_valid = false;
   return P3M_OK;
 }
 
@@ -729,6 +732,7 @@ p3m_status p3m_deposit(p3m_ctx* c, const double* x, int64_t n) {
   launch_deposit(c, n);
   c->deposited = true;
   c->phi_valid = false;
+  c->diff_valid = false;
   return finish(c);
 }
 
@@ -744,9 +748,11 @@ p3m_status p3m_solve(p3m_ctx* c) {
 }
 
 p3m_status p3m_get_mesh(p3m_ctx* c, int32_t which, double* out) {
-  if (!c || !out || (which != 0 && which != 1)) return P3M_EINVAL;
+  if (!c || !out || which < 0 || which > 4) return P3M_EINVAL;
   if (which == 0 && !c->deposited) return fail(c, P3M_ESTATE, "no deposit");
   if (which == 1 && !c->phi_valid) return fail(c, P3M_ESTATE, "no potential (call p3m_solve)");
+  if (which >= 2 && !(c->fp32 && c->diff_valid))
+    return fail(c, P3M_ESTATE, "no difference fields (FP32 path, after p3m_forces)");
   enter(c);
   launch_get_mesh(c, which, out);
   return finish(c);

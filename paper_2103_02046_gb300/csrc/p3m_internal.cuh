@@ -310,6 +310,7 @@ struct p3m_ctx {
 
   // state
   bool deposited = false, solved = false, phi_valid = false;
+  bool diff_valid = false;  // FP32: freal holds the difference fields of the current deposit
   int64_t last_n = 0;
   int last_parts = 0;
   std::string last_error;

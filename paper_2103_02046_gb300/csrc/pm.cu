@@ -1047,7 +1047,10 @@ void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, d
 
 void launch_get_mesh(const p3m_ctx* c, int which, double* out) {
   const size_t total = static_cast<size_t>(c->g.n[0]) * c->g.n[1] * c->g.n[2];
-  const void* src = which == 0 ? c->qpad : c->phireal;
+  const void* src = which == 0   ? c->qpad
+                    : which == 1 ? c->phireal
+                                 : static_cast<const void*>(static_cast<const float*>(c->freal) +
+                                                            (which - 2) * c->n_real);
   const double scale = which == 0 ? c->g.q : 1.0;
   if (c->fp32)
     k_get_mesh<float><<<blocks_for(total), kThreads, 0, c->work>>>(

@@ -114,6 +114,34 @@ def test_mesh_charge_and_potential(precision):
     assert float(Qg.sum()) == pytest.approx(len(x) * P.q, rel=1e-12 if precision == 0 else 1e-6)
 
 
+DIFF_CASES = [("open_32_fused", 32, 0), ("cathode_20x24x64_fused", (20, 24, 64), 1),
+              ("cathode_16_cufft", 16, 1)]
+
+
+@pytest.mark.parametrize("case", DIFF_CASES, ids=[c[0] for c in DIFF_CASES])
+def test_fp32_difference_fields(case):
+    # the FP32 path's long range convolves the charge with forward-difference kernels (the fused
+    # z solve for a doubled z length of 64 or more, cuFFT and the Green's multiply otherwise):
+    # D_d phi(g) = phi(g + e_d) - phi(g) against the differences of the oracle's FP64 potential,
+    # on every node whose neighbour g + e_d is on the mesh
+    _, n, pm_bc = case
+    x = bunch_4k(pm_bc == 1)
+    P = O.auto_mesh(x, n, pm_bc=pm_bc, z_cathode=0.0)
+    phi = O.solve(O.deposit(x, P)[0], P)
+    ctx = p3m().Context(gpu_params(P, 1), len(x))
+    with pytest.raises(p3m().P3MError):
+        ctx.get_mesh(2)          # nothing computed yet
+    ctx.forces(cuda(x))
+    D = [ctx.get_mesh(2 + d).cpu().numpy() for d in range(3)]
+    ctx.sync()
+    ref = [phi[:, :, 1:] - phi[:, :, :-1], phi[:, 1:, :] - phi[:, :-1, :],
+           phi[1:, :, :] - phi[:-1, :, :]]
+    got = [D[0][:, :, :-1], D[1][:, :-1, :], D[2][:-1, :, :]]
+    for d in range(3):
+        assert rel(got[d], ref[d]) <= 1e-5, d
+    ctx.close()
+
+
 @pytest.mark.parametrize("order", [1, 2])
 def test_deposit_dense_clump(order):
     # 3072 coincident particles on one mesh node: a deposit block (1024 particles) puts its
@@ -708,5 +736,6 @@ def test_workload_gradient_4096_200_steps():
     ctx = p3m().Context(gpu_params(P, 0, adj_slots=10, adj_segment=20), len(x0))
     gx0, gp0 = ctx.backward(cuda(x0), cuda(p0), dt, T, cuda(gxT), cuda(gpT))
     ctx.sync()
+    print(f"gradient vs oracle: x0 {rel(gx0, ogx):.3e}, p0 {rel(gp0, ogp):.3e}")
     assert rel(gx0, ogx) <= 1e-9
     assert rel(gp0, ogp) <= 1e-9
