@@ -509,6 +509,10 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
           }
         }
       }
+      // the own sums: plain FP32 over at most 32 terms (16 steps of two records), then folded
+      // into the TwoSum accumulators; so the rounding of a particle's own sum is at most
+      // 31 * 2^-24 times the largest 32-term partial sum, per fold, instead of growing with the
+      // neighbour count
       if ((++step & 15) == 0) {
         for (int c = 0; c < 4; ++c) {
           sa[c].add(qa[c]);
