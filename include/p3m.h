@@ -180,10 +180,16 @@ p3m_status p3m_search_layout(const p3m_ctx* ctx, int32_t* rows, int32_t* xcells)
 /* Leapfrog, eq. (leapfrog) with the Stoermer form of eq. (eom_p3m_coord), as kick-drift-kick
  * (a reading: the paper leaves the start-up open):
  *   p += dt/2 F(x);  x += dt p / mass;  p += dt/2 F(x)   per step, nsteps >= 0 steps.
- * x, p: device [n][3] float64, updated in place. f: device [n][3] float64; on entry F(x0)
- * if f_valid != 0 (reused), else it is computed; on exit F(x_end). */
+ * x, p: device [n][3] float64, updated in place. f (nullable, device [n][3] float64): if given,
+ * it holds F(x0) on entry (reused, not recomputed) and F(x_end) on exit; if NULL, F(x0) is
+ * computed and the forces stay in the context's scratch. */
 p3m_status p3m_push(p3m_ctx* ctx, double* x, double* p, int64_t n, double dt, int32_t nsteps,
-                    double* f, int32_t f_valid);
+                    double* f);
+
+/* p3m_push with the entry force made optional: f (device [n][3] float64, required) holds F(x0)
+ * on entry if f_valid != 0, else F(x0) is computed into it; on exit it holds F(x_end). */
+p3m_status p3m_push_ex(p3m_ctx* ctx, double* x, double* p, int64_t n, double dt, int32_t nsteps,
+                       double* f, int32_t f_valid);
 
 /* Vector-Jacobian product of the force map: out = (dF/dx)^T w for positions x and cotangent
  * w (all device [n][3] float64). The long-range part uses the symmetry of the solve
@@ -192,12 +198,14 @@ p3m_status p3m_force_vjp(p3m_ctx* ctx, const double* x, int64_t n, const double*
 
 /* Reverse pass of p3m_push: given dJ/dx_T (gx_T) and dJ/dp_T (gp_T) for the state after
  * nsteps steps from (x0, p0), writes dJ/dx_0 (gx0) and dJ/dp_0 (gp0). States are
- * re-computed from checkpoints taken every adj_segment steps (needs
- * adj_slots * adj_segment >= nsteps). All arrays device [n][3] float64. ESTATE if the
- * context was created with adj_slots = 0; EINVAL if nsteps exceeds the checkpoint budget. */
+ * re-computed from checkpoints taken every ckpt_every steps (0 = adj_segment; at most
+ * adj_segment, the length of the segment buffer p3m_create sizes; needs
+ * adj_slots * ckpt_every >= nsteps). All arrays device [n][3] float64. ESTATE if the
+ * context was created with adj_slots = 0; EINVAL if ckpt_every is outside [0, adj_segment] or
+ * nsteps exceeds the checkpoint budget. */
 p3m_status p3m_backward(p3m_ctx* ctx, const double* x0, const double* p0, int64_t n, double dt,
-                        int32_t nsteps, const double* gx_T, const double* gp_T, double* gx0,
-                        double* gp0);
+                        int32_t nsteps, int32_t ckpt_every, const double* gx_T,
+                        const double* gp_T, double* gx0, double* gp0);
 
 /* Normalised rms emittance eps_u = sqrt(<du^2><dp_u^2> - <du dp_u>^2)/(mass c), u = x, y, z
  * (a reading: the paper names emittance but does not define it). eps3: device float64[3].

@@ -810,8 +810,8 @@ p3m_status p3m_search_layout(const p3m_ctx* c, int32_t* rows, int32_t* xcells) {
   return P3M_OK;
 }
 
-p3m_status p3m_push(p3m_ctx* c, double* x, double* p, int64_t n, double dt, int32_t nsteps,
-                    double* f, int32_t f_valid) {
+p3m_status p3m_push_ex(p3m_ctx* c, double* x, double* p, int64_t n, double dt, int32_t nsteps,
+                       double* f, int32_t f_valid) {
   if (!c) return P3M_EINVAL;
   if ((!x || !p || !f) && n > 0) return fail(c, P3M_EINVAL, "x, p or f is NULL");
   if (nsteps < 0 || !std::isfinite(dt)) return fail(c, P3M_EINVAL, "bad dt or nsteps");
@@ -821,6 +821,15 @@ p3m_status p3m_push(p3m_ctx* c, double* x, double* p, int64_t n, double dt, int3
   s = push_impl(c, x, p, n, dt, nsteps, f, f_valid != 0);
   if (s != P3M_OK) return s;
   return finish(c);
+}
+
+p3m_status p3m_push(p3m_ctx* c, double* x, double* p, int64_t n, double dt, int32_t nsteps,
+                    double* f) {
+  if (!c) return P3M_EINVAL;
+  // f given: it holds F(x0) and receives F(x_end); NULL: the forces live in the context's
+  // scratch (f_work, not otherwise in use during a push)
+  if (f) return p3m_push_ex(c, x, p, n, dt, nsteps, f, 1);
+  return p3m_push_ex(c, x, p, n, dt, nsteps, c->f_work, 0);
 }
 
 p3m_status p3m_force_vjp(p3m_ctx* c, const double* x, int64_t n, const double* w, double* out) {
@@ -837,17 +846,20 @@ p3m_status p3m_force_vjp(p3m_ctx* c, const double* x, int64_t n, const double* w
 }
 
 p3m_status p3m_backward(p3m_ctx* c, const double* x0, const double* p0, int64_t n, double dt,
-                        int32_t nsteps, const double* gx_T, const double* gp_T, double* gx0,
-                        double* gp0) {
+                        int32_t nsteps, int32_t ckpt_every, const double* gx_T,
+                        const double* gp_T, double* gx0, double* gp0) {
   if (!c) return P3M_EINVAL;
   if ((!x0 || !p0 || !gx_T || !gp_T || !gx0 || !gp0) && n > 0)
     return fail(c, P3M_EINVAL, "NULL argument");
   if (c->prm.adj_slots <= 0) return fail(c, P3M_ESTATE, "context created with adj_slots = 0");
   if (c->g.force_diff)
     return fail(c, P3M_ESTATE, "the adjoint needs the variational force (force_diff = 0)");
-  const int C = c->prm.adj_segment;
+  // checkpoints every ckpt_every steps (0: adj_segment); the segment buffer holds adj_segment
+  if (ckpt_every < 0 || ckpt_every > c->prm.adj_segment)
+    return fail(c, P3M_EINVAL, "ckpt_every must be in [0, adj_segment]");
+  const int C = ckpt_every > 0 ? ckpt_every : c->prm.adj_segment;
   if (nsteps < 1 || static_cast<int64_t>(c->prm.adj_slots) * C < nsteps || !std::isfinite(dt))
-    return fail(c, P3M_EINVAL, "nsteps must be in [1, adj_slots * adj_segment]");
+    return fail(c, P3M_EINVAL, "nsteps must be in [1, adj_slots * ckpt_every]");
   p3m_status s = take_deferred(c);
   if (s != P3M_OK) return s;
   if ((s = check_n(c, n)) != P3M_OK) return s;

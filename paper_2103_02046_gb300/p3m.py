@@ -81,9 +81,10 @@ def lib():
             "p3m_pair_count": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
             "p3m_candidate_count": [P, ctypes.POINTER(I64)],
             "p3m_search_layout": [P, ctypes.POINTER(I32), ctypes.POINTER(I32)],
-            "p3m_push": [P, P, P, I64, D, I32, P, I32],
+            "p3m_push": [P, P, P, I64, D, I32, P],
+            "p3m_push_ex": [P, P, P, I64, D, I32, P, I32],
             "p3m_force_vjp": [P, P, I64, P, P],
-            "p3m_backward": [P, P, P, I64, D, I32, P, P, P, P],
+            "p3m_backward": [P, P, P, I64, D, I32, I32, P, P, P, P],
             "p3m_emittance": [P, P, P, I64, P, P, P],
             "p3m_sync": [P],
             "p3m_get_timings": [P, ctypes.POINTER(D), I32, ctypes.POINTER(I32)],
@@ -258,14 +259,19 @@ class Context:
         return r.value, c.value
 
     def push(self, x, p, dt: float, nsteps: int, f=None):
-        """In-place leapfrog; returns F(x_end) (p3m_push)."""
+        """In-place leapfrog; returns F(x_end). With f = F(x0) given: p3m_push, which reuses it
+        and overwrites it with F(x_end); without: p3m_push_ex into a new tensor."""
         _vec3(x, "x")
         _vec3(p, "p")
-        valid = f is not None
-        f = torch.empty_like(x) if f is None else _vec3(f, "f")
         self._bind()
-        self._check(lib().p3m_push(self._h, _ptr(x), _ptr(p), x.shape[0], float(dt), int(nsteps),
-                                   _ptr(f), int(valid)), "p3m_push")
+        if f is not None:
+            _vec3(f, "f")
+            self._check(lib().p3m_push(self._h, _ptr(x), _ptr(p), x.shape[0], float(dt),
+                                       int(nsteps), _ptr(f)), "p3m_push")
+            return f
+        f = torch.empty_like(x)
+        self._check(lib().p3m_push_ex(self._h, _ptr(x), _ptr(p), x.shape[0], float(dt),
+                                      int(nsteps), _ptr(f), 0), "p3m_push_ex")
         return f
 
     def force_vjp(self, x, w):
@@ -277,15 +283,16 @@ class Context:
                     "p3m_force_vjp")
         return out
 
-    def backward(self, x0, p0, dt, nsteps, gxT, gpT):
+    def backward(self, x0, p0, dt, nsteps, gxT, gpT, ckpt_every: int = 0):
+        """Reverse pass (p3m_backward), checkpoints every ckpt_every steps (0 = adj_segment)."""
         for t, nm in ((x0, "x0"), (p0, "p0"), (gxT, "gxT"), (gpT, "gpT")):
             _vec3(t, nm)
         gx0 = torch.empty_like(x0)
         gp0 = torch.empty_like(p0)
         self._bind()
         self._check(lib().p3m_backward(self._h, _ptr(x0), _ptr(p0), x0.shape[0], float(dt),
-                                       int(nsteps), _ptr(gxT), _ptr(gpT), _ptr(gx0), _ptr(gp0)),
-                    "p3m_backward")
+                                       int(nsteps), int(ckpt_every), _ptr(gxT), _ptr(gpT),
+                                       _ptr(gx0), _ptr(gp0)), "p3m_backward")
         return gx0, gp0
 
     def emittance(self, x, p, grad: bool = False):

@@ -532,6 +532,15 @@ def test_push_parity(precision):
     assert rel(xg - cuda(x), xT - x) <= 10 * tol
     assert rel(pg, pT) <= 10 * tol
     assert rel(fg, fT) <= 10 * tol
+    # the C-ABI push with f = NULL: the forces stay in the context, the trajectory is the same
+    import ctypes
+    xn, pn = cuda(x), cuda(p)
+    st = p3m().lib().p3m_push(ctx._h, ctypes.c_void_p(xn.data_ptr()),
+                              ctypes.c_void_p(pn.data_ptr()), len(x), 1e-12, 10, None)
+    assert st == 0
+    ctx.sync()
+    assert rel(xn - cuda(x), xT - x) <= 10 * tol
+    assert rel(pn, pT) <= 10 * tol
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -595,12 +604,20 @@ def test_backward_parity(precision):
     xT, pT, _ = O.push(x0, p0, dt, T, P, force=lambda y: O.forces(y, P, kernels=kern).F)
     gxT, gpT = O.emittance_grad(xT, pT, P)
     ogx, ogp = O.backward(x0, p0, dt, T, gxT, gpT, P, kern)
-    ctx = p3m().Context(gpu_params(P, precision, adj_slots=3, adj_segment=3), len(x0))
-    gx0, gp0 = ctx.backward(cuda(x0), cuda(p0), dt, T, cuda(gxT), cuda(gpT))
-    ctx.sync()
+    ctx = p3m().Context(gpu_params(P, precision, adj_slots=4, adj_segment=3), len(x0))
     tol = 1e-10 if precision == 0 else 1e-4
-    assert rel(gx0, ogx) <= tol
-    assert rel(gp0, ogp) <= tol
+    # checkpoints every adj_segment (3) steps, and every 2 steps (ckpt_every of the call)
+    for every in (0, 2):
+        gx0, gp0 = ctx.backward(cuda(x0), cuda(p0), dt, T, cuda(gxT), cuda(gpT),
+                                ckpt_every=every)
+        ctx.sync()
+        assert rel(gx0, ogx) <= tol
+        assert rel(gp0, ogp) <= tol
+    # a checkpoint interval the segment buffer cannot hold, or too few slots for nsteps
+    for every, steps in ((4, T), (1, T)):
+        with pytest.raises(p3m().P3MError) as ei:
+            ctx.backward(cuda(x0), cuda(p0), dt, steps, cuda(gxT), cuda(gpT), ckpt_every=every)
+        assert ei.value.status == p3m().P3M_EINVAL
 
 
 def test_autograd_emittance_gradient():
@@ -619,7 +636,7 @@ def test_autograd_emittance_gradient():
     xT_o, pT_o, _ = O.push(x0, p0, dt, T, P, force=lambda y: O.forces(y, P, kernels=kern).F)
     gxT, gpT = O.emittance_grad(xT_o, pT_o, P)
     ogx, ogp = O.backward(x0, p0, dt, T, gxT, gpT, P, kern)
-    assert float(J) == pytest.approx(O.emittance(xT_o, pT_o, P).sum(), rel=1e-12)
+    assert float(J.detach()) == pytest.approx(O.emittance(xT_o, pT_o, P).sum(), rel=1e-12)
     assert rel(xg.grad, ogx) <= 1e-10
     assert rel(pg.grad, ogp) <= 1e-10
 
