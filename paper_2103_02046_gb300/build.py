@@ -34,7 +34,8 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "p3m_internal.cuh"), os.path.join(ROOT, "include", "p3m.h")]
+    deps = [src, os.path.join(CSRC, "p3m_internal.cuh"), os.path.join(CSRC, "df_math.cuh"),
+            os.path.join(ROOT, "include", "p3m.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

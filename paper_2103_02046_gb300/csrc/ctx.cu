@@ -8,11 +8,13 @@
 // The short range (ALU-bound, the longest stage) runs at high priority; the mesh chain fills
 // the SMs its blocks leave free, mostly in its tail.
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
 
+#include "df_math.cuh"
 #include "p3m_internal.cuh"
 
 using namespace p3m;
@@ -246,7 +248,7 @@ cudaError_t alloc(T** ptr, size_t count) {
 
 void free_all(p3m_ctx* c) {
   void* bufs[] = {c->counts, c->starts, c->bsum, c->keys, c->ranks, c->recp, c->recm, c->fpp,
-                  c->fplo,
+                  c->fplo, c->pdf,
                   c->acc, c->qpad, c->qhat, c->qhat2, c->khat_f, c->khat_i, c->fhat, c->freal,
                   c->phihat, c->phireal, c->dfac, c->ztw, c->box_real, c->box_spec, c->box_mult,
                   c->energy_acc, c->pair_acc,
@@ -604,6 +606,16 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
     A(alloc(&c->dred, 2 * 1024));
   }
   A(alloc(&c->f_work, 3 * n_max));
+  // FP64 path: the pair function in double-float arithmetic (kappa up to 6.5, where its relative
+  // error stays below about 2e-13; beyond, the FP64 pair function)
+  if (!c->fp32 && c->g.kappa_eff <= 6.5 && e == cudaSuccess) {
+    std::unique_ptr<dfm::PairDF> tab(new dfm::PairDF());  // filled on the host, then copied
+    if (dfm::fit_pair_df(c->g.kappa_eff, *tab)) {
+      A(alloc(&c->pdf, 1));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(c->pdf, tab.get(), sizeof(dfm::PairDF), cudaMemcpyHostToDevice);
+    }
+  }
   if (params->adj_slots > 0) {
     A(alloc(&c->ckpt, static_cast<size_t>(params->adj_slots) * 6 * n_max));
     A(alloc(&c->seg, static_cast<size_t>(params->adj_segment + 1) * 3 * n_max));

@@ -27,6 +27,10 @@
 
 #include "p3m.h"
 
+namespace dfm {
+struct PairDF;
+}
+
 namespace p3m {
 
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
@@ -227,6 +231,8 @@ struct p3m_ctx {
   p3m_params prm{};
   p3m::Geom g{};
   p3m::PairPoly poly{};
+  dfm::PairDF* pdf = nullptr;   // FP64 path: device copy of the double-float pair-function fit
+                                // (kappa <= 6.5; otherwise nullptr and the FP64 pair function)
   int64_t n_max = 0;
   int device = 0;
   bool fp32 = false;

@@ -21,7 +21,9 @@
 // small fraction of an addition per pair.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
+#include "df_math.cuh"
 #include "p3m_internal.cuh"
 
 namespace p3m {
@@ -789,6 +791,47 @@ __global__ void k_gather_w(const uint32_t* __restrict__ total, const float4* __r
 // ------------------------------------------------------------------------------------------
 constexpr int kRing64 = 4;
 
+// The FP64 path's pair function in double-float arithmetic (df_math.cuh): the fit table copied
+// into shared memory by the block (only the intervals and degrees in use), s = rho^2 split into
+// two floats with integer operations, the results widened exactly and summed in FP64.
+struct DFTable {
+  dfm::PairConsts k;
+  dfm::Coef coef[dfm::kMaxIntervals];
+};
+
+__device__ __forceinline__ void load_df_table(const dfm::PairDF* __restrict__ src, DFTable& dst) {
+  constexpr int kWords = sizeof(dfm::PairConsts) / sizeof(uint32_t);
+  static_assert(sizeof(dfm::PairConsts) % sizeof(uint32_t) == 0, "copied in words");
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(&src->k);
+  uint32_t* d = reinterpret_cast<uint32_t*>(&dst.k);
+  for (int t = threadIdx.x; t < kWords; t += blockDim.x) d[t] = s[t];
+  const int nint = src->k.nint, deg1 = src->k.deg + 1;
+  for (int t = threadIdx.x; t < nint * deg1; t += blockDim.x)
+    dst.coef[t / deg1][t % deg1] = src->coef[t / deg1][t % deg1];
+  __syncthreads();
+}
+
+__device__ __forceinline__ double df_to_double(dfm::F2 v) {
+  return float_to_double_exact(v.hi) + float_to_double_exact(v.lo);
+}
+
+__device__ __forceinline__ void pair_terms_df(const DFTable& T, double r2, double& fco,
+                                              double& pot) {
+  const DF sd = df_from_double(r2);
+  const dfm::PairOut o = dfm::pair_df(T.k, T.coef, dfm::F2{sd.hi, sd.lo});
+  fco = df_to_double(o.fco);
+  pot = df_to_double(o.pot);
+}
+
+__device__ __forceinline__ void pair_hess_dfd(const DFTable& T, double r2, double& fco,
+                                              double& dfr) {
+  const DF sd = df_from_double(r2);
+  dfm::F2 f, d;
+  dfm::pair_hess_df(T.k, T.coef, dfm::F2{sd.hi, sd.lo}, f, d);
+  fco = df_to_double(f);
+  dfr = df_to_double(d);
+}
+
 template <int kRows>
 __device__ __forceinline__ void row_range64(const Geom& g, const uint32_t* __restrict__ starts,
                                             double px, double py, double pz, int cy, int cz,
@@ -816,12 +859,14 @@ __device__ __forceinline__ void row_range64(const Geom& g, const uint32_t* __res
 // block, j != i), with no reductions: each particle's sum runs in the fixed sorted order and is
 // stored as is, together with its potential (w), from which the energy is summed in a fixed
 // order afterwards.
-template <int kRows, bool kDet>
+template <int kRows, bool kDet, bool kDF>
 __global__ void __launch_bounds__(kThreads)
     k_pp_f64(Geom g, const uint32_t* __restrict__ total, const Rec64* __restrict__ rec,
              const Rec64* __restrict__ recm, const uint32_t* __restrict__ starts,
              D4* __restrict__ fpp, double* __restrict__ energy,
-             unsigned long long* __restrict__ pairs) {
+             unsigned long long* __restrict__ pairs, const dfm::PairDF* __restrict__ dftab) {
+  __shared__ typename std::conditional<kDF, DFTable, char>::type dft_s[1];
+  if constexpr (kDF) load_df_table(dftab, dft_s[0]);
   __shared__ D4 ring_s[kThreads / 32][kRing64][32];
   __shared__ uint32_t ringj_s[kThreads / 32][kRing64][32];
   D4(*ring)[32] = ring_s[threadIdx.x >> 5];
@@ -850,7 +895,10 @@ __global__ void __launch_bounds__(kThreads)
     const uint32_t j = ringj[head & (kRing64 - 1)][lane];
     if (!has) e = D4{0.0, 0.0, 0.0, 0.5};
     double fco, pot;
-    pair_terms(e.w, kappa, c2k, fco, pot);
+    if constexpr (kDF)
+      pair_terms_df(dft_s[0], e.w, fco, pot);
+    else
+      pair_terms(e.w, kappa, c2k, fco, pot);
     if (has) {
       const double fx = fco * e.x, fy = fco * e.y, fz = fco * e.z;
       sum[0] += fx;
@@ -905,7 +953,10 @@ __global__ void __launch_bounds__(kThreads)
         const double r2 = ax * ax + ay * ay + az * az;
         if (r2 < 1.0 && r2 > 0.0) {
           double fco, pot;
-          pair_terms(r2, kappa, c2k, fco, pot);
+          if constexpr (kDF)
+            pair_terms_df(dft_s[0], r2, fco, pot);
+          else
+            pair_terms(r2, kappa, c2k, fco, pot);
           sum[0] -= fco * ax;
           sum[1] -= fco * ay;
           sum[2] -= fco * az;
@@ -951,12 +1002,21 @@ __device__ __forceinline__ void pair_hess(T r2, T kappa, T c2k, T& fco, T& dfr) 
 // FP64 vector-Jacobian product of the short-range force map (every ordered pair, one thread
 // per particle): acc_i = scale sum_j H(d_ij) (w_i - w_j) - scale sum_j H(d_ij') (w_i - S w_j)
 // over image pairs (pp_bc).
+template <bool kDF>
 __global__ void __launch_bounds__(kThreads)
     k_pp_vjp(Geom g, const uint32_t* __restrict__ total, PosD pos,
              const uint32_t* __restrict__ starts, const double* __restrict__ w,
-             double* __restrict__ acc, double scale) {
+             double* __restrict__ acc, double scale, const dfm::PairDF* __restrict__ dftab) {
+  __shared__ typename std::conditional<kDF, DFTable, char>::type dft_s[1];
+  if constexpr (kDF) load_df_table(dftab, dft_s[0]);
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *total) return;
+  auto hess = [&](double r2, double& fco, double& dfr) {
+    if constexpr (kDF)
+      pair_hess_dfd(dft_s[0], r2, fco, dfr);
+    else
+      pair_hess(r2, g.kappa_eff, 2.0 * g.kappa_eff * 0.56418958354775628695, fco, dfr);
+  };
   const double kappa = g.kappa_eff;
   const double c2k = 2.0 * g.kappa_eff * 0.56418958354775628695;
   const Rec64 me = pos.r[i];
@@ -972,7 +1032,7 @@ __global__ void __launch_bounds__(kThreads)
       const double r2 = rx * rx + ry * ry + rz * rz;
       if (r2 < 1.0 && r2 > 0.0) {
         double fco, dfr;
-        pair_hess(r2, kappa, c2k, fco, dfr);
+        hess(r2, fco, dfr);
         const double v0 = wi[0] - w[3 * rj.idx];
         const double v1 = wi[1] - w[3 * rj.idx + 1];
         const double v2 = wi[2] - w[3 * rj.idx + 2];
@@ -992,7 +1052,7 @@ __global__ void __launch_bounds__(kThreads)
         const double r2 = rx * rx + ry * ry + rz * rz;
         if (r2 < 1.0 && r2 > 0.0) {
           double fco, dfr;
-          pair_hess(r2, kappa, c2k, fco, dfr);
+          hess(r2, fco, dfr);
           const double v0 = wi[0] - w[3 * rj.idx];
           const double v1 = wi[1] - w[3 * rj.idx + 1];
           const double v2 = wi[2] + w[3 * rj.idx + 2];  // w_i - S w_j
@@ -1048,16 +1108,22 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
       default: run(k_pp_f32<15, 1>, k_pp_f32<15, 2>, k_pp_f32<15, 3>); break;
     }
   } else {
-    auto kern = c->det ? (c->g.rows == 1   ? k_pp_f64<1, true>
-                          : c->g.rows == 2 ? k_pp_f64<2, true>
-                                           : k_pp_f64<3, true>)
-                       : (c->g.rows == 1   ? k_pp_f64<1, false>
-                          : c->g.rows == 2 ? k_pp_f64<2, false>
-                                           : k_pp_f64<3, false>);
+    auto pick = [&](auto k1, auto k2, auto k3) {
+      return c->g.rows == 1 ? k1 : (c->g.rows == 2 ? k2 : k3);
+    };
+    auto kern = c->pdf ? (c->det ? pick(k_pp_f64<1, true, true>, k_pp_f64<2, true, true>,
+                                        k_pp_f64<3, true, true>)
+                                 : pick(k_pp_f64<1, false, true>, k_pp_f64<2, false, true>,
+                                        k_pp_f64<3, false, true>))
+                       : (c->det ? pick(k_pp_f64<1, true, false>, k_pp_f64<2, true, false>,
+                                        k_pp_f64<3, true, false>)
+                                 : pick(k_pp_f64<1, false, false>, k_pp_f64<2, false, false>,
+                                        k_pp_f64<3, false, false>));
     if (!c->det) cudaMemsetAsync(c->fpp, 0, sizeof(D4) * static_cast<size_t>(n), s);
     kern<<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const Rec64*>(c->recp),
                                      static_cast<const Rec64*>(c->recm), c->starts,
-                                     static_cast<D4*>(c->fpp), c->energy_acc, c->pair_acc);
+                                     static_cast<D4*>(c->fpp), c->energy_acc, c->pair_acc,
+                                     c->pdf);
     if (c->det) launch_det_sum_pp(c, n, s);
   }
 }
@@ -1108,8 +1174,9 @@ void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s)
   } else {
     // d/dxi of (k_e q^2 / r_c^2) f(rho): one more factor 1/r_c
     const double scale = c->g.ke * c->g.q * c->g.q / (c->g.rc * c->g.rc * c->g.rc);
-    k_pp_vjp<<<blocks, kThreads, 0, s>>>(
-        c->g, total, PosD{static_cast<const Rec64*>(c->recp)}, c->starts, w, c->acc, scale);
+    auto kern = c->pdf ? k_pp_vjp<true> : k_pp_vjp<false>;
+    kern<<<blocks, kThreads, 0, s>>>(c->g, total, PosD{static_cast<const Rec64*>(c->recp)},
+                                     c->starts, w, c->acc, scale, c->pdf);
   }
 }
 
