@@ -784,12 +784,15 @@ __global__ void k_gather_w(const uint32_t* __restrict__ total, const float4* __r
 // FP64 short range: each unordered pair once, as in the FP32 kernel: particle i takes the pairs
 // with j > i in sorted order (every one of the 25 neighbour rows is clipped to j > i, so this
 // holds however the row of i was rounded) and adds the reaction to j with FP64 reductions into
-// the zeroed result. Rows are walked in lockstep. The FP64 pair function (erfc, exp, division)
-// costs far more than finding a pair on this part, so pairs found wait in a per-lane ring in
-// shared memory and are evaluated, a batch of one per lane, whenever some lane's ring is full:
-// the pair function then runs with most lanes busy.
+// the zeroed result. Rows are walked in lockstep. FP64 arithmetic is scarce on this part, so the
+// walk itself runs in FP32: the row search and a distance prefilter on the leading 24 bits of
+// each coordinate (within the search slack of the exact test). Candidates that pass wait in a
+// per-lane ring in shared memory and are evaluated, a batch of one per lane, whenever some lane's
+// ring is full: the exact FP64 separation decides the pair (r^2 < 1 in FP64, as the definition
+// reads), and the pair terms follow (in double-float, or FP64 for large kappa), with most lanes
+// busy.
 // ------------------------------------------------------------------------------------------
-constexpr int kRing64 = 4;
+constexpr int kRingJ = 16;  // queued candidates per lane of the FP64 short range
 
 // The FP64 path's pair function in double-float arithmetic (df_math.cuh): the fit table copied
 // into shared memory by the block (only the intervals and degrees in use), s = rho^2 split into
@@ -867,9 +870,7 @@ __global__ void __launch_bounds__(kThreads)
              unsigned long long* __restrict__ pairs, const dfm::PairDF* __restrict__ dftab) {
   __shared__ typename std::conditional<kDF, DFTable, char>::type dft_s[1];
   if constexpr (kDF) load_df_table(dftab, dft_s[0]);
-  __shared__ D4 ring_s[kThreads / 32][kRing64][32];
-  __shared__ uint32_t ringj_s[kThreads / 32][kRing64][32];
-  D4(*ring)[32] = ring_s[threadIdx.x >> 5];
+  __shared__ uint32_t ringj_s[kThreads / 32][kRingJ][32];
   uint32_t(*ringj)[32] = ringj_s[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const uint32_t N = *total;
@@ -881,6 +882,11 @@ __global__ void __launch_bounds__(kThreads)
   const uint32_t ie = alive ? i : 0u;
   const Rec64 me = rec[ie];
   const double px = me.u[0], py = me.u[1], pz = me.u[2];
+  // FP32 copies (the leading 24 bits) for the search and the distance prefilter; the search
+  // slack exceeds their truncation error (2^-23 of the coordinate, twice, on each axis)
+  const float pxf = df_from_double(px).hi, pyf = df_from_double(py).hi,
+              pzf = df_from_double(pz).hi;
+  const float thr = (1.f + g.slack_f) * (1.f + g.slack_f);
   // the row the sort put the particle in (two particles closer than r_c sit in sort rows at most
   // kRows apart, whatever the rounding of either binning)
   const uint32_t row = static_cast<uint32_t>(static_cast<unsigned long long>(recm[ie].idx) >> 32);
@@ -889,22 +895,26 @@ __global__ void __launch_bounds__(kThreads)
   double sum[4] = {0.0, 0.0, 0.0, 0.0};
   unsigned int np = 0, ncand = 0;  // pairs found, records tested
   int head = 0, cnt = 0;
+  // one queued candidate per lane: the exact FP64 separation decides, then the pair terms
   auto evaluate = [&]() {
     const bool has = cnt > 0;
-    D4 e = ring[head & (kRing64 - 1)][lane];
-    const uint32_t j = ringj[head & (kRing64 - 1)][lane];
-    if (!has) e = D4{0.0, 0.0, 0.0, 0.5};
+    const uint32_t j = has ? ringj[head & (kRingJ - 1)][lane] : ie;
+    const Rec64 rj = rec[j];
+    const double rx = px - rj.u[0], ry = py - rj.u[1], rz = pz - rj.u[2];
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    const bool hit = has && r2 < 1.0 && r2 > 0.0;
     double fco, pot;
     if constexpr (kDF)
-      pair_terms_df(dft_s[0], e.w, fco, pot);
+      pair_terms_df(dft_s[0], hit ? r2 : 0.5, fco, pot);
     else
-      pair_terms(e.w, kappa, c2k, fco, pot);
-    if (has) {
-      const double fx = fco * e.x, fy = fco * e.y, fz = fco * e.z;
+      pair_terms(hit ? r2 : 0.5, kappa, c2k, fco, pot);
+    if (hit) {
+      const double fx = fco * rx, fy = fco * ry, fz = fco * rz;
       sum[0] += fx;
       sum[1] += fy;
       sum[2] += fz;
       sum[3] += pot;
+      ++np;
       if (!kDet) {
         double* fj = &fpp[j].x;
         // the potential is summed on the owner's side only: j's fourth component stays unused
@@ -919,7 +929,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int r = 0; r < Rows<kRows>::last; ++r) {
     uint32_t j0 = 0, j1 = 0;
     if (alive) {
-      row_range64<kRows>(g, starts, px, py, pz, cy, cz, r, j0, j1);
+      row_range<kRows>(g, starts, pxf, pyf, pzf, cy, cz, r, j0, j1);
       if (!kDet) j0 = max(j0, i + 1);
       j1 = max(j1, j0);
     }
@@ -928,17 +938,17 @@ __global__ void __launch_bounds__(kThreads)
     int maxlen = len;
     for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
     for (int t = 0; t < maxlen; ++t) {
-      const uint32_t j = t < len ? j0 + t : ie;  // an idle lane re-reads itself: no pair
+      const bool v = t < len;
+      const uint32_t j = v ? j0 + t : ie;
       const Rec64 rj = rec[j];
-      const double rx = px - rj.u[0], ry = py - rj.u[1], rz = pz - rj.u[2];
-      const double r2 = rx * rx + ry * ry + rz * rz;
-      if (alive && j != i && r2 < 1.0 && r2 > 0.0) {
-        ring[(head + cnt) & (kRing64 - 1)][lane] = D4{rx, ry, rz, r2};
-        ringj[(head + cnt) & (kRing64 - 1)][lane] = j;
+      const float dx = pxf - df_from_double(rj.u[0]).hi;
+      const float dy = pyf - df_from_double(rj.u[1]).hi;
+      const float dz = pzf - df_from_double(rj.u[2]).hi;
+      if (alive && v && j != i && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < thr) {
+        ringj[(head + cnt) & (kRingJ - 1)][lane] = j;
         ++cnt;
-        ++np;
       }
-      if (__any_sync(0xffffffffu, cnt == kRing64)) evaluate();
+      if (__any_sync(0xffffffffu, cnt == kRingJ)) evaluate();
     }
   }
   while (__any_sync(0xffffffffu, cnt > 0)) evaluate();
