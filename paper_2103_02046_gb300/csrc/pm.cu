@@ -608,18 +608,29 @@ __device__ __forceinline__ void grad_from_diff(const Geom& g, const float* __res
 // FP64: from the potential phi (volts), analytic derivative of W.
 __device__ __forceinline__ void grad_from_phi(const Geom& g, const double* __restrict__ phi,
                                               const Axis<double> ax[3], double G[3]) {
+  // G_x = sum_c w_c sum_b w_b sum_a phi dw_a, and likewise for y and z, summed axis by axis
+  // (sums along x per row, then along y per plane, then along z): about 90 FP64 operations per
+  // particle instead of 243 for the node-by-node triple products (FP64 units are scarce here)
   const int S = g.order == 2 ? 3 : 2;
   G[0] = G[1] = G[2] = 0.0;
-  for (int c = 0; c < S; ++c)
+  for (int c = 0; c < S; ++c) {
+    double ty = 0.0, tdy = 0.0, tdx = 0.0;  // sum_b of w_b sx, dw_b sx, w_b sdx
     for (int b = 0; b < S; ++b) {
       const double* row = phi + real_index(g, ax[0].c, ax[1].c + b, ax[2].c + c);
+      double sx = 0.0, sdx = 0.0;  // sum_a of phi w_a, phi dw_a
       for (int a = 0; a < S; ++a) {
         const double p = row[a];
-        G[0] += p * ax[0].dw[a] * ax[1].w[b] * ax[2].w[c];
-        G[1] += p * ax[0].w[a] * ax[1].dw[b] * ax[2].w[c];
-        G[2] += p * ax[0].w[a] * ax[1].w[b] * ax[2].dw[c];
+        sx = fma(p, ax[0].w[a], sx);
+        sdx = fma(p, ax[0].dw[a], sdx);
       }
+      ty = fma(ax[1].w[b], sx, ty);
+      tdy = fma(ax[1].dw[b], sx, tdy);
+      tdx = fma(ax[1].w[b], sdx, tdx);
     }
+    G[0] = fma(ax[2].w[c], tdx, G[0]);
+    G[1] = fma(ax[2].w[c], tdy, G[1]);
+    G[2] = fma(ax[2].dw[c], ty, G[2]);
+  }
 }
 
 // Central-difference field, interpolated with W (force_diff = 1): G_d = sum_g W (phi_{g+e_d} -
