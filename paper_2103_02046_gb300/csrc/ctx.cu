@@ -187,28 +187,42 @@ Geom make_geom(const p3m_params* p, int64_t n_max) {
   return g;
 }
 
-// Polynomial for the FP32 pair kernel: R(x) = erfc(x) e^{x^2} on [0, kappa] by Chebyshev
-// interpolation in t = 2x/kappa - 1, converted to monomials in t; the lowest degree whose erfc
-// error is below 2e-7 absolute is kept (a force error of the same relative size, since
-// erfc(x) <= 1 multiplies 1/rho^2 in the pair force).
+// Polynomial for the FP32 pair kernel: R(x) = erfc(x) e^{x^2} on [0, kappa] in the variable
+// t = 1 / (1 + p x) of Abramowitz & Stegun's form of erfc (7.1.26), p = 0.47, in which R is close
+// to t times a low-degree polynomial: R(x) = t P(u), u = t - t_c, t_c the midpoint of
+// [t_min, 1], t_min = 1 / (1 + p kappa) (the subtraction is exact where t and t_c are within a
+// factor 2 of each other, i.e. for kappa up to about 4). P is fitted by Chebyshev interpolation
+// at 96 nodes and converted to monomials in u. Evaluated as the kernel does in FP32, the erfc
+// error falls with the degree to a floor of about 2e-7 set by FP32 rounding; the lowest degree
+// whose error is below 2e-7 absolute, or within 30% of that floor, is kept (a force error of the
+// same relative size, since erfc(x) <= 1 multiplies 1/rho^2 in the pair force): degree 6 for
+// kappa = 3, where a polynomial in x itself needs degree 12.
 PairPoly fit_pair_poly(double kappa) {
   PairPoly pp{};
+  const double p = 0.47;
+  const double tmin = 1.0 / (1.0 + p * kappa);
   const int N = 96;
-  std::vector<double> tn(N), fn(N);
+  std::vector<double> un(N), fn(N);
   for (int j = 0; j < N; ++j) {
-    tn[j] = std::cos(kPi * (j + 0.5) / N);
-    const double x = 0.5 * (tn[j] + 1.0) * kappa;
-    fn[j] = std::erfc(x) * std::exp(x * x);
+    un[j] = std::cos(kPi * (j + 0.5) / N);
+    const double t = tmin + 0.5 * (un[j] + 1.0) * (1.0 - tmin);
+    const double x = (1.0 / t - 1.0) / p;
+    fn[j] = std::erfc(x) * std::exp(x * x) / t;
   }
-  for (int deg = 6; deg < kMaxPoly; ++deg) {
+  const double tc = 0.5 * (1.0 + tmin), hw = 0.5 * (1.0 - tmin);
+  pp.pk = static_cast<float>(p * kappa);
+  pp.tc = static_cast<float>(tc);
+  std::vector<std::vector<float>> coefs(kMaxPoly);
+  std::vector<double> errs(kMaxPoly, 1.0);
+  for (int deg = 4; deg < kMaxPoly; ++deg) {
     std::vector<double> ch(deg + 1);
     for (int k = 0; k <= deg; ++k) {
       double acc = 0.0;
-      for (int j = 0; j < N; ++j) acc += fn[j] * std::cos(k * std::acos(tn[j]));
+      for (int j = 0; j < N; ++j) acc += fn[j] * std::cos(k * std::acos(un[j]));
       ch[k] = acc * 2.0 / N;
     }
     ch[0] *= 0.5;
-    // Chebyshev -> monomial: T_0 = 1, T_1 = t, T_{k+1} = 2 t T_k - T_{k-1}
+    // Chebyshev -> monomial in v = (t - t_c) / hw: T_0 = 1, T_1 = v, T_{k+1} = 2 v T_k - T_{k-1}
     std::vector<double> mono(deg + 1, 0.0), tkm1(deg + 1, 0.0), tk(deg + 1, 0.0), tkp1(deg + 1);
     tkm1[0] = 1.0;
     tk[1] = 1.0;
@@ -220,19 +234,32 @@ PairPoly fit_pair_poly(double kappa) {
       tkm1 = tk;
       tk = tkp1;
     }
+    // then in u = t - t_c: coefficient m scaled by hw^-m
+    coefs[deg].resize(deg + 1);
+    for (int m = 0; m <= deg; ++m) coefs[deg][m] = static_cast<float>(mono[m] / std::pow(hw, m));
     double err = 0.0;
-    for (int q = 0; q <= 2000; ++q) {
-      const double x = kappa * q / 2000.0;
-      const float t = static_cast<float>(2.0 * x / kappa - 1.0);
-      float r = static_cast<float>(mono[deg]);
-      for (int m = deg - 1; m >= 0; --m) r = std::fma(r, t, static_cast<float>(mono[m]));
+    for (int q = 0; q <= 4000; ++q) {
+      const double x = kappa * q / 4000.0;
+      const float rho = static_cast<float>(x / kappa);
+      const float t = 1.0f / std::fma(pp.pk, rho, 1.0f);
+      const float u = t - pp.tc;
+      float r = coefs[deg][deg];
+      for (int m = deg - 1; m >= 0; --m) r = std::fma(r, u, coefs[deg][m]);
+      r *= t;
       err = std::max(err, std::fabs(static_cast<double>(r) * std::exp(-x * x) - std::erfc(x)));
     }
-    pp.deg = deg;
-    for (int m = 0; m <= deg; ++m) pp.c[m] = static_cast<float>(mono[m]);
-    pp.max_abs_err = static_cast<float>(err);
-    if (err < 2e-7) break;
+    errs[deg] = err;
   }
+  const double floor_err = *std::min_element(errs.begin() + 4, errs.end());
+  int deg = kMaxPoly - 1;
+  for (int d = 4; d < kMaxPoly; ++d)
+    if (errs[d] < 2e-7 || errs[d] <= 1.3 * floor_err) {
+      deg = d;
+      break;
+    }
+  pp.deg = deg;
+  for (int m = 0; m <= deg; ++m) pp.c[m] = coefs[deg][m];
+  pp.max_abs_err = static_cast<float>(errs[deg]);
   pp.kappa2_log2e = static_cast<float>(kappa * kappa * 1.4426950408889634);
   pp.kappa2 = static_cast<float>(kappa * kappa);
   pp.c2k = static_cast<float>(2.0 * kappa / std::sqrt(kPi));

@@ -158,12 +158,13 @@ __device__ __forceinline__ DF df_from_double(double v) {
   return DF{__uint_as_float(hb), lo};
 }
 
-// FP32 pair kernel: erfc(x) e^{x^2} on x in [0, kappa_eff] as a polynomial in t = 2 x /
-// kappa_eff - 1 (Horner, highest degree first), fitted at context creation.
+// FP32 pair kernel: erfc(x) e^{x^2} on x in [0, kappa_eff] as t P(u), t = 1 / (1 + pk rho),
+// u = t - tc, P a polynomial (Horner, highest degree first), fitted at context creation.
 constexpr int kMaxPoly = 16;
 struct PairPoly {
   int deg;
   float c[kMaxPoly];
+  float pk, tc;        // p kappa_eff; the midpoint of t's range
   float kappa2_log2e;  // kappa_eff^2 log2(e): e^{-kappa^2 rho^2} = 2^{-kappa2_log2e rho^2}
   float kappa2;        // kappa_eff^2
   float c2k;           // 2 kappa_eff / sqrt(pi)

@@ -156,9 +156,10 @@ struct PosD {
 // candidates per step some lane nearly always holds a pair. Separations are exact to FP32
 // relative rounding ((hi_i - hi_j) + (lo_i - lo_j)). FP32 partial sums are folded into a
 // two-float (TwoSum) accumulator every 16 steps.
-// The pair function uses one ex2 for both e^{-kappa^2 rho^2} terms and the fitted polynomial
-// R(x) = erfc(x) e^{x^2}: erfc(kappa rho) = R * e^{-kappa^2 rho^2}; rsqrt and ex2 are the
-// hardware approximations (flush-to-zero: every argument here is a normal number).
+// The pair function uses one ex2 for both e^{-kappa^2 rho^2} terms and the fitted form
+// R(x) = erfc(x) e^{x^2} = t P(u), t = 1 / (1 + p x): erfc(kappa rho) = R * e^{-kappa^2 rho^2};
+// rsqrt, rcp and ex2 are the hardware approximations (flush-to-zero: every argument here is a
+// normal number).
 // ------------------------------------------------------------------------------------------
 constexpr int kPpBlocksPerSm = 6;    // resident blocks per SM of the short range (80 registers)
 constexpr int kVjpBlocksPerSm = 10;  // resident blocks per SM of its adjoint (48 registers)
@@ -260,16 +261,30 @@ __device__ __forceinline__ float ex2_ftz(float x) {
   return y;
 }
 
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// R(x) = erfc(x) e^{x^2}, x = kappa rho, as t P(u): t = 1 / (1 + p kappa rho), u = t - t_c
+template <int kDeg, bool kHw>
+__device__ __forceinline__ float erfcx_poly(const PairPoly& P, float rho) {
+  const float t = kHw ? rcp_ftz(fmaf(P.pk, rho, 1.f)) : 1.f / fmaf(P.pk, rho, 1.f);
+  const float u = t - P.tc;
+  float R = P.c[kDeg];
+#pragma unroll
+  for (int m = kDeg - 1; m >= 0; --m) R = fmaf(R, u, P.c[m]);
+  return R * t;
+}
+
 // pair_poly on the hardware approximations; r2 in (0, 1]
 template <int kDeg>
 __device__ __forceinline__ void pair_poly_hw(const PairPoly& P, float r2, float& fco,
                                              float& pot) {
   const float rinv = rsqrt_ftz(r2);
   const float rho = r2 * rinv;
-  const float t = fmaf(2.f, rho, -1.f);
-  float R = P.c[kDeg];
-#pragma unroll
-  for (int m = kDeg - 1; m >= 0; --m) R = fmaf(R, t, P.c[m]);
+  const float R = erfcx_poly<kDeg, true>(P, rho);
   const float ex = ex2_ftz(-P.kappa2_log2e * r2);
   pot = R * ex * rinv;
   fco = fmaf(P.c2k, ex, pot) * (rinv * rinv);
@@ -279,10 +294,7 @@ template <int kDeg>
 __device__ __forceinline__ void pair_poly(const PairPoly& P, float r2, float& fco, float& pot) {
   const float rinv = rsqrtf(r2);
   const float rho = r2 * rinv;
-  const float t = fmaf(2.f, rho, -1.f);
-  float R = P.c[kDeg];
-#pragma unroll
-  for (int m = kDeg - 1; m >= 0; --m) R = fmaf(R, t, P.c[m]);
+  const float R = erfcx_poly<kDeg, false>(P, rho);
   const float ex = exp2f(-P.kappa2_log2e * r2);
   pot = R * ex * rinv;
   fco = fmaf(P.c2k, ex, pot) * (rinv * rinv);
@@ -624,10 +636,7 @@ __device__ __forceinline__ void pair_hess_poly(const PairPoly& P, float r2, floa
                                                float& dfr) {
   const float rinv = rsqrtf(r2);
   const float rho = r2 * rinv;
-  const float t = fmaf(2.f, rho, -1.f);
-  float R = P.c[kDeg];
-#pragma unroll
-  for (int m = kDeg - 1; m >= 0; --m) R = fmaf(R, t, P.c[m]);
+  const float R = erfcx_poly<kDeg, false>(P, rho);
   const float ex = exp2f(-P.kappa2_log2e * r2);
   const float pot = R * ex * rinv;           // erfc(kappa rho) / rho
   const float cex = P.c2k * ex;
@@ -1106,6 +1115,8 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
                                        c->pp_tile, c->energy_acc, c->pair_acc);
     };
     switch (c->poly.deg) {
+      case 4: run(k_pp_f32<4, 1>, k_pp_f32<4, 2>, k_pp_f32<4, 3>); break;
+      case 5: run(k_pp_f32<5, 1>, k_pp_f32<5, 2>, k_pp_f32<5, 3>); break;
       case 6: run(k_pp_f32<6, 1>, k_pp_f32<6, 2>, k_pp_f32<6, 3>); break;
       case 7: run(k_pp_f32<7, 1>, k_pp_f32<7, 2>, k_pp_f32<7, 3>); break;
       case 8: run(k_pp_f32<8, 1>, k_pp_f32<8, 2>, k_pp_f32<8, 3>); break;
@@ -1170,6 +1181,8 @@ void launch_pp_vjp(const p3m_ctx* c, int64_t n, const double* w, cudaStream_t s)
                                         static_cast<float4*>(c->fpp), c->pp_tile);
     };
     switch (c->poly.deg) {
+      case 4: run(k_pp_vjp_f32<4, 1>, k_pp_vjp_f32<4, 2>, k_pp_vjp_f32<4, 3>); break;
+      case 5: run(k_pp_vjp_f32<5, 1>, k_pp_vjp_f32<5, 2>, k_pp_vjp_f32<5, 3>); break;
       case 6: run(k_pp_vjp_f32<6, 1>, k_pp_vjp_f32<6, 2>, k_pp_vjp_f32<6, 3>); break;
       case 7: run(k_pp_vjp_f32<7, 1>, k_pp_vjp_f32<7, 2>, k_pp_vjp_f32<7, 3>); break;
       case 8: run(k_pp_vjp_f32<8, 1>, k_pp_vjp_f32<8, 2>, k_pp_vjp_f32<8, 3>); break;
