@@ -46,14 +46,14 @@ KERNELS_PER_EVAL = 10  # bin, 3 scan passes, scatter, short range, deposit, fuse
 # particle count); the 1M Gaussian is captured at full size. Workloads without a capture of the
 # current kernel report traffic null.
 PP_DRAM = {
-    "sphere16m": dict(bytes=144.48896e6 + 30.167808e6, particles=2097152,
-                      source="k_pp_f32<12, 2> on the 2,097,152-particle sphere (128^3), scaled "
+    "sphere16m": dict(bytes=144.439552e6 + 30.444544e6, particles=2097152,
+                      source="k_pp_f32<6, 2> on the 2,097,152-particle sphere (128^3), scaled "
                              "by particle count",
-                      limiter="instruction issue 76%, L1 data pipe 71% (ncu, "
+                      limiter="instruction issue 75%, L1 data pipe 72% (ncu, "
                               "profiles/k_pp_f32_sphere2m_128.md)"),
-    "gauss1m": dict(bytes=80.014848e6 + 2.086656e6, particles=1048576,
-                    source="k_pp_f32<12, 3> on this workload (1,048,576 particles)",
-                    limiter="L1 data pipe 78%, L2 72% (vector reductions), issue 53% "
+    "gauss1m": dict(bytes=79.892736e6 + 1.780224e6, particles=1048576,
+                    source="k_pp_f32<6, 3> on this workload (1,048,576 particles)",
+                    limiter="L1 data pipe 79%, L2 73% (vector reductions), issue 51% "
                             "(ncu, profiles/k_pp_f32_gauss1m_64.md)"),
 }
 
