@@ -98,6 +98,34 @@ def test_forces_parity(case, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("kappa", [1.5, 6.0, 7.0])
+def test_short_range_kappa(kappa, precision):
+    # the pair function's fits depend on kappa = alpha r_c: the FP64 path evaluates it in
+    # double-float arithmetic up to kappa = 6.5 (intervals of erfc(x) e^{x^2}, an exact ln2/16
+    # reduction of e^{-x^2}) and in FP64 above; the FP32 path fits t P(t - t_c),
+    # t = 1/(1 + 0.47 x), to its FP32 floor for any kappa. Forces, energy, pair count and the
+    # force VJP (the Hessian terms) against the oracle, with images (pp_bc = 1) above a cathode.
+    x = bunch_4k(True)
+    P = O.auto_mesh(x, 16, rc_over_h=2.0, kappa=kappa, pm_bc=1, pp_bc=1, z_cathode=0.0)
+    ref = O.forces(x, P, parts=1)
+    ctx = p3m().Context(gpu_params(P, precision), len(x))
+    xg = cuda(x)
+    f, e = ctx.forces(xg, energy=True, parts=1)
+    npairs, nimg = ctx.pair_count()
+    w = np.random.default_rng(31).standard_normal(x.shape)
+    g = ctx.force_vjp(xg, cuda(w))
+    ctx.sync()
+    tol = TOL[precision]
+    assert rel(f, ref.F_pp) <= tol
+    assert e.cpu().numpy()[0] == pytest.approx(ref.U_pp, rel=10 * tol)
+    if precision == 0:
+        assert (npairs, nimg) == (ref.pairs, ref.image_pairs)
+        assert rel(g, O.force_vjp(x, w, P)) <= 1e-11
+    else:
+        assert rel(g, O.force_vjp(x, w, P)) <= 2e-5
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_mesh_charge_and_potential(precision):
     x = bunch_4k(True)
     P = O.auto_mesh(x, 16, pm_bc=1, z_cathode=0.0)
