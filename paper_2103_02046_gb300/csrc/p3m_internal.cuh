@@ -255,9 +255,10 @@ struct p3m_ctx {
   void* recp = nullptr;         // [n_max] sorted positions, cutoff units (2 float4 / Rec64)
   void* recm = nullptr;         // [n_max] FP64 path: sorted assignment records (Rec64)
   void* fpp = nullptr;          // [n_max] short-range result, sorted (FP32 float4, FP64 D4)
-  float4* fplo = nullptr;       // [2 n_max] FP32 path: the fine parts of the short-range terms,
-                                // then (from n_max on) the rare big terms; fpp holds the coarse
-                                // parts (summed exactly)
+  float4* fplo = nullptr;       // [2 n_max] FP32 path: the fine x and y parts of the
+                                // short-range terms (float2 [n]), then (from n_max on) the rare
+                                // big terms; fpp holds the coarse x, y, z parts (summed exactly)
+                                // and the fine z part
   double* acc = nullptr;        // [3 n_max] adjoint accumulator, sorted order
 
   // mesh

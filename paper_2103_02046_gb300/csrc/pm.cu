@@ -694,11 +694,13 @@ __global__ void k_interp(Geom g, const uint32_t* __restrict__ total,
     }
     float4* out = reinterpret_cast<float4*>(fpp) + i;
     if (parts & 1) {
-      // the short range: its coarse, fine and big parts
-      const float4 s = *out, l = fplo[i], b = fbig[i];
+      // the short range: coarse x, y, z with the fine z part (float4), fine x and y (float2),
+      // big terms (float4)
+      const float4 s = *out, b = fbig[i];
+      const float2 l = reinterpret_cast<const float2*>(fplo)[i];
       F[0] = fmaf(pp_scale_f, (s.x + l.x) + b.x, F[0]);
       F[1] = fmaf(pp_scale_f, (s.y + l.y) + b.y, F[1]);
-      F[2] = fmaf(pp_scale_f, (s.z + l.z) + b.z, F[2]);
+      F[2] = fmaf(pp_scale_f, (s.z + s.w) + b.z, F[2]);
     }
     *out = make_float4(F[0], F[1], F[2], 0.f);
   } else {

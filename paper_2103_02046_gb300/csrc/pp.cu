@@ -215,12 +215,24 @@ __device__ __forceinline__ bool big_term(float a, float b, float c) {
   return fmaf(a, a, fmaf(b, b, c * c)) >= kBigTerm * kBigTerm;
 }
 
-// One particle's short-range force held as three float4 arrays: coarse (co) + fine (fi) + big
-// (bg). Each added term is split, its coarse part reduced into co and its fine part into fi, or,
-// if it is big, reduced whole into bg. The result is the exact sum up to the rounding of the
-// fine sums, whose terms are at most kSplitQ / 2, and of the (rare) big terms. `big` may be
-// set for terms below kBigTerm too (a cheaper test that never misses a big term).
-__device__ __forceinline__ void split_add_v4_if(bool p, bool big, float4* co, float4* fi,
+// 2-wide reduction (the fine x and y parts)
+__device__ __forceinline__ void red_add_v2_if(bool p, float2* dst, float a, float b) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t"
+      "@q red.global.add.v2.f32 [%0], {%1, %2};\n\t}" ::"l"(dst),
+      "f"(a), "f"(b), "r"(static_cast<int>(p))
+      : "memory");
+}
+
+// One particle's short-range force held in three arrays: co (float4: the coarse x, y, z parts and
+// the fine z part), fi (float2: the fine x and y parts) and bg (float4: big terms). Each added
+// term is split; the coarse parts and the fine z part go out in one 4-wide reduction into co, the
+// fine x and y parts in one 2-wide reduction into fi (24 bytes a term; the fourth coarse slot
+// would otherwise carry a zero), or, if the term is big, it is reduced whole into bg. The result
+// is the exact sum up to the rounding of the fine sums, whose terms are at most kSplitQ / 2, and
+// of the (rare) big terms. `big` may be set for terms below kBigTerm too (a cheaper test that
+// never misses a big term).
+__device__ __forceinline__ void split_add_v4_if(bool p, bool big, float4* co, float2* fi,
                                                 float4* bg, float a, float b, float c) {
   // x and y split on the two-wide FP32 instructions, z on the scalar ones (the same steps)
   const float2 ab = make_float2(a, b);
@@ -229,24 +241,25 @@ __device__ __forceinline__ void split_add_v4_if(bool p, bool big, float4* co, fl
   const float2 abf = __fadd2_rn(ab, make_float2(-abc.x, -abc.y));
   float cc, cf;
   split_q(c, cc, cf);
-  red_add_v4_if(p && !big, co, abc.x, abc.y, cc, 0.f);
-  red_add_v4_if(p && !big, fi, abf.x, abf.y, cf, 0.f);
+  red_add_v4_if(p && !big, co, abc.x, abc.y, cc, cf);
+  red_add_v2_if(p && !big, fi, abf.x, abf.y);
   if (p && big) red_add_v4(bg, abc.x + abf.x, abc.y + abf.y, cc + cf, 0.f);  // (a, b, c); rare
 }
 // the same for a compensated sum hi + lo (lo far below hi): hi is split, lo joins the fine part
-__device__ __forceinline__ void split_add_v4(float4* co, float4* fi, float4* bg, float a, float b,
+__device__ __forceinline__ void split_add_v4(float4* co, float2* fi, float4* bg, float a, float b,
                                              float c, float la, float lb, float lc) {
   if (big_term(a, b, c)) {
     red_add_v4(bg, a, b, c, 0.f);
-    red_add_v4(fi, la, lb, lc, 0.f);
+    red_add_v4(co, 0.f, 0.f, 0.f, lc);
+    red_add_v2_if(true, fi, la, lb);
     return;
   }
   float ac, af, bc, bf, cc, cf;
   split_q(a, ac, af);
   split_q(b, bc, bf);
   split_q(c, cc, cf);
-  red_add_v4(co, ac, bc, cc, 0.f);
-  red_add_v4(fi, __fadd_rn(af, la), __fadd_rn(bf, lb), __fadd_rn(cf, lc), 0.f);
+  red_add_v4(co, ac, bc, cc, __fadd_rn(cf, lc));
+  red_add_v2_if(true, fi, __fadd_rn(af, la), __fadd_rn(bf, lb));
 }
 
 __device__ __forceinline__ float rsqrt_ftz(float x) {
@@ -391,7 +404,7 @@ template <int kDeg, int kRows>
 __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
              const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
-             float4* __restrict__ fpp, float4* __restrict__ flo, float4* __restrict__ fbig,
+             float4* __restrict__ fpp, float2* __restrict__ flo, float4* __restrict__ fbig,
              uint32_t* __restrict__ next_tile,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
   constexpr uint32_t kTile = 2 * kThreads;  // particles per tile
@@ -1099,7 +1112,7 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
     // parts) starts at zero
     float4* fbig = c->fplo + c->n_max;
     cudaMemsetAsync(c->fpp, 0, sizeof(float4) * static_cast<size_t>(n), s);
-    cudaMemsetAsync(c->fplo, 0, sizeof(float4) * static_cast<size_t>(n), s);
+    cudaMemsetAsync(c->fplo, 0, sizeof(float2) * static_cast<size_t>(n), s);
     cudaMemsetAsync(fbig, 0, sizeof(float4) * static_cast<size_t>(n), s);
     cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
     // persistent grid of a few blocks per SM: the SM resources it leaves free let the mesh
@@ -1111,8 +1124,9 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
     auto run = [&](auto k_rows1, auto k_rows2, auto k_rows3) {
       auto kern = c->g.rows == 1 ? k_rows1 : (c->g.rows == 2 ? k_rows2 : k_rows3);
       kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
-                                       c->starts, static_cast<float4*>(c->fpp), c->fplo, fbig,
-                                       c->pp_tile, c->energy_acc, c->pair_acc);
+                                       c->starts, static_cast<float4*>(c->fpp),
+                                       reinterpret_cast<float2*>(c->fplo), fbig, c->pp_tile,
+                                       c->energy_acc, c->pair_acc);
     };
     switch (c->poly.deg) {
       case 4: run(k_pp_f32<4, 1>, k_pp_f32<4, 2>, k_pp_f32<4, 3>); break;
