@@ -41,19 +41,19 @@ KERNELS_PER_EVAL = 10  # bin, 3 scan passes, scatter, short range, deposit, fuse
 # DRAM bytes (read + write) of one k_pp_f32 launch, from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum), with the particle count captured and the limiter the capture showed:
 # the 2,097,152-particle sphere on a 128^3 mesh stands in for the 16M sphere (same density; the
-# kernel reads each 32-B record about once from DRAM and its reductions into the coarse, fine
-# and big result arrays miss L2 about once per particle, so its traffic scales with the
+# kernel reads each 32-B record about once from DRAM and its reductions into the coarse (16 B),
+# fine (8 B) and big (16 B) result arrays miss L2 about once per particle, so its traffic scales with the
 # particle count); the 1M Gaussian is captured at full size. Workloads without a capture of the
 # current kernel report traffic null.
 PP_DRAM = {
-    "sphere16m": dict(bytes=144.439552e6 + 30.444544e6, particles=2097152,
+    "sphere16m": dict(bytes=127.7248e6 + 21.083136e6, particles=2097152,
                       source="k_pp_f32<6, 2> on the 2,097,152-particle sphere (128^3), scaled "
                              "by particle count",
-                      limiter="instruction issue 75%, L1 data pipe 72% (ncu, "
+                      limiter="instruction issue 76%, L1 data pipe 70% (ncu, "
                               "profiles/k_pp_f32_sphere2m_128.md)"),
-    "gauss1m": dict(bytes=79.892736e6 + 1.780224e6, particles=1048576,
+    "gauss1m": dict(bytes=71.542272e6 + 0.877568e6, particles=1048576,
                     source="k_pp_f32<6, 3> on this workload (1,048,576 particles)",
-                    limiter="L1 data pipe 79%, L2 73% (vector reductions), issue 51% "
+                    limiter="L1 data pipe 77%, L2 72% (vector reductions), issue 52% "
                             "(ncu, profiles/k_pp_f32_gauss1m_64.md)"),
 }
 
