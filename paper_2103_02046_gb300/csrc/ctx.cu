@@ -435,7 +435,7 @@ p3m_status forces_impl(p3m_ctx* c, const double* x, int64_t n, double* f, double
     cudaEventRecord(c->ev_fork, st);
     cudaStreamWaitEvent(c->s_pp, c->ev_fork, 0);
     cudaEventRecord(c->tev[6], c->s_pp);
-    launch_pp(c, n, c->s_pp);
+    launch_pp(c, n, c->s_pp, energy != nullptr);
     cudaEventRecord(c->tev[7], c->s_pp);
     cudaEventRecord(c->ev_join, c->s_pp);
   }

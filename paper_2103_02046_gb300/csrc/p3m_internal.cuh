@@ -354,7 +354,9 @@ void launch_vjp_gather(const p3m_ctx* c, int64_t n, int pass, const double* w, d
 void launch_get_mesh(const p3m_ctx* c, int which, double* out);
 
 // short range (pp.cu)
-void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s);
+// want_energy: the short-range energy is asked for (the FP64 path skips the pair potentials
+// otherwise)
+void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s, bool want_energy);
 // (particle, record) distance tests of the FP32 short range on the current sorted records,
 // into *out (FP64 contexts: nothing; their short range counts as it runs)
 void launch_pp_count(const p3m_ctx* c, int64_t n, unsigned long long* out, cudaStream_t s);

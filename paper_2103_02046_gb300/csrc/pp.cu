@@ -848,6 +848,12 @@ __device__ __forceinline__ void pair_terms_df(const DFTable& T, double r2, doubl
   pot = df_to_double(o.pot);
 }
 
+// the force coefficient alone (no potential: the energy is not asked for)
+__device__ __forceinline__ double pair_fco_df(const DFTable& T, double r2) {
+  const DF sd = df_from_double(r2);
+  return df_to_double(dfm::pair_df(T.k, T.coef, dfm::F2{sd.hi, sd.lo}).fco);
+}
+
 __device__ __forceinline__ void pair_hess_dfd(const DFTable& T, double r2, double& fco,
                                               double& dfr) {
   const DF sd = df_from_double(r2);
@@ -884,7 +890,7 @@ __device__ __forceinline__ void row_range64(const Geom& g, const uint32_t* __res
 // block, j != i), with no reductions: each particle's sum runs in the fixed sorted order and is
 // stored as is, together with its potential (w), from which the energy is summed in a fixed
 // order afterwards.
-template <int kRows, bool kDet, bool kDF>
+template <int kRows, bool kDet, bool kDF, bool kPot>
 __global__ void __launch_bounds__(kThreads)
     k_pp_f64(Geom g, const uint32_t* __restrict__ total, const Rec64* __restrict__ rec,
              const Rec64* __restrict__ recm, const uint32_t* __restrict__ starts,
@@ -925,24 +931,30 @@ __global__ void __launch_bounds__(kThreads)
     const double rx = px - rj.u[0], ry = py - rj.u[1], rz = pz - rj.u[2];
     const double r2 = rx * rx + ry * ry + rz * rz;
     const bool hit = has && r2 < 1.0 && r2 > 0.0;
-    double fco, pot;
-    if constexpr (kDF)
-      pair_terms_df(dft_s[0], hit ? r2 : 0.5, fco, pot);
-    else
+    double fco, pot = 0.0;
+    if constexpr (kDF) {
+      if constexpr (kPot)
+        pair_terms_df(dft_s[0], hit ? r2 : 0.5, fco, pot);
+      else
+        fco = pair_fco_df(dft_s[0], hit ? r2 : 0.5);
+    } else {
       pair_terms(hit ? r2 : 0.5, kappa, c2k, fco, pot);
+    }
     if (hit) {
-      const double fx = fco * rx, fy = fco * ry, fz = fco * rz;
-      sum[0] += fx;
-      sum[1] += fy;
-      sum[2] += fz;
-      sum[3] += pot;
+      // the reaction's components, -fco (xi_i - xi_j): the own sum subtracts them
+      const double nf = -fco;
+      const double gx = nf * rx, gy = nf * ry, gz = nf * rz;
+      sum[0] -= gx;
+      sum[1] -= gy;
+      sum[2] -= gz;
+      if constexpr (kPot) sum[3] += pot;
       ++np;
       if (!kDet) {
         double* fj = &fpp[j].x;
         // the potential is summed on the owner's side only: j's fourth component stays unused
-        atomicAdd(fj, -fx);
-        atomicAdd(fj + 1, -fy);
-        atomicAdd(fj + 2, -fz);
+        atomicAdd(fj, gx);
+        atomicAdd(fj + 1, gy);
+        atomicAdd(fj + 2, gz);
       }
     }
     head += has;
@@ -992,7 +1004,7 @@ __global__ void __launch_bounds__(kThreads)
           sum[0] -= fco * ax;
           sum[1] -= fco * ay;
           sum[2] -= fco * az;
-          sum[3] -= pot;
+          if constexpr (kPot) sum[3] -= pot;
           ++ni;
         }
       }
@@ -1103,7 +1115,7 @@ __global__ void __launch_bounds__(kThreads)
 
 }  // namespace
 
-void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
+void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s, bool want_energy) {
   if (n == 0) return;
   const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   const uint32_t* total = c->starts + c->nkeys;
@@ -1146,19 +1158,30 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s) {
     auto pick = [&](auto k1, auto k2, auto k3) {
       return c->g.rows == 1 ? k1 : (c->g.rows == 2 ? k2 : k3);
     };
-    auto kern = c->pdf ? (c->det ? pick(k_pp_f64<1, true, true>, k_pp_f64<2, true, true>,
-                                        k_pp_f64<3, true, true>)
-                                 : pick(k_pp_f64<1, false, true>, k_pp_f64<2, false, true>,
-                                        k_pp_f64<3, false, true>))
-                       : (c->det ? pick(k_pp_f64<1, true, false>, k_pp_f64<2, true, false>,
-                                        k_pp_f64<3, true, false>)
-                                 : pick(k_pp_f64<1, false, false>, k_pp_f64<2, false, false>,
-                                        k_pp_f64<3, false, false>));
+    // the pair potentials are summed for the energy or the deterministic mode's fixed-order sum
+    const bool pot = c->det || want_energy;
+    auto kern = c->pdf
+                    ? (c->det ? pick(k_pp_f64<1, true, true, true>, k_pp_f64<2, true, true, true>,
+                                     k_pp_f64<3, true, true, true>)
+                              : (pot ? pick(k_pp_f64<1, false, true, true>,
+                                            k_pp_f64<2, false, true, true>,
+                                            k_pp_f64<3, false, true, true>)
+                                     : pick(k_pp_f64<1, false, true, false>,
+                                            k_pp_f64<2, false, true, false>,
+                                            k_pp_f64<3, false, true, false>)))
+                    : (c->det ? pick(k_pp_f64<1, true, false, true>, k_pp_f64<2, true, false, true>,
+                                     k_pp_f64<3, true, false, true>)
+                              : (pot ? pick(k_pp_f64<1, false, false, true>,
+                                            k_pp_f64<2, false, false, true>,
+                                            k_pp_f64<3, false, false, true>)
+                                     : pick(k_pp_f64<1, false, false, false>,
+                                            k_pp_f64<2, false, false, false>,
+                                            k_pp_f64<3, false, false, false>)));
     if (!c->det) cudaMemsetAsync(c->fpp, 0, sizeof(D4) * static_cast<size_t>(n), s);
     kern<<<blocks, kThreads, 0, s>>>(c->g, total, static_cast<const Rec64*>(c->recp),
                                      static_cast<const Rec64*>(c->recm), c->starts,
-                                     static_cast<D4*>(c->fpp), c->energy_acc, c->pair_acc,
-                                     c->pdf);
+                                     static_cast<D4*>(c->fpp), pot ? c->energy_acc : nullptr,
+                                     c->pair_acc, c->pdf);
     if (c->det) launch_det_sum_pp(c, n, s);
   }
 }
