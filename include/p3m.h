@@ -72,7 +72,14 @@ typedef struct p3m_params {
   int32_t influence;     /* 0 = sampled G^L; optimal influence function of eq. (Ghfinal) as a
                             factor on the sampled kernels: 1 = principal alias only (1/U^2),
                             2 = alias sums over |m_d| <= 2 (computed once in p3m_create) */
-  int32_t precision;     /* p3m_precision */
+  int32_t precision;     /* p3m_precision. P3M_FP64: positions, separations, pair decisions
+                            (r^2 < r_c^2), sums, mesh and transforms in FP64; the short-range pair
+                            function erfc/exp in double-float arithmetic (pairs of FP32 numbers,
+                            relative error about 5e-14 at kappa = 3) for kappa <= 6.5, FP64 above;
+                            forces match an FP64 evaluation to 1e-12. P3M_FP32_MIXED: FP32 short
+                            range with exact FP32 separations and compensated sums, FP32 mesh and
+                            transforms, FP64 positions, results and reductions; forces match the
+                            FP64 path to about 2e-7 (bounded by 1e-5) */
   int32_t deterministic; /* 1 = run-to-run identical results (FP64 path, pm_bc 0 or 1): particles
                             in a fixed order within each cell, every ordered pair evaluated by
                             its own particle without reductions, node charges summed exactly in
