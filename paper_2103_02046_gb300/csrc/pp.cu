@@ -67,13 +67,14 @@ __device__ __forceinline__ void pair_terms(double r2, double kappa, double c2k, 
   fco = (pot + c2k * ex) / r2;
 }
 
+template <int kBlk = kThreads>
 __device__ __forceinline__ void block_reduce_add(double v, double* dst) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __shared__ double ws[kThreads / 32];
+  __shared__ double ws[kBlk / 32];
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double s = threadIdx.x < kThreads / 32 ? ws[threadIdx.x] : 0.0;
+    double s = threadIdx.x < kBlk / 32 ? ws[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) atomicAdd(dst, s);
   }
@@ -161,6 +162,7 @@ struct PosD {
 // rsqrt, rcp and ex2 are the hardware approximations (flush-to-zero: every argument here is a
 // normal number).
 // ------------------------------------------------------------------------------------------
+constexpr int kPpThreads = 128;     // threads per block of the FP32 short range
 constexpr int kPpBlocksPerSm = 6;    // resident blocks per SM of the short range (80 registers)
 constexpr int kVjpBlocksPerSm = 10;  // resident blocks per SM of its adjoint (48 registers)
 
@@ -400,22 +402,55 @@ __device__ __forceinline__ void pair_runs(const Geom& g, const uint32_t* __restr
   if (!kOnlyA && !same) b_runs<kRows>(g, starts, pb, lb, ib, emit);
 }
 
+// Run slots per lane of k_pp_f32: a's and b's runs, up to twice the half shell when their rows
+// differ. With 3 rows per cutoff (25 half-shell rows) that would not fit beside 6 blocks per
+// SM: a lane whose particles sit in different rows then walks a's runs first and b's after
+// them, in the same slots.
+__host__ __device__ constexpr int pp_pair_runs(int rows) {
+  return (rows >= 3 ? 1 : 2) * ((2 * rows + 1) * (2 * rows + 1) - (2 * rows + 1) * (2 * rows + 1) / 2);
+}
+inline size_t pp_run_bytes(int rows) {
+  return 2 * sizeof(uint32_t) * static_cast<size_t>(pp_pair_runs(rows)) * kPpThreads;
+}
+
+// Work stealing inside a warp: once at least kStealMin lanes have walked all their runs, each
+// of them takes work from a lane that still has some: that lane's last unstarted run, or else
+// the back half of its current run if at least 2 kStealRecs records are left of it. The thief
+// first sends the sums of the pair it held to their force arrays, then adopts the donor's pair
+// (positions, index, which of the two the run is tested against) with zeroed sums, which it
+// sends out in turn when it is done or steals again; the reduction targets are shared, so the
+// owner's force is the sum of its holders' parts. This takes the warp's step count from the
+// maximum of its lanes' walks towards their mean.
+constexpr int kStealMin = 8;
+constexpr uint32_t kStealRecs = 4;
+
+__device__ __forceinline__ float4 shfl_f4(float4 v, int src) {
+  v.x = __shfl_sync(0xffffffffu, v.x, src);
+  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  v.z = __shfl_sync(0xffffffffu, v.z, src);
+  v.w = __shfl_sync(0xffffffffu, v.w, src);
+  return v;
+}
+
 template <int kDeg, int kRows>
-__global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
+__global__ void __launch_bounds__(kPpThreads, kPpBlocksPerSm)
     k_pp_f32(Geom g, PairPoly P, const uint32_t* __restrict__ total,
              const float4* __restrict__ rec, const uint32_t* __restrict__ starts,
              float4* __restrict__ fpp, float2* __restrict__ flo, float4* __restrict__ fbig,
              uint32_t* __restrict__ next_tile,
              double* __restrict__ energy, unsigned long long* __restrict__ pairs) {
-  constexpr uint32_t kTile = 2 * kThreads;  // particles per tile
-  // a's and b's runs: up to twice the half shell when their rows differ. With 3 rows per cutoff
-  // (25 half-shell rows) that would not fit beside 6 blocks per SM: a lane whose particles sit
-  // in different rows then walks a's runs first and b's after them, in the same slots (kPhased)
+  constexpr uint32_t kTile = 2 * kPpThreads;  // particles per tile
   constexpr bool kPhased = kRows >= 3;
-  constexpr int kPairRuns = (kPhased ? 1 : 2) * Rows<kRows>::half;
-  __shared__ uint32_t run_j0[kPairRuns][kThreads], run_j1[kPairRuns][kThreads];
+  constexpr int kPairRuns = pp_pair_runs(kRows);
+  static_assert(kPairRuns == (kPhased ? 1 : 2) * Rows<kRows>::half, "run slots");
+  // the lanes' runs, [kPairRuns][kPpThreads] each, in dynamic shared memory
+  extern __shared__ uint32_t pp_runs[];
+  uint32_t(*run_j0)[kPpThreads] = reinterpret_cast<uint32_t(*)[kPpThreads]>(pp_runs);
+  uint32_t(*run_j1)[kPpThreads] = run_j0 + kPairRuns;
+  __shared__ uint8_t donor_s[kPpThreads / 32][32];
   __shared__ uint32_t tile_s;
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
   const uint32_t N = *total;
   double e_acc = 0.0;
   unsigned long long np = 0, ni = 0;
@@ -428,13 +463,14 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     const uint32_t tile = tile_s;
     __syncthreads();
     if (static_cast<uint64_t>(tile) * kTile >= N) break;
-    const uint32_t ia = tile * kTile + 2 * tid, ib = ia + 1;
-    const bool alive_a = ia < N, alive_b = ib < N;
+    // the pair the lane holds: a = ia, b = ia + 1 (a thief adopts another lane's pair)
+    uint32_t ia = tile * kTile + 2 * tid;
+    bool alive_a = ia < N, alive_b = ia + 1 < N;
     // lanes past the last particle read record 0 (in bounds) and take part in the lockstep
     // loop with every result masked out
-    const uint32_t ea = alive_a ? ia : 0u, eb = alive_b ? ib : ea;
-    const float4 pa = rec[2 * ea], la = rec[2 * ea + 1];
-    const float4 pb = rec[2 * eb], lb = rec[2 * eb + 1];
+    const uint32_t ea = alive_a ? ia : 0u, eb = alive_b ? ia + 1 : ea;
+    float4 pa = rec[2 * ea], la = rec[2 * ea + 1];
+    float4 pb = rec[2 * eb], lb = rec[2 * eb + 1];
     // runs: with a and b in one row, the hull of their two runs per neighbour row (tested
     // against both); otherwise a's runs [0, split) and b's runs [split, cnt) (kPhased: a's
     // runs, then b's in their place once they are walked, while pending_b)
@@ -460,6 +496,65 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
     for (int c = 0; c < 4; ++c) sa[c].hi = sa[c].lo = sb[c].hi = sb[c].lo = 0.f;
     float qa[4] = {0.f, 0.f, 0.f, 0.f}, qb[4] = {0.f, 0.f, 0.f, 0.f};
     uint32_t np_part = 0;
+    // images within r_c of particles less than r_c above the cathode (rare): plain loop over
+    // all rows around the image point; image pairs act on the particle only. Taken before the
+    // walk, for the lane's own pair; their potential goes straight to the energy (once)
+    auto images = [&](const float4 pi, const float4 li, Acc2* sum) {
+      const double zi = static_cast<double>(pi.z) + static_cast<double>(li.z);
+      if (zi - 0.5 * g.img_c >= 1.0) return;
+      const float mz = static_cast<float>(g.img_c - zi);
+      const float ch = static_cast<float>(g.img_c);
+      const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
+      for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t ja, uint32_t jb) {
+        float rowv[4] = {0.f, 0.f, 0.f, 0.f};
+        for (uint32_t jj = ja; jj < jb; ++jj) {
+          const float4 hj = rec[2 * jj], lj = rec[2 * jj + 1];
+          const float ax = (pi.x - hj.x) + (li.x - lj.x);
+          const float ay = (pi.y - hj.y) + (li.y - lj.y);
+          const float s = pi.z + hj.z;
+          const float bp = s - pi.z;
+          const float e = (pi.z - (s - bp)) + (hj.z - bp);
+          const float az = ((s - ch) + e) + ((li.z + lj.z) - cl);
+          const float r2 = ax * ax + ay * ay + az * az;
+          if (r2 < 1.f && r2 > 0.f) {
+            float fco, pot;
+            pair_poly<kDeg>(P, r2, fco, pot);
+            rowv[0] -= fco * ax;
+            rowv[1] -= fco * ay;
+            rowv[2] -= fco * az;
+            rowv[3] -= pot;
+            ++ni;
+          }
+        }
+        for (int c = 0; c < 3; ++c) sum[c].add(rowv[c]);
+        e_acc += static_cast<double>(rowv[3]);
+      });
+    };
+    if (g.pp_bc) {
+      if (alive_a) images(pa, la, sa);
+      if (alive_b) images(pb, lb, sb);
+    }
+    // the held pair's sums (hi + lo of the compensated accumulators) to its force arrays, split
+    // like the reactions, and zeroed; sum_i phi_i over ordered pairs takes each unordered
+    // pair's potential twice
+    auto flush = [&]() {
+      for (int c = 0; c < 4; ++c) {
+        sa[c].add(qa[c]);
+        sb[c].add(qb[c]);
+        qa[c] = qb[c] = 0.f;
+      }
+      if (alive_a) {
+        split_add_v4(fpp + ia, flo + ia, fbig + ia, sa[0].hi, sa[1].hi, sa[2].hi, sa[0].lo,
+                     sa[1].lo, sa[2].lo);
+        e_acc += 2.0 * static_cast<double>(sa[3].value());
+      }
+      if (alive_b) {
+        split_add_v4(fpp + ia + 1, flo + ia + 1, fbig + ia + 1, sb[0].hi, sb[1].hi, sb[2].hi,
+                     sb[0].lo, sb[1].lo, sb[2].lo);
+        e_acc += 2.0 * static_cast<double>(sb[3].value());
+      }
+      for (int c = 0; c < 4; ++c) sa[c].hi = sa[c].lo = sb[c].hi = sb[c].lo = 0.f;
+    };
     // one candidate record j (hj, lj) against a and b
     auto cand = [&](bool v, uint32_t j, const float4& hj, const float4& lj) {
       const float ax = (pa.x - hj.x) + (la.x - lj.x);
@@ -526,13 +621,81 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
         if (__any_sync(0xffffffffu, go)) {
           if (go) {
             cnt = 0;
-            b_runs<kRows>(g, starts, pb, lb, ib, emit);
+            b_runs<kRows>(g, starts, pb, lb, ia + 1, emit);
             k = 0;
             pending_b = false;
             ta = false;
             tb = true;
             ptr = cnt > 0 ? run_j0[0][tid] : 0u;
             end = cnt > 0 ? run_j1[0][tid] : 0u;
+          }
+        }
+      }
+      {
+        const bool idle = ptr >= end && !pending_b;
+        const unsigned im = __ballot_sync(0xffffffffu, idle);
+        if (__popc(im) >= kStealMin) {
+          const bool spare = k + 1 < cnt;  // an unstarted run (runs are never empty)
+          const bool halve = !spare && ptr < end && end - ptr >= 2 * kStealRecs;
+          const bool offer = spare || halve;
+          const unsigned om = __ballot_sync(0xffffffffu, offer);
+          if (om != 0u) {
+            // the offered run [g0, g1) and whom it is tested against (bit 0: a, bit 1: b);
+            // bit 2: b exists
+            uint32_t g0 = 0, g1 = 0, gf = alive_b ? 4u : 0u;
+            if (spare) {
+              const int kk = cnt - 1;
+              g0 = run_j0[kk][tid];
+              g1 = run_j1[kk][tid];
+              if constexpr (kPhased)  // all runs of the current phase are tested alike
+                gf |= (ta ? 1u : 0u) | (tb ? 2u : 0u);
+              else
+                gf |= ((same || kk < split) ? 1u : 0u) |
+                      ((alive_b && (same || kk >= split)) ? 2u : 0u);
+            } else if (halve) {
+              g0 = ptr + (((end - ptr) >> 1) & ~1u);  // the donor keeps an even count
+              g1 = end;
+              gf |= (ta ? 1u : 0u) | (tb ? 2u : 0u);
+            }
+            // the r-th idle lane takes from the r-th offering lane
+            const unsigned lt = (1u << lane) - 1u;
+            const int nt = __popc(im), no = __popc(om);
+            const int orank = __popc(om & lt), trank = __popc(im & lt);
+            if (offer) donor_s[tid >> 5][orank] = static_cast<uint8_t>(lane);
+            __syncwarp();
+            const bool take = idle && trank < no;
+            const int src = take ? static_cast<int>(donor_s[tid >> 5][trank]) : lane;
+            __syncwarp();
+            if (offer && orank < nt) {
+              if (spare)
+                --cnt;
+              else
+                end = g0;
+            }
+            if (take) flush();  // the sums of the pair held so far
+            // every lane takes part; a lane that takes nothing reads its own values
+            pa = shfl_f4(pa, src);
+            la = shfl_f4(la, src);
+            pb = shfl_f4(pb, src);
+            lb = shfl_f4(lb, src);
+            ia = __shfl_sync(0xffffffffu, ia, src);
+            g0 = __shfl_sync(0xffffffffu, g0, src);
+            g1 = __shfl_sync(0xffffffffu, g1, src);
+            gf = __shfl_sync(0xffffffffu, gf, src);
+            if (take) {
+              alive_a = true;
+              alive_b = (gf & 4u) != 0u;
+              ta = (gf & 1u) != 0u;
+              tb = (gf & 2u) != 0u;
+              // the run-switch formulas above then keep (ta, tb) for this single run (an idle
+              // lane has no b runs pending)
+              same = ta && tb;
+              split = ta ? 1 : 0;
+              k = 0;
+              cnt = 0;
+              ptr = g0;
+              end = g1;
+            }
           }
         }
       }
@@ -550,62 +713,10 @@ __global__ void __launch_bounds__(kThreads, kPpBlocksPerSm)
         np_part = 0;
       }
     }
-    for (int c = 0; c < 4; ++c) {
-      sa[c].add(qa[c]);
-      sb[c].add(qb[c]);
-    }
     np += np_part;
-    const float pair_pot_a = sa[3].value(), pair_pot_b = sb[3].value();
-    // images within r_c of particles less than r_c above the cathode (rare): plain loop over
-    // all rows around the image point; image pairs act on the particle only
-    auto images = [&](const float4 pi, const float4 li, Acc2* sum) {
-      const double zi = static_cast<double>(pi.z) + static_cast<double>(li.z);
-      if (zi - 0.5 * g.img_c >= 1.0) return;
-      const float mz = static_cast<float>(g.img_c - zi);
-      const float ch = static_cast<float>(g.img_c);
-      const float cl = static_cast<float>(g.img_c - static_cast<double>(ch));
-      for_rows<float>(g, starts, pi.x, pi.y, mz, [&](uint32_t ja, uint32_t jb) {
-        float rowv[4] = {0.f, 0.f, 0.f, 0.f};
-        for (uint32_t jj = ja; jj < jb; ++jj) {
-          const float4 hj = rec[2 * jj], lj = rec[2 * jj + 1];
-          const float ax = (pi.x - hj.x) + (li.x - lj.x);
-          const float ay = (pi.y - hj.y) + (li.y - lj.y);
-          const float s = pi.z + hj.z;
-          const float bp = s - pi.z;
-          const float e = (pi.z - (s - bp)) + (hj.z - bp);
-          const float az = ((s - ch) + e) + ((li.z + lj.z) - cl);
-          const float r2 = ax * ax + ay * ay + az * az;
-          if (r2 < 1.f && r2 > 0.f) {
-            float fco, pot;
-            pair_poly<kDeg>(P, r2, fco, pot);
-            rowv[0] -= fco * ax;
-            rowv[1] -= fco * ay;
-            rowv[2] -= fco * az;
-            rowv[3] -= pot;
-            ++ni;
-          }
-        }
-        for (int c = 0; c < 4; ++c) sum[c].add(rowv[c]);
-      });
-    };
-    if (g.pp_bc) {
-      if (alive_a) images(pa, la, sa);
-      if (alive_b) images(pb, lb, sb);
-    }
-    // sum_i phi_i over ordered pairs: each pair's potential was taken once here, plus images
-    // the own sums (hi + lo of the compensated accumulators), split like the reactions
-    if (alive_a) {
-      split_add_v4(fpp + ia, flo + ia, fbig + ia, sa[0].hi, sa[1].hi, sa[2].hi, sa[0].lo,
-                   sa[1].lo, sa[2].lo);
-      e_acc += static_cast<double>(sa[3].value()) + pair_pot_a;
-    }
-    if (alive_b) {
-      split_add_v4(fpp + ib, flo + ib, fbig + ib, sb[0].hi, sb[1].hi, sb[2].hi, sb[0].lo,
-                   sb[1].lo, sb[2].lo);
-      e_acc += static_cast<double>(sb[3].value()) + pair_pot_b;
-    }
+    flush();
   }
-  if (energy) block_reduce_add(e_acc, energy);
+  if (energy) block_reduce_add<kPpThreads>(e_acc, energy);
   warp_add_u64(2ull * np, pairs);
   warp_add_u64(ni, pairs + 1);
 }
@@ -1129,16 +1240,20 @@ void launch_pp(const p3m_ctx* c, int64_t n, cudaStream_t s, bool want_energy) {
     cudaMemsetAsync(c->pp_tile, 0, sizeof(uint32_t), s);
     // persistent grid of a few blocks per SM: the SM resources it leaves free let the mesh
     // chain, on the other stream, run at the same time
-    const int64_t tiles = (n + 2 * kThreads - 1) / (2 * kThreads);  // two particles a thread
+    const int64_t tiles = (n + 2 * kPpThreads - 1) / (2 * kPpThreads);  // two particles a thread
     const unsigned wblocks = static_cast<unsigned>(
         std::min<int64_t>(tiles, static_cast<int64_t>(kPpBlocksPerSm) * c->num_sms));
     // the kernel for the context's row geometry (Geom::rows cell rows per cutoff)
     auto run = [&](auto k_rows1, auto k_rows2, auto k_rows3) {
       auto kern = c->g.rows == 1 ? k_rows1 : (c->g.rows == 2 ? k_rows2 : k_rows3);
-      kern<<<wblocks, kThreads, 0, s>>>(c->g, c->poly, total, static_cast<const float4*>(c->recp),
-                                       c->starts, static_cast<float4*>(c->fpp),
-                                       reinterpret_cast<float2*>(c->fplo), fbig, c->pp_tile,
-                                       c->energy_acc, c->pair_acc);
+      const size_t smem = pp_run_bytes(c->g.rows);
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem));
+      kern<<<wblocks, kPpThreads, smem, s>>>(
+          c->g, c->poly, total, static_cast<const float4*>(c->recp), c->starts,
+          static_cast<float4*>(c->fpp), reinterpret_cast<float2*>(c->fplo), fbig, c->pp_tile,
+          c->energy_acc, c->pair_acc);
     };
     switch (c->poly.deg) {
       case 4: run(k_pp_f32<4, 1>, k_pp_f32<4, 2>, k_pp_f32<4, 3>); break;
