@@ -46,14 +46,14 @@ KERNELS_PER_EVAL = 10  # bin, 3 scan passes, scatter, short range, deposit, fuse
 # particle count); the 1M Gaussian is captured at full size. Workloads without a capture of the
 # current kernel report traffic null.
 PP_DRAM = {
-    "sphere16m": dict(bytes=127.7248e6 + 21.083136e6, particles=2097152,
+    "sphere16m": dict(bytes=127.666688e6 + 20.851968e6, particles=2097152,
                       source="k_pp_f32<6, 2> on the 2,097,152-particle sphere (128^3), scaled "
                              "by particle count",
-                      limiter="instruction issue 76%, L1 data pipe 70% (ncu, "
+                      limiter="L1 data pipe 73%, instruction issue 71%, L2 48% (ncu, "
                               "profiles/k_pp_f32_sphere2m_128.md)"),
-    "gauss1m": dict(bytes=71.542272e6 + 0.877568e6, particles=1048576,
+    "gauss1m": dict(bytes=71.533568e6 + 0.91648e6, particles=1048576,
                     source="k_pp_f32<6, 3> on this workload (1,048,576 particles)",
-                    limiter="L1 data pipe 77%, L2 72% (vector reductions), issue 52% "
+                    limiter="L1 data pipe 75%, L2 72% (vector reductions), issue 48% "
                             "(ncu, profiles/k_pp_f32_gauss1m_64.md)"),
 }
 
