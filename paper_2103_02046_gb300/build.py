@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libp3m.so")
-SOURCES = ["ctx.cu", "sort.cu", "pm.cu", "zconv.cu", "box.cu", "pp.cu", "particles.cu", "noalloc.cu"]
+SOURCES = ["ctx.cu", "sort.cu", "pm.cu", "zconv.cu", "zsolve_df.cu", "box.cu", "pp.cu",
+           "particles.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

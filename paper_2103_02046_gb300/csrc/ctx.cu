@@ -400,6 +400,19 @@ p3m_status mesh_solve(p3m_ctx* c, bool want_phi, bool want_diff, bool want_energ
     c->diff_valid = true;
     return P3M_OK;
   }
+  if (c->zsolve_df) {
+    // FP64 potential: x-y transforms of the charged planes, the fused z solve in double-float,
+    // x-y inverses of the planes z < n_z
+    if (cufftExecD2Z(c->plan_xy_f, static_cast<cufftDoubleReal*>(c->qpad),
+                     static_cast<cufftDoubleComplex*>(c->qhat)) != CUFFT_SUCCESS)
+      return fail(c, P3M_ECUFFT, "cuFFT forward transform failed");
+    launch_zsolve_df(c, want_energy);
+    if (cufftExecZ2D(c->plan_xy_i, static_cast<cufftDoubleComplex*>(c->phihat),
+                     static_cast<cufftDoubleReal*>(c->phireal)) != CUFFT_SUCCESS)
+      return fail(c, P3M_ECUFFT, "cuFFT inverse transform failed");
+    c->phi_valid = true;
+    return P3M_OK;
+  }
   p3m_status s = fft_r2c(c);
   if (s != P3M_OK) return s;
   if (!c->fp32) want_phi = true, want_diff = false;
@@ -733,6 +746,10 @@ p3m_status p3m_create(const p3m_params* params, int64_t n_max, void* stream, p3m
   if (e == cudaSuccess && zconv_supported(c)) {
     e = zconv_setup(c);
     c->zconv = e == cudaSuccess;
+  }
+  if (e == cudaSuccess && zsolve_df_supported(c)) {
+    e = zsolve_df_setup(c);
+    c->zsolve_df = e == cudaSuccess;
   }
   if (e != cudaSuccess) {
     free_all(c);

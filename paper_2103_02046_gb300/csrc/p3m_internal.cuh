@@ -273,7 +273,8 @@ struct p3m_ctx {
   void* phihat = nullptr;       // potential spectrum
   void* phireal = nullptr;      // potential on the doubled mesh
   float2* dfac = nullptr;       // FP32: difference factors e^{2 pi i k/M} - 1 per axis (Mx/2+1 + My + Mz)
-  float2* ztw = nullptr;        // FP32 fused z solve: e^{-2 pi i t / Mz}, t < Mz
+  float2* ztw = nullptr;        // fused z solve: e^{-2 pi i t / Mz}, t < Mz (FP32 path: float2;
+                                // FP64 path: double-float, two float2 per entry)
   // grounded box (pm_bc = 2, FP64): odd extension (2(n-1))^3, its half spectrum, multiplier
   double* box_real = nullptr;
   double2* box_spec = nullptr;
@@ -281,6 +282,7 @@ struct p3m_ctx {
   cufftHandle plan_box_f = 0, plan_box_i = 0;
   bool have_box_f = false, have_box_i = false;
   bool zconv = false;           // FP32 forces use the fused z solve
+  bool zsolve_df = false;       // the FP64 potential uses the double-float fused z solve
   // Pruned transforms of the doubled mesh: the charge is non-zero, and the fields are needed,
   // only in the n^3 block, so the x-y plane transforms run on the first n_z planes only and
   // the z transforms are strided 1D batches over all (kx, ky) columns.
@@ -342,6 +344,11 @@ void launch_green_multiply(const p3m_ctx* c, bool want_phi, bool want_diff, bool
 bool zconv_supported(const p3m_ctx* c);
 cudaError_t zconv_setup(p3m_ctx* c);
 void launch_zconv(const p3m_ctx* c, bool want_energy);
+// FP64 path: forward z transform, Green's multiply (with the cathode image term) and inverse z
+// transform of the potential, fused, in double-float arithmetic (zsolve_df.cu)
+bool zsolve_df_supported(const p3m_ctx* c);
+cudaError_t zsolve_df_setup(p3m_ctx* c);
+void launch_zsolve_df(const p3m_ctx* c, bool want_energy);
 // grounded box (pm_bc = 2): discrete-Laplacian solve of the deposit into phireal
 p3m_status box_setup(p3m_ctx* c);
 p3m_status box_solve(p3m_ctx* c, bool want_energy);
