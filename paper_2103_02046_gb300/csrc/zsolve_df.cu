@@ -14,7 +14,9 @@
 // Transforms: power-of-two Mz in [64, 2048], radix-8 Stockham autosort passes (then one radix-4
 // or radix-2 pass when log2 Mz is not a multiple of 3) in shared memory; twiddles from a table
 // computed in FP64 on the host and split into double-float. A block holds C = 2048 / Mz columns
-// of consecutive kx (one 8-point butterfly per thread and pass, 256 threads).
+// of consecutive kx (one 8-point butterfly per thread and pass, 256 threads). The Green's spectra
+// are held in double-float from context creation on, and the charge spectrum is split by
+// integer operations, so that no FP64 instruction runs per element but the final conversion.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -65,10 +67,31 @@ __device__ __forceinline__ F2 df_from(double v) {
   const float h = static_cast<float>(v);
   return F2{h, static_cast<float>(v - static_cast<double>(h))};
 }
+// v = hi + lo by integer operations on v's bits, without FP64 instructions (GB300's FP64 pipe
+// runs at a small fraction of the FP32 rate): hi holds the sign, the exponent and the leading 23
+// stored significand bits of v (truncated, so exact in FP32); the remaining 29 bits, r = r1 2^6 +
+// r0 (r1 < 2^23, r0 < 2^6, each exact in FP32 through the 2^23 magic number), give
+// lo = (r1 2^6 + r0) 2^(e - 1075), rounded once to FP32, with v's sign. Zero and subnormal v give
+// zero; |v| outside [2^-74, 2^127] takes the FP64 conversion.
+__device__ __forceinline__ F2 df_split(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = static_cast<int>((b >> 52) & 0x7ffu);
+  const unsigned sgn = static_cast<unsigned>(b >> 32) & 0x80000000u;
+  if (e == 0) return F2{__uint_as_float(sgn), 0.f};
+  if (e < 949 || e > 1150) return df_from(v);
+  const unsigned mh = static_cast<unsigned>(b >> 29) & 0x7fffffu;
+  const float hi = __uint_as_float(sgn | (static_cast<unsigned>(e - 1023 + 127) << 23) | mh);
+  const unsigned r = static_cast<unsigned>(b) & 0x1fffffffu;
+  const float r1 = __fsub_rn(__uint_as_float(0x4b000000u | (r >> 6)), 8388608.f);
+  const float r0 = __fsub_rn(__uint_as_float(0x4b000000u | (r & 63u)), 8388608.f);
+  const float scale = __uint_as_float(sgn | (static_cast<unsigned>(e - 1075 + 127) << 23));
+  return F2{hi, __fmul_rn(__fmaf_rn(r1, 64.f, r0), scale)};
+}
 __device__ __forceinline__ double d_of(F2 a) {
   return static_cast<double>(a.hi) + static_cast<double>(a.lo);
 }
 __device__ __forceinline__ double2 cd_to(CD a) { return make_double2(d_of(a.x), d_of(a.y)); }
+__device__ __forceinline__ CD cd_split(double2 v) { return CD{df_split(v.x), df_split(v.y)}; }
 
 // sqrt(1/2) in double-float
 __device__ __forceinline__ F2 half_sqrt2() {
@@ -227,7 +250,7 @@ __device__ void dcolumn_fft(CD* a, int logN, int i0, int tpc, const CD* __restri
 // One block: columns kx0 .. kx0 + C - 1 (clipped to Hx) at one ky.
 __global__ void __launch_bounds__(kDThreads, 2)
     k_zsolve_df(Geom g, int logN, int padN, const double2* __restrict__ qhat,
-                const double* __restrict__ kf, const double2* __restrict__ ki,
+                const F2* __restrict__ kf, const CD* __restrict__ ki,
                 const CD* __restrict__ tw_g, double2* __restrict__ phihat,
                 double* __restrict__ energy) {
   extern __shared__ CD zd[];
@@ -249,7 +272,7 @@ __global__ void __launch_bounds__(kDThreads, 2)
   for (int idx = tid; idx < kDElems; idx += kDThreads) {
     const int z = idx >> logC, kx = kx0 + (idx & (C - 1));
     A[(idx & (C - 1)) * padN + dpad(z)] =
-        (z < nz && kx < Hx) ? cd_from(qhat[z * plane + row + kx]) : cd_zero();
+        (z < nz && kx < Hx) ? cd_split(qhat[z * plane + row + kx]) : cd_zero();
   }
   __syncthreads();
   const int c = tid / tpc, i0 = tid - c * tpc;
@@ -266,12 +289,12 @@ __global__ void __launch_bounds__(kDThreads, 2)
     CD* cl = A + cc * padN;
     const CD a = cl[dpad(kz)], b = cl[dpad(kz2)];
     const size_t ia = kz * plane + row + kxx, ib = kz2 * plane + row + kxx;
-    const F2 fa = df_from(kf[ia]), fb = df_from(kf[ib]);
+    const F2 fa = kf[ia], fb = kf[ib];
     CD ba{dfm::mul(a.x, fa), dfm::mul(a.y, fa)};
     CD bb{dfm::mul(b.x, fb), dfm::mul(b.y, fb)};
     if (ki) {
-      ba = cd_sub(ba, cd_mul(cd_from(ki[ia]), b));
-      bb = cd_sub(bb, cd_mul(cd_from(ki[ib]), a));
+      ba = cd_sub(ba, cd_mul(ki[ia], b));
+      bb = cd_sub(bb, cd_mul(ki[ib], a));
     }
     if (energy) {
       const double wx = (kxx == 0 || 2 * kxx == g.M[0]) ? 1.0 : 2.0;
@@ -294,6 +317,16 @@ __global__ void __launch_bounds__(kDThreads, 2)
   if (energy) {
     for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
     if ((tid & 31) == 0 && e != 0.0) atomicAdd(energy, e);
+  }
+}
+
+// The Green's spectra, FP64 as built, to double-float in place (8 bytes each either way), once
+// at context creation: the fused solve is then their only reader.
+__global__ void k_spectra_to_df(double* __restrict__ v, size_t n) {
+  const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (i < n) {
+    const F2 d = df_from(v[i]);
+    reinterpret_cast<F2*>(v)[i] = d;
   }
 }
 
@@ -327,6 +360,16 @@ cudaError_t zsolve_df_setup(p3m_ctx* c) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_zsolve_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(zsolve_df_smem_bytes(N)));
+  // the spectra: n_cplx reals (free kernel) and n_cplx complex values (image kernel)
+  auto convert = [&](void* p, size_t n) {
+    if (p == nullptr || e != cudaSuccess) return;
+    k_spectra_to_df<<<static_cast<unsigned>((n + 255) / 256), 256, 0, c->work>>>(
+        static_cast<double*>(p), n);
+    e = cudaGetLastError();
+  };
+  convert(c->khat_f, c->n_cplx);
+  convert(c->khat_i, 2 * c->n_cplx);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->work);
   return e;
 }
 
@@ -341,7 +384,7 @@ void launch_zsolve_df(const p3m_ctx* c, bool want_energy) {
   double* en = want_energy ? c->energy_acc + 1 : nullptr;
   k_zsolve_df<<<blocks, kDThreads, zsolve_df_smem_bytes(N), c->work>>>(
       g, logN, dpad(N), static_cast<const double2*>(c->qhat),
-      static_cast<const double*>(c->khat_f), static_cast<const double2*>(c->khat_i),
+      static_cast<const F2*>(c->khat_f), static_cast<const CD*>(c->khat_i),
       reinterpret_cast<const CD*>(c->ztw), static_cast<double2*>(c->phihat), en);
 }
 
