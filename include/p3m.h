@@ -73,10 +73,12 @@ typedef struct p3m_params {
                             factor on the sampled kernels: 1 = principal alias only (1/U^2),
                             2 = alias sums over |m_d| <= 2 (computed once in p3m_create) */
   int32_t precision;     /* p3m_precision. P3M_FP64: positions, separations, pair decisions
-                            (r^2 < r_c^2), sums, mesh and transforms in FP64; the short-range pair
-                            function erfc/exp in double-float arithmetic (pairs of FP32 numbers,
-                            relative error about 5e-14 at kappa = 3) for kappa <= 6.5, FP64 above;
-                            forces match an FP64 evaluation to 1e-12. P3M_FP32_MIXED: FP32 short
+                            (r^2 < r_c^2), sums, mesh and x-y transforms in FP64; the short-range
+                            pair function erfc/exp in double-float arithmetic (pairs of FP32
+                            numbers, relative error about 5e-14 at kappa = 3) for kappa <= 6.5,
+                            FP64 above; the z transforms and the Green's-function multiply in
+                            double-float (non-deterministic contexts, Mz a power of two in
+                            [64, 2048]), else FP64; forces match an FP64 evaluation to 1e-12. P3M_FP32_MIXED: FP32 short
                             range with exact FP32 separations and compensated sums, FP32 mesh and
                             transforms, FP64 positions, results and reductions; forces match the
                             FP64 path to about 2e-7 (bounded by 1e-5) */
