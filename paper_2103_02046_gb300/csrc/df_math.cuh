@@ -27,6 +27,7 @@
 
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <vector>
 
@@ -109,6 +110,54 @@ DFM_HD F2 mul_f(F2 a, float b) {
   const F2 p = two_prod(a.hi, b);
   return fast_two_sum(p.hi, fma_rn(a.lo, b, p.lo));
 }
+// Bit views (the device intrinsics, or a copy of the bytes on the host).
+DFM_HD uint64_t bits_of(double v) {
+#if defined(__CUDA_ARCH__)
+  return static_cast<uint64_t>(__double_as_longlong(v));
+#else
+  uint64_t b;
+  memcpy(&b, &v, sizeof b);
+  return b;
+#endif
+}
+DFM_HD float float_of(uint32_t b) {
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(b);
+#else
+  float v;
+  memcpy(&v, &b, sizeof v);
+  return v;
+#endif
+}
+
+// A double as hi + lo by FP64 conversions (hi its FP32 rounding, lo the rest rounded).
+DFM_HD F2 split_double_fp64(double v) {
+  const float h = static_cast<float>(v);
+  return F2{h, static_cast<float>(v - static_cast<double>(h))};
+}
+
+// A double as hi + lo by integer operations on its bits, with no FP64 instruction (GB300's FP64
+// pipe runs at a small fraction of its FP32 rate): hi holds the sign, the exponent and the
+// leading 23 stored significand bits (truncated, so exact in FP32); the remaining 29 bits,
+// r = r1 2^6 + r0 (r1 < 2^23 and r0 < 2^6, each exact in FP32 through the 2^23 magic number), give
+// lo = (r1 2^6 + r0) 2^(e - 1075), rounded once to FP32, with v's sign. So |lo| < ulp(hi) and
+// hi + lo = v to 2^-47 relative. Zero and subnormal doubles give zero (of v's sign); |v| outside
+// [2^-74, 2^128) takes the FP64 conversion.
+DFM_HD F2 split_double(double v) {
+  const uint64_t b = bits_of(v);
+  const int e = static_cast<int>((b >> 52) & 0x7ffu);
+  const uint32_t sgn = static_cast<uint32_t>(b >> 32) & 0x80000000u;
+  if (e == 0) return F2{float_of(sgn), 0.f};
+  if (e < 949 || e > 1150) return split_double_fp64(v);
+  const uint32_t mh = static_cast<uint32_t>(b >> 29) & 0x7fffffu;
+  const float hi = float_of(sgn | (static_cast<uint32_t>(e - 1023 + 127) << 23) | mh);
+  const uint32_t r = static_cast<uint32_t>(b) & 0x1fffffffu;
+  const float r1 = sub_rn(float_of(0x4b000000u | (r >> 6)), 8388608.f);
+  const float r0 = sub_rn(float_of(0x4b000000u | (r & 63u)), 8388608.f);
+  const float scale = float_of(sgn | (static_cast<uint32_t>(e - 1075 + 127) << 23));
+  return F2{hi, mul_rn(fma_rn(r1, 64.f, r0), scale)};
+}
+
 // a 2^n for -126 < n <= 0 on normal results (exact)
 DFM_HD F2 scale_pow2(F2 a, int n) {
   const float s = ldexpf(1.0f, n);

@@ -58,40 +58,14 @@ __device__ __forceinline__ CD cd_mul_si(CD a, float s) {
   return s > 0.f ? CD{dfm::neg(a.y), a.x} : CD{a.y, dfm::neg(a.x)};
 }
 __device__ __forceinline__ CD cd_zero() { return CD{F2{0.f, 0.f}, F2{0.f, 0.f}}; }
-__device__ __forceinline__ CD cd_from(double2 v) {
-  const float xh = static_cast<float>(v.x), yh = static_cast<float>(v.y);
-  return CD{F2{xh, static_cast<float>(v.x - static_cast<double>(xh))},
-            F2{yh, static_cast<float>(v.y - static_cast<double>(yh))}};
-}
-__device__ __forceinline__ F2 df_from(double v) {
-  const float h = static_cast<float>(v);
-  return F2{h, static_cast<float>(v - static_cast<double>(h))};
-}
-// v = hi + lo by integer operations on v's bits, without FP64 instructions (GB300's FP64 pipe
-// runs at a small fraction of the FP32 rate): hi holds the sign, the exponent and the leading 23
-// stored significand bits of v (truncated, so exact in FP32); the remaining 29 bits, r = r1 2^6 +
-// r0 (r1 < 2^23, r0 < 2^6, each exact in FP32 through the 2^23 magic number), give
-// lo = (r1 2^6 + r0) 2^(e - 1075), rounded once to FP32, with v's sign. Zero and subnormal v give
-// zero; |v| outside [2^-74, 2^127] takes the FP64 conversion.
-__device__ __forceinline__ F2 df_split(double v) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-  const int e = static_cast<int>((b >> 52) & 0x7ffu);
-  const unsigned sgn = static_cast<unsigned>(b >> 32) & 0x80000000u;
-  if (e == 0) return F2{__uint_as_float(sgn), 0.f};
-  if (e < 949 || e > 1150) return df_from(v);
-  const unsigned mh = static_cast<unsigned>(b >> 29) & 0x7fffffu;
-  const float hi = __uint_as_float(sgn | (static_cast<unsigned>(e - 1023 + 127) << 23) | mh);
-  const unsigned r = static_cast<unsigned>(b) & 0x1fffffffu;
-  const float r1 = __fsub_rn(__uint_as_float(0x4b000000u | (r >> 6)), 8388608.f);
-  const float r0 = __fsub_rn(__uint_as_float(0x4b000000u | (r & 63u)), 8388608.f);
-  const float scale = __uint_as_float(sgn | (static_cast<unsigned>(e - 1075 + 127) << 23));
-  return F2{hi, __fmul_rn(__fmaf_rn(r1, 64.f, r0), scale)};
-}
 __device__ __forceinline__ double d_of(F2 a) {
   return static_cast<double>(a.hi) + static_cast<double>(a.lo);
 }
 __device__ __forceinline__ double2 cd_to(CD a) { return make_double2(d_of(a.x), d_of(a.y)); }
-__device__ __forceinline__ CD cd_split(double2 v) { return CD{df_split(v.x), df_split(v.y)}; }
+// the charge spectrum's doubles, split without FP64 instructions
+__device__ __forceinline__ CD cd_split(double2 v) {
+  return CD{dfm::split_double(v.x), dfm::split_double(v.y)};
+}
 
 // sqrt(1/2) in double-float
 __device__ __forceinline__ F2 half_sqrt2() {
@@ -325,7 +299,7 @@ __global__ void __launch_bounds__(kDThreads, 2)
 __global__ void k_spectra_to_df(double* __restrict__ v, size_t n) {
   const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
   if (i < n) {
-    const F2 d = df_from(v[i]);
+    const F2 d = dfm::split_double_fp64(v[i]);
     reinterpret_cast<F2*>(v)[i] = d;
   }
 }

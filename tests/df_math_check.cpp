@@ -3,14 +3,61 @@
 // line, the largest relative errors of the potential erfc(x)/rho, the force coefficient
 // [erfc(x)/rho + (2 kappa/sqrt(pi)) e^{-x^2}]/rho^2 and the Hessian term of the adjoint over
 // rho in (0, 1] (eq. (ewald_split), eq. (summation_short)), printed as one JSON line.
+// With the argument "split": the bit-level split of doubles into double-float that the FP64
+// path's fused z solve applies to the charge spectrum, against the doubles themselves.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <memory>
+#include <random>
 
 #include "df_math.cuh"
 
+// Largest relative error of hi + lo over seeded random doubles whose magnitudes span
+// 10^-22 .. 10^37 (the fast path; smaller and larger ones take the FP64 conversion), how many
+// violate |lo| < ulp(hi) or carry the wrong sign, and the special values.
+static int split_check() {
+  std::mt19937_64 gen(20210302);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  std::uniform_real_distribution<double> ud(-22.0, 37.0);
+  double worst = 0.0, worst_slow = 0.0;
+  long bad_ulp = 0, bad_sign = 0, fast = 0;
+  for (int k = 0; k < 400000; ++k) {
+    const double v = nd(gen) * std::pow(10.0, ud(gen));
+    if (v == 0.0) continue;
+    const dfm::F2 d = dfm::split_double(v);
+    const double err = std::fabs((static_cast<double>(d.hi) + d.lo - v) / v);
+    const int e = static_cast<int>((dfm::bits_of(v) >> 52) & 0x7ff);
+    if (e >= 949 && e <= 1150) {
+      ++fast;
+      worst = std::fmax(worst, err);
+      if (std::fabs(d.lo) >= std::ldexp(std::fabs(d.hi), -23)) ++bad_ulp;
+      if ((d.hi < 0) != (v < 0) || (d.lo != 0 && (d.lo < 0) != (v < 0))) ++bad_sign;
+    } else {
+      worst_slow = std::fmax(worst_slow, err);
+    }
+  }
+  const dfm::F2 z = dfm::split_double(0.0), nz = dfm::split_double(-0.0);
+  const dfm::F2 one = dfm::split_double(1.0), third = dfm::split_double(-1.0 / 3.0);
+  const double sub = std::ldexp(1.0, -1050);  // subnormal
+  const dfm::F2 s = dfm::split_double(sub);
+  const double edge = std::ldexp(1.0, -74);  // smallest value on the fast path
+  const dfm::F2 ed = dfm::split_double(edge * 1.2345);
+  std::printf("{\"fast\": %ld, \"worst\": %.3e, \"worst_slow\": %.3e, \"bad_ulp\": %ld, "
+              "\"bad_sign\": %ld, \"zero\": %d, \"neg_zero\": %d, \"one\": %d, "
+              "\"third_err\": %.3e, \"subnormal\": %d, \"edge_err\": %.3e}\n",
+              fast, worst, worst_slow, bad_ulp, bad_sign,
+              z.hi == 0.f && z.lo == 0.f && !std::signbit(z.hi),
+              nz.hi == 0.f && std::signbit(nz.hi), one.hi == 1.f && one.lo == 0.f,
+              std::fabs((static_cast<double>(third.hi) + third.lo) * 3.0 + 1.0),
+              s.hi == 0.f && s.lo == 0.f,
+              std::fabs((static_cast<double>(ed.hi) + ed.lo) / (edge * 1.2345) - 1.0));
+  return 0;
+}
+
 int main(int argc, char** argv) {
+  if (argc > 1 && std::strcmp(argv[1], "split") == 0) return split_check();
   const double kappa = argc > 1 ? std::atof(argv[1]) : 3.0;
   std::unique_ptr<dfm::PairDF> P(new dfm::PairDF());
   if (!dfm::fit_pair_df(kappa, *P)) {

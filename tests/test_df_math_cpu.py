@@ -30,8 +30,9 @@ def checker(tmp_path_factory):
     return exe
 
 
-def run(exe, kappa):
-    out = subprocess.run([exe, repr(kappa)], check=True, capture_output=True, text=True)
+def run(exe, arg):
+    out = subprocess.run([exe, str(arg) if isinstance(arg, str) else repr(arg)], check=True,
+                         capture_output=True, text=True)
     return json.loads(out.stdout)
 
 
@@ -50,3 +51,17 @@ def test_pair_function_fit_range(checker):
     # the exponential's table covers kappa^2 < 88
     assert run(checker, 9.0)["fit"]
     assert not run(checker, 9.5)["fit"]
+
+
+def test_split_double_by_bits(checker):
+    # the charge spectrum enters the FP64 path's fused z solve as double-float, split by integer
+    # operations on each double's bits: hi the leading 24 significand bits, lo the other 29
+    # rounded once, so |hi + lo - v| <= 2^-47 |v| and |lo| < ulp(hi)
+    r = run(checker, "split")
+    assert r["fast"] > 350000
+    assert r["worst"] <= 2.0 ** -47, r
+    assert r["bad_ulp"] == 0 and r["bad_sign"] == 0, r
+    assert r["zero"] and r["neg_zero"] and r["one"] and r["subnormal"], r
+    assert r["third_err"] <= 3 * 2.0 ** -47 and r["edge_err"] <= 2.0 ** -47, r
+    # the FP64 conversion outside the fast path (FP32's rounding of hi, then of the rest)
+    assert r["worst_slow"] < 1e-13, r
