@@ -29,7 +29,8 @@ def _worker(rank, world, port, out):
 def test_two_rank_timing_is_max_and_rate_counts_all_ranks():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    # the manager's server process spawned too: no fork of a process that may hold threads
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
